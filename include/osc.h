@@ -1,0 +1,177 @@
+/*
+ * osc.h -- C ABI of the GB300 (sm_103a) event-by-event neutrino oscillation
+ * reweighting library.
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2.1 and its code
+ * listing): event energies are placed in device memory, the components that
+ * depend only on the oscillation parameters are computed once per parameter
+ * set, a kernel computes every event's oscillation probability in parallel,
+ * and the results come back to the caller.  Unlike the paper, samples stay
+ * resident on the device between calls and many parameter points are handled
+ * in one launch.
+ *
+ * Physics (Sec. 1.1, Eq. (1) and the matter term; Sec. 1.1.1 weights):
+ *   M = U diag(0, dm21, dm31) U^dagger + diag(A, 0, 0) [eV^2], dm31 = dm32 + dm21,
+ *   U the PMNS matrix (PDG parametrisation, U_e3 = s13 e^{-i delta}),
+ *   A = k_A * Y_e * rho[g/cm^3] * E_true[GeV], k_A = 2 sqrt(2) G_F N_A (hbar c)^3
+ *     = 1.526493e-4 eV^2/GeV per g/cm^3,
+ *   antineutrinos: U -> U*, A -> -A,
+ *   P(alpha -> beta) = |[exp(-i c_L M L / E_true)]_{beta alpha}|^2,
+ *     c_L = 1e-6 / (2 hbar c[eV m]) = 2.533865 (eV^2, km, GeV),
+ *   event weight   = P * w_mc * norm,
+ *   histogram bin  = FP32 sequence x = (float)escale * e_reco, t = x - (float)lo,
+ *                    u = t * (float)(nbins / (hi - lo)); kept iff t >= 0 and
+ *                    u < nbins; bin = (int)u  (half-open [lo, hi), no clamping).
+ *
+ * Conventions
+ *   - Ownership: the library owns every device copy it makes (samples, point
+ *     table, work lists, accumulators).  The caller owns every output buffer.
+ *     No caller pointer is retained after a call returns (except the CUDA
+ *     stream given to osc_create, which must outlive the context).
+ *   - Errors: every call returns an osc_status.  On error, outputs are left
+ *     untouched and osc_last_error() describes the cause.  Invalid input is
+ *     rejected on the host before any launch.  A CUDA error poisons the
+ *     context: later calls return OSC_E_STATE.  Device code never traps.
+ *   - Threading: a context is not re-entrant, except osc_submit/osc_wait,
+ *     which may be called from any thread while serving runs.
+ *   - Determinism: histogram bins are accumulated in exact 128-bit fixed
+ *     point, so results are bitwise identical for any tile shape, launch
+ *     configuration or scheduling order.
+ */
+#ifndef OSC_GB300_H
+#define OSC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OSC_OK = 0,
+    OSC_E_ARG = 1,     /* malformed argument (null pointer, bad enum, bad size) */
+    OSC_E_RANGE = 2,   /* value outside the physical / supported range */
+    OSC_E_NOMEM = 3,   /* device allocation failed or workspace cap exceeded */
+    OSC_E_CUDA = 4,    /* a CUDA call failed; the context is now poisoned */
+    OSC_E_STATE = 5,   /* context poisoned, or call not valid in this state */
+    OSC_E_TIMEOUT = 6, /* a bounded wait expired */
+    OSC_E_BUSY = 7     /* serving queue full */
+} osc_status;
+
+typedef enum {
+    OSC_FP64 = 0,      /* all-FP64 path: closed-form cubic eigenvalues, FP64 amplitude */
+    OSC_FP32_BULK = 1  /* FP32 bulk with FP64-derived per-point constants (see DESIGN) */
+} osc_precision;
+
+typedef enum { OSC_NU_E = 0, OSC_NU_MU = 1, OSC_NU_TAU = 2 } osc_flavour;
+
+typedef struct osc_ctx osc_ctx;
+
+/* One resident Monte Carlo sample at a fixed baseline and constant density
+ * (Sec. 2.1: the per-event energy arrays; Sec. 1.1: L, rho).  All arrays are
+ * host pointers of length n, read during osc_load_sample only. */
+typedef struct {
+    int64_t n;                /* number of events, >= 1 */
+    const float *e_true;      /* true neutrino energy [GeV], finite, > 0 */
+    const float *e_reco;      /* reconstructed energy [GeV], finite */
+    const float *w_mc;        /* Monte Carlo weight, finite */
+    const uint8_t *flav_in;   /* initial flavour alpha, osc_flavour */
+    const uint8_t *flav_out;  /* final flavour beta, osc_flavour */
+    const uint8_t *is_nubar;  /* 0 = neutrino, 1 = antineutrino */
+    double baseline_km;       /* L > 0 */
+    double density_gcc;       /* rho >= 0 */
+    double ye;                /* electron fraction in [0, 1] */
+} osc_sample_desc;
+
+/* One oscillation-parameter point plus its systematics (Table 1 fields;
+ * Sec. 1.1.1 energy-scale systematic).  sign(dm32) selects the hierarchy. */
+typedef struct {
+    double s2_12, s2_13, s2_23; /* sin^2 theta_ij in [0, 1] */
+    double dm21;                /* eV^2, > 0 */
+    double dm32;                /* eV^2, |dm32| > dm21 (non-degenerate vacuum spectrum) */
+    double dcp;                 /* rad, finite */
+    double escale;              /* energy scale applied to E_reco before binning, > 0 */
+    double norm;                /* weight normalisation, finite */
+} osc_point;
+
+/* Library version string (static storage). */
+const char *osc_version(void);
+
+/* Create a context on CUDA device `device`.  workspace_cap_bytes bounds all
+ * device memory the context allocates (0 = no cap).  cuda_stream is a
+ * cudaStream_t to launch on (NULL: the context creates its own). */
+osc_status osc_create(int device, size_t workspace_cap_bytes, void *cuda_stream, osc_ctx **out);
+
+/* Stop serving, free every device and host resource of the context. NULL is a no-op. */
+void osc_destroy(osc_ctx *ctx);
+
+/* Last error message of the context (static "no context" for NULL). */
+const char *osc_last_error(const osc_ctx *ctx);
+
+/* Validate, sort by (channel, E_reco) and copy a sample to the device
+ * (Sec. 2.1: host arrays copied to device memory).  The event order seen by
+ * osc_reweight outputs is the caller's original order. */
+osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *desc, int32_t *sample_id);
+
+/* Free a resident sample. */
+osc_status osc_unload_sample(osc_ctx *ctx, int32_t sample_id);
+
+/* Replace the parameter-point table with n_points host points (copied), and
+ * compute every point's parameter-only constants on the device in FP64
+ * (Sec. 2.1: "components dependent only on the oscillation parameters").
+ * n_points in [1, 1<<20]. */
+osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points);
+
+/* Per-event probability and weight (P * w_mc * norm) for one point of the
+ * table, in the caller's event order (Sec. 2.1: result array copied back).
+ * out_prob / out_weight: n doubles each, either may be NULL; host pointers if
+ * out_on_device == 0, device pointers otherwise.  Synchronous. */
+osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_precision prec,
+                        double *out_prob, double *out_weight, int out_on_device);
+
+/* Event-by-event binned PDFs (Sec. 1.1.1): out[s][p][b] for s < n_samples,
+ * p < n_points (table points point_begin + p), b < nbins, over [lo, hi).
+ * All (sample, point, event) work runs in one launch.  out is host memory if
+ * out_on_device == 0 (the call then returns after the copy), device memory
+ * otherwise (the call returns once the work is enqueued on the context stream). */
+osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                         int32_t point_begin, int32_t n_points, osc_precision prec, double lo,
+                         double hi, int32_t nbins, double *out, int out_on_device);
+
+/* Launch-shape control.  points_per_block in {1, 4, 16, 64, 256}, or 0 to let
+ * the autotuner choose per workload class (default).  Results never depend on it. */
+osc_status osc_set_tile(osc_ctx *ctx, int32_t points_per_block, int32_t events_per_item);
+
+/* Enable (1) / disable (0) CUDA-event timing of each kernel; osc_last_timing
+ * then reports the durations (ms) of the last constants, histogram and
+ * finalize kernels (negative when not measured). */
+osc_status osc_enable_timing(osc_ctx *ctx, int enable);
+osc_status osc_last_timing(const osc_ctx *ctx, double *k_const_ms, double *k_hist_ms,
+                           double *k_final_ms);
+
+/* Number of kernels this context has launched so far (graph replays count
+ * each kernel node). */
+osc_status osc_launch_count(const osc_ctx *ctx, uint64_t *count);
+
+/* Block until all work enqueued by the context has finished. */
+osc_status osc_sync(osc_ctx *ctx);
+
+/* Continuous-batching serving loop (spec item 5; each request is one MCMC
+ * step's reweight, Sec. 2.2).  A scheduler thread inside the library admits
+ * queued (sample, point) requests into at most max_slots in-flight slots under
+ * the workspace cap and packs them into persistent launches on the context
+ * stream; each request yields one nbins histogram over [lo, hi). */
+osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi, int32_t nbins);
+osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_precision prec,
+                      uint64_t *ticket);
+/* Wait for a ticket's histogram (host buffer of nbins doubles); latency_us (may
+ * be NULL) receives submit-to-completion time.  timeout_ms < 0 waits forever. */
+osc_status osc_wait(osc_ctx *ctx, uint64_t ticket, double *out_hist, int32_t timeout_ms,
+                    double *latency_us);
+osc_status osc_serve_stop(osc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSC_GB300_H */

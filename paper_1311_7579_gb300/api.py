@@ -1,0 +1,259 @@
+"""Thin Python binding of the C ABI in ``include/osc.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Arrays are numpy
+arrays (host) or torch CUDA tensors (device); a non-OK status raises
+``OscError`` carrying the status and ``osc_last_error``.  All arithmetic runs in
+the CUDA library; there is no CPU fallback -- if the library cannot be built or
+loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OSC_OK, OSC_E_ARG, OSC_E_RANGE, OSC_E_NOMEM, OSC_E_CUDA, OSC_E_STATE, OSC_E_TIMEOUT, OSC_E_BUSY = range(8)
+STATUS_NAMES = ["OSC_OK", "OSC_E_ARG", "OSC_E_RANGE", "OSC_E_NOMEM", "OSC_E_CUDA", "OSC_E_STATE",
+                "OSC_E_TIMEOUT", "OSC_E_BUSY"]
+OSC_FP64, OSC_FP32_BULK = 0, 1
+PRECISIONS = {"fp64": OSC_FP64, "fp32": OSC_FP32_BULK, OSC_FP64: OSC_FP64, OSC_FP32_BULK: OSC_FP32_BULK}
+
+# Every entry point declared in include/osc.h, in declaration order.
+ENTRY_POINTS = [
+    "osc_version", "osc_create", "osc_destroy", "osc_last_error", "osc_load_sample", "osc_unload_sample",
+    "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
+    "osc_last_timing", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
+    "osc_serve_stop",
+]
+
+
+class OscError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, message))
+
+
+class OscSampleDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64),
+                ("e_true", ctypes.c_void_p), ("e_reco", ctypes.c_void_p), ("w_mc", ctypes.c_void_p),
+                ("flav_in", ctypes.c_void_p), ("flav_out", ctypes.c_void_p), ("is_nubar", ctypes.c_void_p),
+                ("baseline_km", ctypes.c_double), ("density_gcc", ctypes.c_double), ("ye", ctypes.c_double)]
+
+
+class OscPoint(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("s2_12", "s2_13", "s2_23", "dm21", "dm32", "dcp", "escale", "norm")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Build (if stale) and load the CUDA library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i32, i64, d, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            sig = {
+                "osc_version": (ctypes.c_char_p, []),
+                "osc_create": (st, [ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+                "osc_destroy": (None, [vp]),
+                "osc_last_error": (ctypes.c_char_p, [vp]),
+                "osc_load_sample": (st, [vp, ctypes.POINTER(OscSampleDesc), ctypes.POINTER(i32)]),
+                "osc_unload_sample": (st, [vp, i32]),
+                "osc_set_params": (st, [vp, ctypes.POINTER(OscPoint), i32]),
+                "osc_reweight": (st, [vp, i32, i32, ctypes.c_int, vp, vp, ctypes.c_int]),
+                "osc_histogram": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
+                                       ctypes.c_int]),
+                "osc_set_tile": (st, [vp, i32, i32]),
+                "osc_enable_timing": (st, [vp, ctypes.c_int]),
+                "osc_last_timing": (st, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
+                "osc_launch_count": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
+                "osc_sync": (st, [vp]),
+                "osc_serve_start": (st, [vp, i32, d, d, i32]),
+                "osc_submit": (st, [vp, i32, ctypes.POINTER(OscPoint), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+                "osc_wait": (st, [vp, ctypes.c_uint64, vp, i32, ctypes.POINTER(d)]),
+                "osc_serve_stop": (st, [vp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != OSC_OK:
+        msg = lib().osc_last_error(ctx)
+        raise OscError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_device(a):
+    return a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def _points(points):
+    rows = np.ascontiguousarray(np.atleast_2d(np.asarray(points, dtype=np.float64)))
+    if rows.shape[1] != 8:
+        raise ValueError("points must have 8 columns: s2_12 s2_13 s2_23 dm21 dm32 dcp escale norm")
+    arr = (OscPoint * rows.shape[0])()
+    ctypes.memmove(arr, rows.ctypes.data, rows.nbytes)
+    return arr, rows.shape[0]
+
+
+def osc_version() -> str:
+    return lib().osc_version().decode()
+
+
+def osc_create(device=0, workspace_cap_bytes=0, cuda_stream=None):
+    out = ctypes.c_void_p()
+    s = lib().osc_create(int(device), int(workspace_cap_bytes), cuda_stream, ctypes.byref(out))
+    if s != OSC_OK:
+        raise OscError(s, "osc_create failed")
+    return out
+
+
+def osc_destroy(ctx):
+    lib().osc_destroy(ctx)
+
+
+def osc_last_error(ctx) -> str:
+    m = lib().osc_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def osc_load_sample(ctx, sample) -> int:
+    """sample: dict with n, e_true, e_reco, w_mc (float32), flav_in, flav_out, is_nubar
+    (uint8), baseline_km, density_gcc, ye."""
+    arrs = {}
+    for k, dt in (("e_true", np.float32), ("e_reco", np.float32), ("w_mc", np.float32),
+                  ("flav_in", np.uint8), ("flav_out", np.uint8), ("is_nubar", np.uint8)):
+        arrs[k] = np.ascontiguousarray(sample[k], dtype=dt)
+    n = int(sample.get("n", arrs["e_true"].size))
+    for k, a in arrs.items():
+        if a.size < n:
+            raise ValueError("array %s shorter than n" % k)
+    desc = OscSampleDesc(n, *[arrs[k].ctypes.data for k in ("e_true", "e_reco", "w_mc", "flav_in", "flav_out",
+                                                            "is_nubar")],
+                         float(sample["baseline_km"]), float(sample["density_gcc"]), float(sample["ye"]))
+    sid = ctypes.c_int32()
+    _check(ctx, lib().osc_load_sample(ctx, ctypes.byref(desc), ctypes.byref(sid)))
+    return sid.value
+
+
+def osc_unload_sample(ctx, sample_id):
+    _check(ctx, lib().osc_unload_sample(ctx, int(sample_id)))
+
+
+def osc_set_params(ctx, points):
+    arr, n = _points(points)
+    _check(ctx, lib().osc_set_params(ctx, arr, n))
+
+
+def osc_reweight(ctx, sample_id, point, prec, out_prob=None, out_weight=None):
+    """Outputs: numpy float64 arrays (host) or torch float64 CUDA tensors (device), n each."""
+    dev = _is_device(out_prob) or _is_device(out_weight)
+    _check(ctx, lib().osc_reweight(ctx, int(sample_id), int(point), PRECISIONS[prec], _ptr(out_prob),
+                                   _ptr(out_weight), 1 if dev else 0))
+    return out_prob, out_weight
+
+
+def osc_histogram(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, out=None):
+    """out: numpy (n_samples, n_points, nbins) float64 (allocated if None) or a torch CUDA tensor."""
+    ids = np.ascontiguousarray(np.atleast_1d(sample_ids), dtype=np.int32)
+    if out is None:
+        out = np.zeros((ids.size, int(n_points), int(nbins)))
+    dev = _is_device(out)
+    _check(ctx, lib().osc_histogram(ctx, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size,
+                                    int(point_begin), int(n_points), PRECISIONS[prec], float(lo), float(hi),
+                                    int(nbins), _ptr(out), 1 if dev else 0))
+    return out
+
+
+def osc_set_tile(ctx, points_per_block=0, events_per_item=0):
+    _check(ctx, lib().osc_set_tile(ctx, int(points_per_block), int(events_per_item)))
+
+
+def osc_enable_timing(ctx, enable=True):
+    _check(ctx, lib().osc_enable_timing(ctx, 1 if enable else 0))
+
+
+def osc_last_timing(ctx):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().osc_last_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def osc_launch_count(ctx) -> int:
+    v = ctypes.c_uint64()
+    _check(ctx, lib().osc_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def osc_sync(ctx):
+    _check(ctx, lib().osc_sync(ctx))
+
+
+def osc_serve_start(ctx, max_slots, lo, hi, nbins):
+    _check(ctx, lib().osc_serve_start(ctx, int(max_slots), float(lo), float(hi), int(nbins)))
+
+
+def osc_submit(ctx, sample_id, point, prec) -> int:
+    arr, n = _points(point)
+    t = ctypes.c_uint64()
+    _check(ctx, lib().osc_submit(ctx, int(sample_id), arr, PRECISIONS[prec], ctypes.byref(t)))
+    return t.value
+
+
+def osc_wait(ctx, ticket, nbins, timeout_ms=-1, out=None):
+    """Returns (histogram, latency_us)."""
+    if out is None:
+        out = np.zeros(int(nbins))
+    lat = ctypes.c_double()
+    _check(ctx, lib().osc_wait(ctx, int(ticket), out.ctypes.data, int(timeout_ms), ctypes.byref(lat)))
+    return out, lat.value
+
+
+def osc_serve_stop(ctx):
+    _check(ctx, lib().osc_serve_stop(ctx))
+
+
+class Context:
+    """Owning handle: ``with Context() as c: osc_load_sample(c.ptr, ...)``."""
+
+    def __init__(self, device=0, workspace_cap_bytes=0, cuda_stream=None):
+        self.ptr = osc_create(device, workspace_cap_bytes, cuda_stream)
+
+    def close(self):
+        if self.ptr:
+            osc_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,110 @@
+// osc_ctx.h -- the context object behind the C ABI (host runtime internals).
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "osc_internal.h"
+
+struct osc_serve;  // serving state (osc_serve.cu)
+
+namespace osc {
+
+struct Sample {
+    int32_t id = -1;
+    int64_t n = 0, n_pad = 0;
+    double L = 0, rho = 0, ye = 0;
+    int32_t frac_bits = 96;
+    float *e_true = nullptr, *e_reco = nullptr, *w_mc = nullptr;
+    uint8_t *chan = nullptr;
+    int32_t *perm = nullptr;
+    SampleDev dev{};
+};
+
+// A cached launch plan for one histogram call shape.
+struct Plan {
+    std::vector<int32_t> sample_ids;
+    int32_t point_begin = 0, n_points = 0, nbins = 0, prec = 0, pt = 0, chunk = 0;
+    int64_t n_hist = 0;
+    int32_t n_items = 0, grid = 0;
+    WorkItem *d_items = nullptr;
+    SampleDev *d_samples = nullptr;
+    double *d_hmeta = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_hist_node = nullptr, n_final_node = nullptr;
+    uint64_t last_use = 0;
+};
+
+}  // namespace osc
+
+struct osc_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t cap = 0, used = 0;
+    std::unordered_map<void *, size_t> sizes;
+    std::string err;
+    bool poisoned = false;
+    std::mutex api_mu;  // serialises ABI calls against the serving thread
+
+    std::map<int32_t, osc::Sample *> samples;
+    int32_t next_id = 0;
+
+    std::vector<osc_point> pts;
+    osc_point *d_pts = nullptr;
+    float *d_pc32 = nullptr;
+    double *d_pc64 = nullptr;
+    int32_t pts_cap = 0;
+
+    unsigned long long *d_acc = nullptr;
+    int64_t acc_cap_bins = 0;
+    int32_t *d_counter = nullptr;
+    double *d_out = nullptr;
+    int64_t out_cap = 0;
+    double *d_rw = nullptr;
+    int64_t rw_cap = 0;
+
+    std::list<osc::Plan *> plans;
+    uint64_t plan_clock = 0;
+
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    double t_const = -1, t_hist = -1, t_final = -1;
+    uint64_t launches = 0;
+
+    int32_t tile_pt = 0, tile_chunk = 0;
+    std::map<std::string, std::pair<int32_t, int32_t>> tuned;
+
+    osc_serve *serve = nullptr;
+};
+
+namespace osc {
+
+// helpers shared by the runtime and the serving loop
+osc_status fail(osc_ctx *c, osc_status s, const std::string &msg);
+osc_status fail_cuda(osc_ctx *c, cudaError_t e, const char *what);
+osc_status dalloc(osc_ctx *c, void **p, size_t bytes);
+void dfree(osc_ctx *c, void *p);
+osc_status validate_point(osc_ctx *c, const osc_point &p, int index);
+osc_status ensure_acc(osc_ctx *c, int64_t bins);
+// Histogram launch over explicit work (used by osc_histogram and serving).
+osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_items, int32_t n_items, int grid,
+                            const SampleDev *d_samples, const float *pc32, const double *pc64, int32_t nbins,
+                            double lo, double hi, const double *d_hmeta, int64_t n_hist, double *d_out,
+                            cudaStream_t st);
+int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items);
+void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,
+                 int32_t chunk, int64_t acc_hist_base, std::vector<WorkItem> &items);
+
+}  // namespace osc

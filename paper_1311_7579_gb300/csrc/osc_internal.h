@@ -1,0 +1,117 @@
+// osc_internal.h -- types shared by the host runtime and the CUDA kernels of
+// the GB300 oscillation-reweighting library.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/osc.h"
+
+namespace osc {
+
+// Unit constant of the propagation phase: lambda[eV^2] L[km] / E[GeV] -> radians
+// of lambda L / (2E); 1e-6 / (2 hbar c), hbar c = 1.973269804e-7 eV m (CODATA 2018).
+constexpr double kCL = 1e-6 / (2.0 * 1.973269804e-7);
+// Matter term A = kKA * Y_e * rho[g/cm^3] * E[GeV] in eV^2: 2 sqrt(2) G_F N_A (hbar c)^3 * 1e9
+// with G_F = 1.1663788e-23 eV^-2 (PDG), N_A = 6.02214076e23, hbar c = 1.973269804e-5 eV cm.
+double matter_k_A();
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Channel id of an event: nubar * 9 + alpha * 3 + beta.
+__host__ __device__ inline int chan_id(int alpha, int beta, int nubar) { return nubar * 9 + alpha * 3 + beta; }
+
+// ---- per-point constants (written by the constants kernel in FP64) ----------
+// FP32 block (floats).  Layout offsets:
+enum PC32 : int {
+    C32_P0 = 0, C32_P1, C32_Q0, C32_Q1, C32_Q2,  // depressed-cubic seed coefficients in A
+    C32_T0, C32_C10, C32_SMT,                    // tr H0, c1(A=0), H0_mumu + H0_tautau
+    C32_D0, C32_D1, C32_D2,                      // sorted vacuum eigenvalues (eV^2)
+    C32_G01, C32_G02, C32_G12,                   // vacuum gaps d_i - d_j
+    C32_V1H, C32_V1L, C32_V2H, C32_V2L,          // (d1 - d0), (d2 - d0) as float-float
+    C32_S0, C32_PI0, C32_W0, C32_E0,             // shifted-cubic constants, sorted root 0
+    C32_S1, C32_PI1, C32_W1, C32_E1,             // ... sorted root 1
+    C32_ESCALE,
+    C32_CH = 32,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
+    C32_STRIDE = 32 + 54 + 10                    // = 96 floats, 384 B
+};
+// FP64 block (doubles).
+enum PC64 : int {
+    C64_P0 = 0, C64_P1, C64_Q0, C64_Q1, C64_Q2, C64_T0, C64_C10, C64_SMT, C64_ESCALE, C64_NORM,
+    C64_CH = 16,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
+    C64_STRIDE = 16 + 54 + 2                     // = 72 doubles, 576 B
+};
+
+// ---- resident sample as seen by a kernel ----------------------------------
+struct SampleDev {
+    const float *e_true;      // sorted by (channel, e_reco)
+    const float *e_reco;
+    const float *w_mc;
+    const uint8_t *chan;      // channel id
+    const int32_t *perm;      // sorted position -> caller's event index
+    int64_t n;
+    double kA_rhoye;          // k_A * rho * Y_e  [eV^2 / GeV]
+    double cLL;               // c_L * L           [rad GeV / eV^2]
+    float kA_rhoye_f;
+    float rev_hi, rev_lo;     // c_L L / (2 pi) as float-float [revolutions GeV / eV^2]
+    float hscale_f;           // 2^(F-64): FP32 weight -> fixed-point high word
+    double hscale_d;
+    int32_t frac_bits;        // F
+    int32_t pad;
+};
+
+// One unit of histogram work: a point tile of one sample over an event range.
+struct WorkItem {
+    int32_t sample;           // index into the launch's SampleDev table
+    int32_t point_base;       // first point (row of the constants tables)
+    int32_t n_pts;            // points in this tile (<= points per block)
+    int32_t ev_count;         // events in this item
+    int64_t ev_begin;         // first (sorted) event
+    int64_t acc_base;         // first histogram of the tile (histogram index)
+};
+
+struct HistParams {
+    const WorkItem *items;
+    int32_t n_items;
+    int32_t nbins;
+    const SampleDev *samples;
+    const float *pc32;
+    const double *pc64;
+    unsigned long long *acc;  // 128-bit fixed-point bins: (lo, hi) per bin
+    int32_t *counter;         // dynamic work counter (reset by the finalize kernel)
+    float lo_f, inv_f, nb_f;
+    int32_t hist_stride_pts;  // histogram index step between consecutive points of a tile
+};
+
+struct FinalParams {
+    unsigned long long *acc;
+    const double *hmeta;      // per histogram: (2^(64-F), 2^-F, point index)
+    const double *pc64;       // per-point FP64 constants (norm)
+    double *out;
+    int64_t n_hist;
+    int32_t nbins;
+    int32_t *counter;
+};
+
+struct ReweightParams {
+    SampleDev s;
+    int32_t point;
+    const float *pc32;
+    const double *pc64;
+    double norm;
+    double *out_prob;         // caller order, may be null
+    double *out_weight;
+};
+
+// Launch helpers implemented in the kernel translation units.
+enum Prec { kFP64 = 0, kFP32 = 1 };
+cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
+cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
+cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
+cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
+// Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
+const void *hist_kernel_fn(int prec, int pt);
+const void *final_kernel_fn();
+int hist_threads();
+
+}  // namespace osc

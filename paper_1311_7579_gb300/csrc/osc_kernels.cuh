@@ -1,0 +1,409 @@
+// osc_kernels.cuh -- CUDA kernels of the reweighting hot path (sm_103a).
+//
+//   k_point_consts  per parameter point, FP64: PMNS matrix, vacuum Hamiltonian
+//                   invariants, cubic coefficients, sorted vacuum spectrum and the
+//                   per-channel (M)_ba, (M^2)_ba pieces (Sec. 2.1: the components
+//                   that depend only on the oscillation parameters).
+//   k_hist<P, PT>   persistent fused kernel: streams the (channel, E_reco)-sorted
+//                   event SoA through shared memory with 128-bit loads, computes
+//                   P, weight and bin for PT points x the tile's events, and
+//                   accumulates each lane's bins run-length in exact 128-bit fixed
+//                   point in registers, flushing with integer atomics (Sec. 1.1.1).
+//   k_final         128-bit bins -> double * norm, and clears the accumulators.
+//   k_reweight<P>   per-event probability and weight in the caller's event order.
+#pragma once
+
+#include "osc_internal.h"
+#include "osc_math.cuh"
+
+namespace osc {
+
+constexpr int kNT = 256;          // threads per block of the histogram kernel
+constexpr int kET = 4 * kNT;      // events per shared-memory tile
+
+// ---------------------------------------------------------------- constants
+struct cplx64 {
+    double re, im;
+};
+__device__ __forceinline__ cplx64 cmul_conj(cplx64 a, double m, cplx64 b) {
+    // a * m * conj(b)
+    return {m * (a.re * b.re + a.im * b.im), m * (a.im * b.re - a.re * b.im)};
+}
+
+__device__ __forceinline__ void split_ff(double v, float *hi, float *lo) {
+    const float h = (float)v;
+    *hi = h;
+    *lo = (float)(v - (double)h);
+}
+
+__device__ inline void point_consts_one(const osc_point &P, float *c32, double *c64) {
+    const double s12 = sqrt(P.s2_12), c12 = sqrt(1.0 - P.s2_12);
+    const double s13 = sqrt(P.s2_13), c13 = sqrt(1.0 - P.s2_13);
+    const double s23 = sqrt(P.s2_23), c23 = sqrt(1.0 - P.s2_23);
+    double sd, cd;
+    sincos(P.dcp, &sd, &cd);
+    // PDG PMNS U[flavour][mass]: U_e3 = s13 e^{-i delta}, e^{+i delta} in the mu, tau rows
+    cplx64 U[3][3];
+    U[0][0] = {c12 * c13, 0.0};
+    U[0][1] = {s12 * c13, 0.0};
+    U[0][2] = {s13 * cd, -s13 * sd};
+    U[1][0] = {-s12 * c23 - c12 * s23 * s13 * cd, -c12 * s23 * s13 * sd};
+    U[1][1] = {c12 * c23 - s12 * s23 * s13 * cd, -s12 * s23 * s13 * sd};
+    U[1][2] = {s23 * c13, 0.0};
+    U[2][0] = {s12 * s23 - c12 * c23 * s13 * cd, -c12 * c23 * s13 * sd};
+    U[2][1] = {-c12 * s23 - s12 * c23 * s13 * cd, -s12 * c23 * s13 * sd};
+    U[2][2] = {c23 * c13, 0.0};
+    const double dm21 = P.dm21, dm31 = P.dm32 + P.dm21;
+    const double m[3] = {0.0, dm21, dm31};
+    // H0 = U diag(m) U^dagger, H2 = H0^2 = U diag(m^2) U^dagger, entries [beta][alpha]
+    cplx64 H[3][3], H2[3][3];
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            cplx64 h = {0, 0}, h2 = {0, 0};
+            for (int k = 1; k < 3; ++k) {
+                const cplx64 t = cmul_conj(U[b][k], m[k], U[a][k]);
+                h.re += t.re; h.im += t.im;
+                h2.re += t.re * m[k]; h2.im += t.im * m[k];
+            }
+            H[b][a] = h;
+            H2[b][a] = h2;
+        }
+    const double T0 = dm21 + dm31;
+    const double c10 = dm21 * dm31;
+    const double smt = H[1][1].re + H[2][2].re;
+    const double mee = H[1][1].re * H[2][2].re - (H[1][2].re * H[1][2].re + H[1][2].im * H[1][2].im);
+    // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
+    //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee
+    const double p0 = c10 - T0 * T0 / 3.0, p1 = smt - 2.0 * T0 / 3.0;
+    const double q0 = -2.0 * T0 * T0 * T0 / 27.0 + c10 * T0 / 3.0;
+    const double q1 = -2.0 * T0 * T0 / 9.0 + c10 / 3.0 + smt * T0 / 3.0 - mee;
+    const double q2 = -2.0 * T0 / 9.0 + smt / 3.0;
+    // sorted vacuum spectrum and |U_e|^2 in the same order
+    const double ze[3] = {U[0][0].re * U[0][0].re, U[0][1].re * U[0][1].re,
+                          U[0][2].re * U[0][2].re + U[0][2].im * U[0][2].im};
+    double d[3], z[3];
+    if (dm31 > 0) {
+        d[0] = 0.0; d[1] = dm21; d[2] = dm31;
+        z[0] = ze[0]; z[1] = ze[1]; z[2] = ze[2];
+    } else {
+        d[0] = dm31; d[1] = 0.0; d[2] = dm21;
+        z[0] = ze[2]; z[1] = ze[0]; z[2] = ze[1];
+    }
+    double S[2], PI[2], W[2], E[2];
+    for (int l = 0; l < 2; ++l) {
+        const int j = (l + 1) % 3, k = (l + 2) % 3;
+        const double aj = d[l] - d[j], ak = d[l] - d[k];
+        S[l] = aj + ak;
+        PI[l] = aj * ak;
+        W[l] = z[l] * (aj + ak) + z[j] * ak + z[k] * aj;
+        E[l] = z[l] * aj * ak;
+    }
+    c32[C32_P0] = (float)p0; c32[C32_P1] = (float)p1;
+    c32[C32_Q0] = (float)q0; c32[C32_Q1] = (float)q1; c32[C32_Q2] = (float)q2;
+    c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10; c32[C32_SMT] = (float)smt;
+    c32[C32_D0] = (float)d[0]; c32[C32_D1] = (float)d[1]; c32[C32_D2] = (float)d[2];
+    c32[C32_G01] = (float)(d[0] - d[1]); c32[C32_G02] = (float)(d[0] - d[2]); c32[C32_G12] = (float)(d[1] - d[2]);
+    split_ff(d[1] - d[0], &c32[C32_V1H], &c32[C32_V1L]);
+    split_ff(d[2] - d[0], &c32[C32_V2H], &c32[C32_V2L]);
+    c32[C32_S0] = (float)S[0]; c32[C32_PI0] = (float)PI[0]; c32[C32_W0] = (float)W[0]; c32[C32_E0] = (float)E[0];
+    c32[C32_S1] = (float)S[1]; c32[C32_PI1] = (float)PI[1]; c32[C32_W1] = (float)W[1]; c32[C32_E1] = (float)E[1];
+    c32[C32_ESCALE] = (float)P.escale;
+    c64[C64_P0] = p0; c64[C64_P1] = p1; c64[C64_Q0] = q0; c64[C64_Q1] = q1; c64[C64_Q2] = q2;
+    c64[C64_T0] = T0; c64[C64_C10] = c10; c64[C64_SMT] = smt;
+    c64[C64_ESCALE] = P.escale; c64[C64_NORM] = P.norm;
+    // channel (alpha -> beta): X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const int o = 6 * (a * 3 + b);
+            double Zr = 0, Zi = 0;
+            if (a == 0) { Zr += H[b][0].re; Zi += H[b][0].im; }
+            if (b == 0) { Zr += H[0][a].re; Zi += H[0][a].im; }
+            const double v[6] = {H[b][a].re, H[b][a].im, H2[b][a].re, H2[b][a].im, Zr, Zi};
+            for (int t = 0; t < 6; ++t) {
+                c32[C32_CH + o + t] = (float)v[t];
+                c64[C64_CH + o + t] = v[t];
+            }
+        }
+}
+
+// ------------------------------------------------------------ lane constants
+__device__ __forceinline__ void load_pt32(const float *__restrict__ c, Pt32 &o) {
+    o.p0 = c[C32_P0]; o.p1 = c[C32_P1]; o.q0 = c[C32_Q0]; o.q1 = c[C32_Q1]; o.q2 = c[C32_Q2];
+    o.T0 = c[C32_T0]; o.c10 = c[C32_C10]; o.smt = c[C32_SMT];
+    o.d0 = c[C32_D0]; o.d1 = c[C32_D1]; o.d2 = c[C32_D2];
+    o.g01 = c[C32_G01]; o.g02 = c[C32_G02]; o.g12 = c[C32_G12];
+    o.v1h = c[C32_V1H]; o.v1l = c[C32_V1L]; o.v2h = c[C32_V2H]; o.v2l = c[C32_V2L];
+    o.S0 = c[C32_S0]; o.PI0 = c[C32_PI0]; o.W0 = c[C32_W0]; o.E0 = c[C32_E0];
+    o.S1 = c[C32_S1]; o.PI1 = c[C32_PI1]; o.W1 = c[C32_W1]; o.E1 = c[C32_E1];
+}
+__device__ __forceinline__ void load_ch32(const float *__restrict__ c, int ch, Ch32 &o) {
+    const int nubar = ch >= 9;
+    const int ab = ch - 9 * nubar;
+    const float *v = c + C32_CH + 6 * ab;
+    const float sg = nubar ? -1.0f : 1.0f;  // antineutrino: M0 -> conj(M0)
+    o.Xr = v[0]; o.Xi = sg * v[1]; o.Yr = v[2]; o.Yi = sg * v[3]; o.Zr = v[4]; o.Zi = sg * v[5];
+    o.ee = (ab == 0) ? 1.0f : 0.0f;
+    o.diag = (ab == 0 || ab == 4 || ab == 8) ? 1.0f : 0.0f;
+}
+__device__ __forceinline__ void load_pt64(const double *__restrict__ c, Pt64 &o) {
+    o.p0 = c[C64_P0]; o.p1 = c[C64_P1]; o.q0 = c[C64_Q0]; o.q1 = c[C64_Q1]; o.q2 = c[C64_Q2];
+    o.T0 = c[C64_T0]; o.c10 = c[C64_C10]; o.smt = c[C64_SMT];
+}
+__device__ __forceinline__ void load_ch64(const double *__restrict__ c, int ch, Ch64 &o) {
+    const int nubar = ch >= 9;
+    const int ab = ch - 9 * nubar;
+    const double *v = c + C64_CH + 6 * ab;
+    const double sg = nubar ? -1.0 : 1.0;
+    o.Xr = v[0]; o.Xi = sg * v[1]; o.Yr = v[2]; o.Yi = sg * v[3]; o.Zr = v[4]; o.Zi = sg * v[5];
+    o.ee = (ab == 0) ? 1.0 : 0.0;
+    o.diag = (ab == 0 || ab == 4 || ab == 8) ? 1.0 : 0.0;
+}
+
+// -------------------------------------------------- 128-bit fixed-point bins
+// A bin holds sum(w) * 2^F as a two's-complement 128-bit integer (lo, hi).
+__device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long long &hi, unsigned long long l,
+                                       unsigned long long h) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
+}
+// y = w * 2^(F-64); exact for every FP32 w (floor and the fraction are exact).
+__device__ __forceinline__ void fx_add_f32(unsigned long long &lo, unsigned long long &hi, float y) {
+    const float fl = floorf(y);
+    const long long h = __float2ll_rz(fl);
+    const unsigned long long l = __float2ull_rz((y - fl) * 18446744073709551616.0f);
+    fx_add(lo, hi, l, (unsigned long long)h);
+}
+__device__ __forceinline__ void fx_add_f64(unsigned long long &lo, unsigned long long &hi, double y) {
+    const double fl = floor(y);
+    const long long h = __double2ll_rz(fl);
+    const unsigned long long l = __double2ull_rz((y - fl) * 18446744073709551616.0);
+    fx_add(lo, hi, l, (unsigned long long)h);
+}
+__device__ __forceinline__ void fx_flush(unsigned long long *p, unsigned long long lo, unsigned long long hi) {
+    const unsigned long long old = atomicAdd(p, lo);
+    const unsigned long long h2 = hi + ((old + lo < old) ? 1ull : 0ull);
+    if (h2) atomicAdd(p + 1, h2);
+}
+
+// ------------------------------------------------------------ event staging
+struct Stage32 {
+    float2 ae[kET];  // (A signed, e_reco)
+    float2 tt[kET];  // c_L L / (2 pi E) float-float
+    float2 wc[kET];  // (w_mc, channel bits)
+};
+struct Stage64 {
+    double a[kET];
+    double tau[kET];
+    float2 ew[kET];  // (e_reco, w_mc)
+    int ch[kET];
+};
+
+__device__ __forceinline__ void stage_one32(Stage32 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
+    const float A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
+    const float r0 = __frcp_rn(E);
+    const float rl = r0 * fmaf(-E, r0, 1.0f);
+    float th = sd.rev_hi * r0;
+    float tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
+    const float sum = th + tl;
+    tl = tl - (sum - th);
+    th = sum;
+    s.ae[j] = make_float2(A, er);
+    s.tt[j] = make_float2(th, tl);
+    s.wc[j] = make_float2(w, __int_as_float(ch));
+}
+__device__ __forceinline__ void stage_one64(Stage64 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
+    const double Ad = sd.kA_rhoye * (double)E;
+    s.a[j] = (ch >= 9) ? -Ad : Ad;
+    s.tau[j] = sd.cLL / (double)E;
+    s.ew[j] = make_float2(er, w);
+    s.ch[j] = ch;
+}
+
+template <int PREC>
+struct StageOf { using T = Stage32; };
+template <>
+struct StageOf<kFP64> { using T = Stage64; };
+
+// Load tile [base, base + nt) of the item into shared memory, 4 events per
+// thread with 128-bit loads (sample arrays are padded to a multiple of 4).
+template <int PREC>
+__device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const SampleDev &sd, int64_t base, int nt) {
+    const int j = 4 * threadIdx.x;
+    if (j >= nt) return;
+    const float4 e = *reinterpret_cast<const float4 *>(sd.e_true + base + j);
+    const float4 r = *reinterpret_cast<const float4 *>(sd.e_reco + base + j);
+    const float4 w = *reinterpret_cast<const float4 *>(sd.w_mc + base + j);
+    const uchar4 c = *reinterpret_cast<const uchar4 *>(sd.chan + base + j);
+    if (PREC == kFP32) {
+        Stage32 &t = reinterpret_cast<Stage32 &>(s);
+        stage_one32(t, j + 0, sd, e.x, r.x, w.x, c.x);
+        stage_one32(t, j + 1, sd, e.y, r.y, w.y, c.y);
+        stage_one32(t, j + 2, sd, e.z, r.z, w.z, c.z);
+        stage_one32(t, j + 3, sd, e.w, r.w, w.w, c.w);
+    } else {
+        Stage64 &t = reinterpret_cast<Stage64 &>(s);
+        stage_one64(t, j + 0, sd, e.x, r.x, w.x, c.x);
+        stage_one64(t, j + 1, sd, e.y, r.y, w.y, c.y);
+        stage_one64(t, j + 2, sd, e.z, r.z, w.z, c.z);
+        stage_one64(t, j + 3, sd, e.w, r.w, w.w, c.w);
+    }
+}
+
+// ----------------------------------------------------------- histogram kernel
+// Lane layout: PT points x (kNT / PT) event slices.  Lane (pt, sl) handles
+// point pt of the tile and the tile events sl, sl + S, sl + 2S, ... (S = kNT/PT),
+// an increasing subsequence of the sorted events, so its bin sequence is
+// monotone within a channel and a register run-length accumulator suffices.
+template <int PREC, int PT>
+__global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const HistParams prm) {
+    constexpr int S = kNT / PT;
+    __shared__ typename StageOf<PREC>::T stg;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int lp = tid % PT;
+    const int sl = tid / PT;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(prm.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= prm.n_items) break;
+        const WorkItem wi = prm.items[it];
+        const SampleDev sd = prm.samples[wi.sample];
+        const bool active = lp < wi.n_pts;
+        const int pidx = wi.point_base + (active ? lp : wi.n_pts - 1);
+        unsigned long long *accp = prm.acc + 2 * (wi.acc_base + lp) * (int64_t)prm.nbins;
+        unsigned long long alo = 0, ahi = 0;
+        int cur_b = -1, cur_ch = -1;
+        if (PREC == kFP32) {
+            const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
+            Pt32 c;
+            load_pt32(pc, c);
+            Ch32 h;
+            const float sf = pc[C32_ESCALE];
+            const float hs = sd.hscale_f;
+            for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
+                const int nt = min(kET, wi.ev_count - t0);
+                __syncthreads();
+                stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
+                __syncthreads();
+                const Stage32 &s = reinterpret_cast<const Stage32 &>(stg);
+                for (int j = sl; j < nt; j += S) {
+                    const float2 ae = s.ae[j], tt = s.tt[j], wc = s.wc[j];
+                    const int ch = __float_as_int(wc.y);
+                    if (ch != cur_ch) {
+                        cur_ch = ch;
+                        load_ch32(pc, ch, h);
+                    }
+                    const float P = prob_fp32(c, h, ae.x, tt.x, tt.y);
+                    const float w = P * wc.x;
+                    const float x = __fmul_rn(sf, ae.y);
+                    const float tb = __fsub_rn(x, prm.lo_f);
+                    const float u = __fmul_rn(tb, prm.inv_f);
+                    if (active && tb >= 0.0f && u < prm.nb_f) {
+                        const int b = __float2int_rz(u);
+                        if (b != cur_b) {
+                            if (cur_b >= 0 && (alo | ahi)) fx_flush(accp + 2 * cur_b, alo, ahi);
+                            alo = ahi = 0;
+                            cur_b = b;
+                        }
+                        fx_add_f32(alo, ahi, w * hs);
+                    }
+                }
+            }
+        } else {
+            const double *pc = prm.pc64 + (int64_t)pidx * C64_STRIDE;
+            Pt64 c;
+            load_pt64(pc, c);
+            Ch64 h;
+            const float sf = (float)pc[C64_ESCALE];
+            const double hs = sd.hscale_d;
+            for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
+                const int nt = min(kET, wi.ev_count - t0);
+                __syncthreads();
+                stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
+                __syncthreads();
+                const Stage64 &s = reinterpret_cast<const Stage64 &>(stg);
+                for (int j = sl; j < nt; j += S) {
+                    const int ch = s.ch[j];
+                    if (ch != cur_ch) {
+                        cur_ch = ch;
+                        load_ch64(pc, ch, h);
+                    }
+                    const double P = prob_fp64(c, h, s.a[j], s.tau[j]);
+                    const float2 ew = s.ew[j];
+                    const double w = P * (double)ew.y;
+                    const float x = __fmul_rn(sf, ew.x);
+                    const float tb = __fsub_rn(x, prm.lo_f);
+                    const float u = __fmul_rn(tb, prm.inv_f);
+                    if (active && tb >= 0.0f && u < prm.nb_f) {
+                        const int b = __float2int_rz(u);
+                        if (b != cur_b) {
+                            if (cur_b >= 0 && (alo | ahi)) fx_flush(accp + 2 * cur_b, alo, ahi);
+                            alo = ahi = 0;
+                            cur_b = b;
+                        }
+                        fx_add_f64(alo, ahi, w * hs);
+                    }
+                }
+            }
+        }
+        if (cur_b >= 0 && (alo | ahi)) fx_flush(accp + 2 * cur_b, alo, ahi);
+    }
+}
+
+// ------------------------------------------------------- per-event reweight
+template <int PREC>
+__global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
+    const SampleDev &sd = r.s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (PREC == kFP32) {
+        const float *pc = r.pc32 + (int64_t)r.point * C32_STRIDE;
+        Pt32 c;
+        load_pt32(pc, c);
+        Ch32 h;
+        int cur_ch = -1;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sd.n; i += stride) {
+            const float E = sd.e_true[i];
+            const int ch = sd.chan[i];
+            if (ch != cur_ch) {
+                cur_ch = ch;
+                load_ch32(pc, ch, h);
+            }
+            const float A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
+            const float r0 = __frcp_rn(E);
+            const float rl = r0 * fmaf(-E, r0, 1.0f);
+            float th = sd.rev_hi * r0;
+            float tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
+            const float sum = th + tl;
+            tl = tl - (sum - th);
+            th = sum;
+            const float P = prob_fp32(c, h, A, th, tl);
+            const float w = P * sd.w_mc[i];
+            const int32_t o = sd.perm[i];
+            if (r.out_prob) r.out_prob[o] = (double)P;
+            if (r.out_weight) r.out_weight[o] = (double)w * r.norm;
+        }
+    } else {
+        const double *pc = r.pc64 + (int64_t)r.point * C64_STRIDE;
+        Pt64 c;
+        load_pt64(pc, c);
+        Ch64 h;
+        int cur_ch = -1;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sd.n; i += stride) {
+            const float E = sd.e_true[i];
+            const int ch = sd.chan[i];
+            if (ch != cur_ch) {
+                cur_ch = ch;
+                load_ch64(pc, ch, h);
+            }
+            const double Ad = sd.kA_rhoye * (double)E;
+            const double P = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+            const double w = P * (double)sd.w_mc[i];
+            const int32_t o = sd.perm[i];
+            if (r.out_prob) r.out_prob[o] = P;
+            if (r.out_weight) r.out_weight[o] = w * r.norm;
+        }
+    }
+}
+
+}  // namespace osc

@@ -1,0 +1,63 @@
+// Constants and finalize kernels, and the precision dispatch of the launch helpers.
+#include "osc_kernels.cuh"
+
+namespace osc {
+
+__global__ void k_point_consts(const osc_point *pts, int n, float *pc32, double *pc64) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    point_consts_one(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
+}
+
+// ---------------------------------------------------------------- finalize
+__global__ void k_final(const FinalParams f) {
+    const int64_t n = f.n_hist * (int64_t)f.nbins;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long lo = f.acc[2 * i], hi = f.acc[2 * i + 1];
+        f.acc[2 * i] = 0ull;
+        f.acc[2 * i + 1] = 0ull;
+        const int64_t h = i / f.nbins;
+        const double v = (double)(long long)hi * f.hmeta[3 * h] + (double)lo * f.hmeta[3 * h + 1];
+        f.out[i] = v * f.pc64[(int64_t)f.hmeta[3 * h + 2] * C64_STRIDE + C64_NORM];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
+}
+
+const void *hist_kernel_fn_fp32(int pt);
+const void *hist_kernel_fn_fp64(int pt);
+cudaError_t launch_hist_fp32(int pt, const HistParams &p, int grid, cudaStream_t st);
+cudaError_t launch_hist_fp64(int pt, const HistParams &p, int grid, cudaStream_t st);
+cudaError_t launch_reweight_fp32(const ReweightParams &p, cudaStream_t st);
+cudaError_t launch_reweight_fp64(const ReweightParams &p, cudaStream_t st);
+
+int hist_threads() { return kNT; }
+
+const void *hist_kernel_fn(int prec, int pt) {
+    return prec == kFP32 ? hist_kernel_fn_fp32(pt) : hist_kernel_fn_fp64(pt);
+}
+
+const void *final_kernel_fn() { return (const void *)k_final; }
+
+cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
+    k_point_consts<<<(n + 127) / 128, 128, 0, st>>>(d_pts, n, pc32, pc64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st) {
+    return prec == kFP32 ? launch_hist_fp32(pt, p, grid, st) : launch_hist_fp64(pt, p, grid, st);
+}
+
+cudaError_t launch_final(const FinalParams &p, cudaStream_t st) {
+    int64_t n = p.n_hist * (int64_t)p.nbins;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_final<<<(int)blocks, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st) {
+    return prec == kFP32 ? launch_reweight_fp32(p, st) : launch_reweight_fp64(p, st);
+}
+
+}  // namespace osc

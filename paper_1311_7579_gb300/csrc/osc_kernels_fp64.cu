@@ -1,0 +1,36 @@
+// Histogram and reweight kernel instantiations for one precision (fp64).
+#include "osc_kernels.cuh"
+
+namespace osc {
+
+const void *hist_kernel_fn_fp64(int pt) {
+    switch (pt) {
+        case 1: return (const void *)k_hist<kFP64, 1>;
+        case 4: return (const void *)k_hist<kFP64, 4>;
+        case 16: return (const void *)k_hist<kFP64, 16>;
+        case 64: return (const void *)k_hist<kFP64, 64>;
+        case 256: return (const void *)k_hist<kFP64, 256>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_hist_fp64(int pt, const HistParams &p, int grid, cudaStream_t st) {
+    switch (pt) {
+        case 1: k_hist<kFP64, 1><<<grid, kNT, 0, st>>>(p); break;
+        case 4: k_hist<kFP64, 4><<<grid, kNT, 0, st>>>(p); break;
+        case 16: k_hist<kFP64, 16><<<grid, kNT, 0, st>>>(p); break;
+        case 64: k_hist<kFP64, 64><<<grid, kNT, 0, st>>>(p); break;
+        case 256: k_hist<kFP64, 256><<<grid, kNT, 0, st>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reweight_fp64(const ReweightParams &p, cudaStream_t st) {
+    int64_t blocks = (p.s.n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_reweight<kFP64><<<(int)blocks, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace osc

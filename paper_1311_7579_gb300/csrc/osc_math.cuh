@@ -1,0 +1,167 @@
+// osc_math.cuh -- per (event, parameter point) arithmetic of the constant-density
+// three-flavour oscillation probability (Sec. 1.1: Eq. (1) and the matter term;
+// Sec. 2.1: parameter-only components computed once per parameter set).
+//
+// Both precisions evaluate the same closed form.  With M = H0 + A Pe the
+// flavour-basis Hamiltonian (H0 = U diag(0, dm21, dm31) U^dagger, Pe = e e^T),
+// the eigenvalues lambda_l of M are the roots of its characteristic cubic
+//   lambda^3 - (T0 + A) lambda^2 + (c1_0 + A s_mt) lambda - A m_ee = 0
+// (T0 = tr H0, c1_0 = dm21 dm31, s_mt = H0_mumu + H0_tautau, m_ee the mu-tau
+// minor; det H0 = 0), and the propagator is Sylvester's formula
+//   S = sum_l exp(-i tau lambda_l) prod_{j != l} (M - lambda_j) / (lambda_l - lambda_j),
+// tau = c_L L / E, whose (beta, alpha) entry needs only (M)_{beta alpha} and
+// (M^2)_{beta alpha}:  N_l = (M^2)_ba - sigma_l M_ba + pi_l delta_ba with
+// sigma_l = lambda_j + lambda_k and pi_l = lambda_j lambda_k.
+//
+// FP64 path: the depressed cubic is solved by Viete's trigonometric form,
+// polished by one Newton step, and everything else is FP64.
+//
+// FP32 path (GB300 has ~1/64 of its FP32 rate in FP64): each eigenvalue is
+// written as its vacuum value plus a matter shift, lambda_l = d_l + delta_l.
+// By the rank-one secular structure of M = U (D + A u u^dagger) U^dagger,
+// delta_l solves the shifted cubic
+//   delta^3 + (a_j + a_k - A) delta^2 + (a_j a_k - A W_l) delta - A z_l a_j a_k = 0,
+// a_j = d_l - d_j, z = |U_e|^2, W_l = z_l (a_j + a_k) + z_j a_k + z_k a_j,
+// whose coefficients carry only FP32 rounding relative to delta itself, so one
+// FP32 Newton step from a trigonometric FP32 seed gives delta to FP32 relative
+// accuracy.  tau delta_l <= tau |A| = c_L L k_A rho Y_e is energy independent
+// (<= 0.72 rad for the workloads here), so those parts of the phases are
+// accurate in FP32; the large vacuum parts tau (d_l - d_0) are formed in
+// float-float and reduced exactly in revolutions.
+#pragma once
+
+#include <stdint.h>
+
+namespace osc {
+
+// ------------------------------------------------------------------ FP32 path
+struct Pt32 {
+    float p0, p1, q0, q1, q2, T0, c10, smt;
+    float d0, d1, d2, g01, g02, g12;
+    float v1h, v1l, v2h, v2l;
+    float S0, PI0, W0, E0, S1, PI1, W1, E1;
+};
+struct Ch32 {
+    float Xr, Xi, Yr, Yi, Zr, Zi;
+    float ee;    // 1 for the e -> e channel, else 0
+    float diag;  // 1 for alpha == beta, else 0
+};
+
+__device__ __forceinline__ float shifted_newton(float dl, float A, float S, float PI, float W, float E) {
+    // one Newton step on g(delta) = delta^3 + b delta^2 + c delta - e
+    const float b = S - A;
+    const float c = fmaf(-A, W, PI);
+    const float e = A * E;
+    const float g = fmaf(fmaf(dl + b, dl, c), dl, -e);
+    const float gp = fmaf(fmaf(3.0f, dl, b + b), dl, c);
+    return dl - __fdividef(g, gp);
+}
+
+// Phase of root l relative to root 0 in revolutions, reduced to about [-0.62, 0.62]:
+// th + tl = c_L L / (2 pi E) (float-float), vh + vl = d_l - d_0, dd = delta_l - delta_0.
+__device__ __forceinline__ float phase_rev(float th, float tl, float vh, float vl, float dd) {
+    const float ph = th * vh;
+    const float e1 = fmaf(th, vh, -ph);
+    const float e2 = fmaf(th, vl, tl * vh);
+    const float fr = ph - rintf(ph);  // exact
+    return fr + fmaf(th, dd, e1 + e2);
+}
+
+// P(alpha -> beta) for one event and one point.  A: signed matter term [eV^2];
+// (th, tl): c_L L / (2 pi E_true) as float-float.
+__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl) {
+    // trigonometric seed of the three sorted roots (depressed cubic in FP32)
+    const float p = fmaf(fmaf(A, -1.0f / 3.0f, c.p1), A, c.p0);
+    const float q = fmaf(fmaf(fmaf(A, -2.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
+    const float mp3 = fmaxf(p * (-1.0f / 3.0f), 1e-30f);
+    const float ir = rsqrtf(mp3);
+    const float r = mp3 * ir;
+    float cth = -0.5f * q * (ir * ir * ir);
+    cth = fminf(fmaxf(cth, -1.0f), 1.0f);
+    const float th3 = acosf(cth) * (1.0f / 3.0f);
+    float sn, cs;
+    __sincosf(th3, &sn, &cs);
+    const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;
+    const float t3 = (c.T0 + A) * (1.0f / 3.0f);
+    const float l0 = t3 - rc - rsn;  // smallest root
+    const float l1 = t3 - rc + rsn;  // middle root
+    // matter shifts from the vacuum eigenvalues: Newton on the shifted cubics
+    const float dl0 = shifted_newton(l0 - c.d0, A, c.S0, c.PI0, c.W0, c.E0);
+    const float dl1 = shifted_newton(l1 - c.d1, A, c.S1, c.PI1, c.W1, c.E1);
+    const float dl2 = A - dl0 - dl1;  // trace: sum of shifts = A
+    const float L0 = c.d0 + dl0, L1 = c.d1 + dl1, L2 = c.d2 + dl2;
+    const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
+    const float inv = __fdividef(1.0f, g01 * g02 * g12);
+    const float iD0 = g12 * inv, iD1 = -g02 * inv, iD2 = g01 * inv;
+    // Sylvester numerators
+    const float TA = c.T0 + A;
+    const float c1 = fmaf(A, c.smt, c.c10);
+    const float Kr = fmaf(A, fmaf(A, h.ee, h.Zr), h.Yr), Ki = fmaf(A, h.Zi, h.Yi);
+    const float Gr = fmaf(A, h.ee, h.Xr), Gi = h.Xi;
+    float sg, pp;
+    sg = TA - L0; pp = fmaf(-L0, sg, c1);
+    const float C0r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD0, C0i = fmaf(-sg, Gi, Ki) * iD0;
+    sg = TA - L1; pp = fmaf(-L1, sg, c1);
+    const float C1r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD1, C1i = fmaf(-sg, Gi, Ki) * iD1;
+    sg = TA - L2; pp = fmaf(-L2, sg, c1);
+    const float C2r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD2, C2i = fmaf(-sg, Gi, Ki) * iD2;
+    // phases relative to root 0
+    const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dl1 - dl0);
+    const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dl2 - dl0);
+    float s1, k1, s2, k2;
+    __sincosf(6.28318530717958647692f * f1, &s1, &k1);
+    __sincosf(6.28318530717958647692f * f2, &s2, &k2);
+    // S = C0 + C1 e^{-i phi1} + C2 e^{-i phi2}
+    const float Sr = C0r + fmaf(C1r, k1, C1i * s1) + fmaf(C2r, k2, C2i * s2);
+    const float Si = C0i + fmaf(C1i, k1, -C1r * s1) + fmaf(C2i, k2, -C2r * s2);
+    return fmaf(Sr, Sr, Si * Si);
+}
+
+// ------------------------------------------------------------------ FP64 path
+struct Pt64 {
+    double p0, p1, q0, q1, q2, T0, c10, smt;
+};
+struct Ch64 {
+    double Xr, Xi, Yr, Yi, Zr, Zi, ee, diag;
+};
+
+// P(alpha -> beta); A signed matter term [eV^2], tau = c_L L / E_true.
+__device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double A, double tau) {
+    const double p = fma(fma(A, -1.0 / 3.0, c.p1), A, c.p0);
+    const double q = fma(fma(fma(A, -2.0 / 27.0, c.q2), A, c.q1), A, c.q0);
+    const double mp3 = fmax(-p / 3.0, 1e-300);
+    const double r = sqrt(mp3);
+    double cth = (-0.5 * q) / (mp3 * r);
+    cth = fmin(fmax(cth, -1.0), 1.0);
+    const double th3 = acos(cth) / 3.0;
+    double sn, cs;
+    sincos(th3, &sn, &cs);
+    const double rc = r * cs, rsn = r * sn * 1.7320508075688772935;
+    double m0 = -rc - rsn, m1 = -rc + rsn, m2 = 2.0 * rc;  // ascending roots of mu^3 + p mu + q
+    m0 -= fma(fma(m0, m0, p), m0, q) / fma(3.0 * m0, m0, p);
+    m1 -= fma(fma(m1, m1, p), m1, q) / fma(3.0 * m1, m1, p);
+    m2 -= fma(fma(m2, m2, p), m2, q) / fma(3.0 * m2, m2, p);
+    const double t3 = (c.T0 + A) / 3.0;
+    const double L0 = m0 + t3, L1 = m1 + t3, L2 = m2 + t3;
+    const double g01 = m0 - m1, g02 = m0 - m2, g12 = m1 - m2;
+    const double iD0 = 1.0 / (g01 * g02), iD1 = -1.0 / (g01 * g12), iD2 = 1.0 / (g02 * g12);
+    const double TA = c.T0 + A;
+    const double c1 = fma(A, c.smt, c.c10);
+    const double Kr = fma(A, fma(A, h.ee, h.Zr), h.Yr), Ki = fma(A, h.Zi, h.Yi);
+    const double Gr = fma(A, h.ee, h.Xr), Gi = h.Xi;
+    double sg, pp;
+    sg = TA - L0; pp = c1 - L0 * sg;
+    const double C0r = (Kr - sg * Gr + pp * h.diag) * iD0, C0i = (Ki - sg * Gi) * iD0;
+    sg = TA - L1; pp = c1 - L1 * sg;
+    const double C1r = (Kr - sg * Gr + pp * h.diag) * iD1, C1i = (Ki - sg * Gi) * iD1;
+    sg = TA - L2; pp = c1 - L2 * sg;
+    const double C2r = (Kr - sg * Gr + pp * h.diag) * iD2, C2i = (Ki - sg * Gi) * iD2;
+    double s1, k1, s2, k2;
+    sincos(tau * (m1 - m0), &s1, &k1);
+    sincos(tau * (m2 - m0), &s2, &k2);
+    const double Sr = C0r + C1r * k1 + C1i * s1 + C2r * k2 + C2i * s2;
+    const double Si = C0i + C1i * k1 - C1r * s1 + C2i * k2 - C2r * s2;
+    return Sr * Sr + Si * Si;
+}
+
+}  // namespace osc

@@ -1,0 +1,77 @@
+"""C-ABI contract checks that need no GPU: the library builds for sm_103a, loads,
+and exports every entry point include/osc.h declares; calls fail cleanly (a
+status, never a crash) without a device or with null arguments."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1311_7579_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_entry_points():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", hdr)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(osc_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (osc_\w+)", out))
+    declared = _declared_entry_points()
+    assert declared, "no declarations parsed"
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    assert sorted(set(declared)) == sorted(set(api.ENTRY_POINTS))
+    L = api.lib()
+    for n in declared:
+        assert hasattr(L, n)
+
+
+def test_build_targets_sm_103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_version_and_error_strings():
+    assert "sm_103a" in api.osc_version()
+    assert api.osc_last_error(None) == "no context"
+
+
+def test_calls_without_context_return_arg_status():
+    L = api.lib()
+    sid = ctypes.c_int32()
+    assert L.osc_load_sample(None, None, ctypes.byref(sid)) == api.OSC_E_ARG
+    assert L.osc_set_params(None, None, 1) == api.OSC_E_ARG
+    assert L.osc_reweight(None, 0, 0, 0, None, None, 0) == api.OSC_E_ARG
+    assert L.osc_histogram(None, None, 1, 0, 1, 0, 0.0, 5.0, 100, None, 0) == api.OSC_E_ARG
+    assert L.osc_sync(None) == api.OSC_E_ARG
+    assert L.osc_serve_stop(None) == api.OSC_E_ARG
+    assert L.osc_create(0, 0, None, None) == api.OSC_E_ARG
+    L.osc_destroy(None)  # no-op
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(api.OscError) as e:
+        api.osc_create(0)
+    assert e.value.status in (api.OSC_E_CUDA, api.OSC_E_ARG)
+
+
+def test_oracle_library_builds():
+    import oracle
+    oracle.build()
+    assert oracle.num_threads() >= 1

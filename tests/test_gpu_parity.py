@@ -1,0 +1,257 @@
+"""GPU-vs-oracle parity through the C ABI (needs a GB300).
+
+Tolerances (from the benchmark spec of the method's precision):
+  * FP64 path probabilities: |dP| <= 1e-12 (Sec. 2.2 validation residual ~1e-12);
+  * FP32-bulk path probabilities: |dP| <= 1e-5;
+  * histogram bins: relative 1e-9 (FP64 path against the oracle's FP64 histogram;
+    FP32-bulk path against the oracle's sum of the GPU's own returned weights,
+    which pins binning and accumulation separately from the probability);
+  * bin selection: exact (a misbinned event moves >= 1e-6 of a bin).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_7579_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+TOL_FP32 = 1e-5
+TOL_HIST = 1e-9
+LO, HI, NB = 0.0, 5.0, 100
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = api.Context(0)
+    yield c.ptr
+    c.close()
+
+
+def _rel_err(a, b):
+    den = np.maximum(np.abs(b), 1e-300)
+    return np.where((a == 0) & (b == 0), 0.0, np.abs(a - b) / den)
+
+
+def _gpu_probs(ctx, sid, point, prec, n):
+    p = np.zeros(n)
+    w = np.zeros(n)
+    api.osc_reweight(ctx, sid, point, prec, p, w)
+    return p, w
+
+
+# ------------------------------------------------------------ probabilities
+def test_table1_sample_fp64_and_fp32(ctx):
+    s = synth.table1_sample()
+    sid = api.osc_load_sample(ctx, s)
+    api.osc_set_params(ctx, synth.table1_point()[None, :])
+    po, wo = oracle.reweight(s, oracle.point_from_row(synth.table1_point()))
+    p64, w64 = _gpu_probs(ctx, sid, 0, "fp64", s["n"])
+    assert np.max(np.abs(p64 - po)) <= TOL_FP64
+    assert np.max(np.abs(w64 - wo)) <= 2 * TOL_FP64
+    p32, w32 = _gpu_probs(ctx, sid, 0, "fp32", s["n"])
+    assert np.max(np.abs(p32 - po)) <= TOL_FP32
+    api.osc_unload_sample(ctx, sid)
+
+
+@pytest.mark.parametrize("L,rho", [(295.0, 2.6), (810.0, 2.8), (1300.0, 2.85)])
+def test_all_channels_random_points(ctx, L, rho):
+    """Every (alpha, beta, nu/nubar) channel, both hierarchies, random delta,
+    E_true uniform in [0.05, 10 L/295] GeV (crosses both MSW resonances)."""
+    s = synth.all_channel_sample(60000, seed=int(L), L_km=L, rho=rho, e_hi=10 * L / 295)
+    sid = api.osc_load_sample(ctx, s)
+    pts = synth.scan_points(6, seed=int(L) + 1)
+    api.osc_set_params(ctx, pts)
+    for k in range(pts.shape[0]):
+        po, _ = oracle.reweight(s, oracle.point_from_row(pts[k]))
+        p64, _ = _gpu_probs(ctx, sid, k, "fp64", s["n"])
+        p32, _ = _gpu_probs(ctx, sid, k, "fp32", s["n"])
+        assert np.max(np.abs(p64 - po)) <= TOL_FP64, (k, np.max(np.abs(p64 - po)))
+        assert np.max(np.abs(p32 - po)) <= TOL_FP32, (k, np.max(np.abs(p32 - po)))
+    api.osc_unload_sample(ctx, sid)
+
+
+def test_validation_residual_10M(ctx, golden_dir):
+    """Sec. 2.2: 10 million energies uniform in (0.05, 30] GeV, Table 1 point:
+    FP64 GPU vs CPU residual within 1e-12."""
+    g = json.load(open(os.path.join(golden_dir, "validation_residual.json")))
+    n = g["n_energies"]
+    e = synth.validation_energies(n)
+    rng = np.random.default_rng(77)
+    s = dict(n=n, e_true=e, e_reco=e.copy(), w_mc=np.ones(n, np.float32),
+             flav_in=rng.integers(0, 3, n).astype(np.uint8), flav_out=rng.integers(0, 3, n).astype(np.uint8),
+             is_nubar=rng.integers(0, 2, n).astype(np.uint8), baseline_km=295.0, density_gcc=2.6, ye=0.5)
+    sid = api.osc_load_sample(ctx, s)
+    api.osc_set_params(ctx, synth.table1_point()[None, :])
+    po, _ = oracle.reweight(s, oracle.point_from_row(synth.table1_point()))
+    p64, _ = _gpu_probs(ctx, sid, 0, "fp64", n)
+    assert np.max(np.abs(p64 - po)) <= g["residual_fp64"]
+    p32, _ = _gpu_probs(ctx, sid, 0, "fp32", n)
+    assert np.max(np.abs(p32 - po)) <= TOL_FP32
+    api.osc_unload_sample(ctx, sid)
+
+
+# --------------------------------------------------------------- histograms
+def _check_fp64_hist(h_gpu, h_orc):
+    assert np.array_equal(h_gpu == 0, h_orc == 0)
+    assert np.max(_rel_err(h_gpu, h_orc)) <= TOL_HIST
+
+
+def test_histograms_multi_point_both_paths(ctx):
+    s = synth.table1_sample(200000, seed=11)
+    sid = api.osc_load_sample(ctx, s)
+    pts = synth.scan_points(37, seed=5)  # ragged against every tile width
+    api.osc_set_params(ctx, pts)
+    h64 = api.osc_histogram(ctx, [sid], 0, pts.shape[0], "fp64", LO, HI, NB)[0]
+    h32 = api.osc_histogram(ctx, [sid], 0, pts.shape[0], "fp32", LO, HI, NB)[0]
+    for k in range(pts.shape[0]):
+        pt = oracle.point_from_row(pts[k])
+        _, wo = oracle.reweight(s, pt)
+        ho = oracle.hist_from_weights(s["e_reco"], wo, pts[k, 6], LO, HI, NB, compensated=True)
+        _check_fp64_hist(h64[k], ho)
+        # FP32 path: accumulation and binning pinned with the GPU's own weights
+        _, w32 = _gpu_probs(ctx, sid, k, "fp32", s["n"])
+        hw = oracle.hist_from_weights(s["e_reco"], w32, pts[k, 6], LO, HI, NB, compensated=True)
+        _check_fp64_hist(h32[k], hw)
+        # and the FP32 histogram against the FP64 oracle: bounded by |dP| <= 1e-5 per event
+        wsum = oracle.hist_from_weights(s["e_reco"], s["w_mc"].astype(np.float64), pts[k, 6], LO, HI, NB)
+        assert np.all(np.abs(h32[k] - ho) <= TOL_FP32 * wsum + 1e-12)
+    api.osc_unload_sample(ctx, sid)
+
+
+def test_histogram_bitwise_independent_of_tile_shape(ctx):
+    s = synth.table1_sample(50000, seed=12)
+    sid = api.osc_load_sample(ctx, s)
+    pts = synth.scan_points(20, seed=6)
+    api.osc_set_params(ctx, pts)
+    ref = {}
+    for prec in ("fp32", "fp64"):
+        for ppb in (1, 4, 16, 64, 256):
+            for chunk in (1024, 4096, 0):
+                api.osc_set_tile(ctx, ppb, chunk)
+                h = api.osc_histogram(ctx, [sid], 0, 20, prec, LO, HI, NB)
+                if prec not in ref:
+                    ref[prec] = h.copy()
+                assert np.array_equal(h, ref[prec]), (prec, ppb, chunk)
+        h2 = api.osc_histogram(ctx, [sid], 0, 20, prec, LO, HI, NB)
+        assert np.array_equal(h2, ref[prec])
+    api.osc_set_tile(ctx, 0, 0)
+    api.osc_unload_sample(ctx, sid)
+
+
+def test_uneven_samples_one_launch(ctx):
+    sizes = (1000, 3, 1023, 1025, 20000, 77777)
+    ss = synth.uneven_samples(sizes)
+    sids = [api.osc_load_sample(ctx, s) for s in ss]
+    pts = synth.uneven_points(9, seed=8)
+    api.osc_set_params(ctx, pts)
+    for prec in ("fp64", "fp32"):
+        h = api.osc_histogram(ctx, sids, 0, 9, prec, LO, 20.0, 80)
+        for j, s in enumerate(ss):
+            for k in range(9):
+                if prec == "fp64":
+                    _, w = oracle.reweight(s, oracle.point_from_row(pts[k]))
+                else:
+                    _, w = _gpu_probs(ctx, sids[j], k, "fp32", s["n"])
+                ho = oracle.hist_from_weights(s["e_reco"], w, pts[k, 6], LO, 20.0, 80, compensated=True)
+                _check_fp64_hist(h[j, k], ho)
+    for sid in sids:
+        api.osc_unload_sample(ctx, sid)
+
+
+def test_edge_cases(ctx):
+    # one event; events outside the range; negative weights and E_reco; norm; nbins = 1; lo != 0
+    s = synth.table1_sample(5, seed=13)
+    s["e_reco"][1] = -0.3
+    s["e_reco"][2] = 7.0
+    s["w_mc"][3] = -1.25
+    sid = api.osc_load_sample(ctx, s)
+    row = synth.table1_point().copy()
+    row[7] = 2.5
+    pts = np.stack([row, synth.table1_point()])
+    api.osc_set_params(ctx, pts)
+    for prec in ("fp64", "fp32"):
+        for lo, hi, nb in ((0.0, 5.0, 100), (0.1, 1.7, 1), (-1.0, 2.0, 7)):
+            h = api.osc_histogram(ctx, [sid], 0, 2, prec, lo, hi, nb)[0]
+            for k in range(2):
+                _, w = _gpu_probs(ctx, sid, k, prec, s["n"])
+                if prec == "fp64":
+                    _, wo = oracle.reweight(s, oracle.point_from_row(pts[k]))
+                    assert np.max(np.abs(w - wo)) <= 3 * TOL_FP64
+                ho = oracle.hist_from_weights(s["e_reco"], w, pts[k, 6], lo, hi, nb)
+                assert np.max(np.abs(h[k] - ho)) <= 1e-12 * max(1.0, np.max(np.abs(ho)))
+    one = synth.table1_sample(1, seed=14)
+    sid1 = api.osc_load_sample(ctx, one)
+    h = api.osc_histogram(ctx, [sid1], 1, 1, "fp64", LO, HI, NB)[0, 0]
+    _, wo = oracle.reweight(one, oracle.point_from_row(pts[1]))
+    assert np.max(np.abs(h - oracle.hist_from_weights(one["e_reco"], wo, 1.0, LO, HI, NB))) <= 1e-12
+    api.osc_unload_sample(ctx, sid)
+    api.osc_unload_sample(ctx, sid1)
+
+
+def test_invalid_input_rejected_before_launch(ctx):
+    s = synth.table1_sample(100, seed=15)
+    bad = dict(s, e_true=s["e_true"].copy())
+    bad["e_true"][7] = 0.0
+    with pytest.raises(api.OscError) as e:
+        api.osc_load_sample(ctx, bad)
+    assert e.value.status == api.OSC_E_RANGE
+    bad = dict(s, flav_out=s["flav_out"].copy())
+    bad["flav_out"][3] = 3
+    with pytest.raises(api.OscError):
+        api.osc_load_sample(ctx, bad)
+    for field, val in ((1, 0.0), (3, 0.0), (4, 5e-5), (6, 0.0), (0, float("nan"))):
+        row = synth.table1_point().copy()
+        row[field] = val
+        with pytest.raises(api.OscError) as e:
+            api.osc_set_params(ctx, row[None, :])
+        assert e.value.status == api.OSC_E_RANGE
+    sid = api.osc_load_sample(ctx, s)
+    api.osc_set_params(ctx, synth.table1_point()[None, :])
+    for args in (([sid], 0, 2), ([sid + 999], 0, 1), ([sid], -1, 1)):
+        with pytest.raises(api.OscError) as e:
+            api.osc_histogram(ctx, args[0], args[1], args[2], "fp64", LO, HI, NB)
+        assert e.value.status == api.OSC_E_ARG
+    with pytest.raises(api.OscError):
+        api.osc_histogram(ctx, [sid], 0, 1, "fp64", 5.0, 5.0, NB)
+    with pytest.raises(api.OscError):
+        api.osc_histogram(ctx, [sid], 0, 1, "fp64", LO, HI, 0)
+    # the context is still usable afterwards
+    h = api.osc_histogram(ctx, [sid], 0, 1, "fp64", LO, HI, NB)
+    assert np.isfinite(h).all()
+    api.osc_unload_sample(ctx, sid)
+
+
+def test_workspace_cap_enforced():
+    with api.Context(0, workspace_cap_bytes=1 << 20) as c:
+        s = synth.table1_sample(200000, seed=16)
+        with pytest.raises(api.OscError) as e:
+            api.osc_load_sample(c.ptr, s)
+        assert e.value.status == api.OSC_E_NOMEM
+        small = synth.table1_sample(1000, seed=16)
+        sid = api.osc_load_sample(c.ptr, small)
+        api.osc_set_params(c.ptr, synth.table1_point()[None, :])
+        h = api.osc_histogram(c.ptr, [sid], 0, 1, "fp32", LO, HI, NB)
+        assert h.sum() > 0
+
+
+def test_device_outputs_match_host_outputs(ctx):
+    torch = pytest.importorskip("torch")
+    s = synth.table1_sample(30000, seed=17)
+    sid = api.osc_load_sample(ctx, s)
+    pts = synth.scan_points(5, seed=9)
+    api.osc_set_params(ctx, pts)
+    hh = api.osc_histogram(ctx, [sid], 0, 5, "fp32", LO, HI, NB)
+    hd = torch.zeros((1, 5, NB), dtype=torch.float64, device="cuda")
+    api.osc_histogram(ctx, [sid], 0, 5, "fp32", LO, HI, NB, out=hd)
+    api.osc_sync(ctx)
+    assert np.array_equal(hd.cpu().numpy(), hh)
+    pd = torch.zeros(s["n"], dtype=torch.float64, device="cuda")
+    api.osc_reweight(ctx, sid, 2, "fp64", out_prob=pd)
+    ph, _ = _gpu_probs(ctx, sid, 2, "fp64", s["n"])
+    assert np.array_equal(pd.cpu().numpy(), ph)
+    api.osc_unload_sample(ctx, sid)
