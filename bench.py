@@ -1,0 +1,385 @@
+"""Benchmark: event-by-event oscillation reweighting on GB300.
+
+Workload (one step = one pass of the whole hot path over one batch): the
+precision-study configuration -- 10M events shaped like the paper's beam MC
+(Gamma(3, 0.25 GeV) true energies, 295 km, 2.6 g/cm^3, Y_e 0.5, nu_mu -> nu_mu
+90 % / nu_mu -> nu_e 10 %, 20 % antineutrinos) at the Table 1 parameter point:
+set the point (H2D of the point + the FP64 constants kernel), then the fused
+probability / weight / bin / histogram kernel and the finalize kernel into a
+100-bin E_reco histogram over [0, 5) GeV.  FP32-bulk path; the all-FP64 path is
+timed on the same workload as the GPU baseline to beat.
+
+Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
+launching stream, with a 256 MB write between steps to flush the 129 MB L2
+(outside the events); barrier + synchronize around the timed region; the max
+over ranks.  Under torchrun every rank reweights its own independent sample
+(weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0
+only), on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "event-weights/s FP32-bulk vs all-FP64 at |dP|<=1e-5; p50/p99 reweight latency"
+UNIT = "event-weights/s"
+N_EVENTS = 10_000_000
+NBINS, LO, HI = 100, 0.0, 5.0
+FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 operations per (event, point) of the FP32-bulk path, counted
+# from osc_math.cuh / osc_kernels.cuh (FMA = 2, add/mul = 1; transcendental and
+# reciprocal calls counted separately as SFU operations, conversions not counted).
+FP32_FLOP_PER_EVPT = 173
+SFU_PER_EVPT = 11
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")] + [time.perf_counter()])
+
+    def window(self, t0, t1):
+        inside = [r for r in self.rows if t0 <= r[-1] <= t1]
+        self.rows = inside if inside else self.rows
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def cpu_baseline_leg(sample, point_row, gpu_p32, gpu_p64, n_sample):
+    """FP64 oracle on the host cores over the first n_sample events: throughput,
+    and the |dP| of both GPU paths on that subsample (precision study)."""
+    import oracle
+    pt = oracle.point_from_row(point_row)
+    sub = {k: (v[:n_sample] if isinstance(v, np.ndarray) else v) for k, v in sample.items()}
+    sub["n"] = n_sample
+    oracle.reweight(dict(sub, n=min(1000, n_sample)), pt)  # warm (thread pool, pages)
+    t0 = time.perf_counter()
+    po, wo = oracle.reweight(sub, pt)
+    h = oracle.hist_from_weights(sub["e_reco"], wo, point_row[6], LO, HI, NBINS)
+    dt = time.perf_counter() - t0
+    d32 = np.abs(gpu_p32[:n_sample] - po)
+    d64 = np.abs(gpu_p64[:n_sample] - po)
+    cpu = {"value": n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "first %d events of the 10M-event sample, Table 1 point: FP64 Jacobi oracle reweight + "
+                     "100-bin histogram, %.2f s wall" % (n_sample, dt)}
+    prec = {"subsample_events": n_sample, "fp32_max_dP": float(d32.max()), "fp32_rms_dP": float(np.sqrt(np.mean(d32 ** 2))),
+            "fp64_max_dP": float(d64.max()), "fp64_rms_dP": float(np.sqrt(np.mean(d64 ** 2)))}
+    return cpu, prec, h
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1311_7579_gb300 import synth
+    s = synth.precision_sample(N_EVENTS, seed=1)
+    pt = oracle.point_from_row(synth.table1_point())
+    # bounded per-step sample so that W + K steps finish in a few minutes
+    per_step = int(max(1024, min(N_EVENTS, 4_000_000 // max(1, args.steps + args.warmup))))
+    sub = {k: (v[:per_step] if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+    sub["n"] = per_step
+    for _ in range(args.warmup):
+        oracle.histogram(sub, [synth.table1_point()], LO, HI, NBINS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.histogram(sub, [synth.table1_point()], LO, HI, NBINS)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "precision study: 10M events x 1 point (Table 1), per-step bounded sample of "
+                                   "%d events" % per_step, "events": N_EVENTS, "points": 1, "nbins": NBINS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d events per step of the 10M-event sample" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1311_7579_gb300 import api, synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # a dedicated (non-legacy-default) stream shared by torch and the library, so
+    # that torch's CUDA events and flush writes order with the library's kernels
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(local, cuda_stream=stream.cuda_stream)
+    c = ctx.ptr
+
+    sample = synth.precision_sample(N_EVENTS, seed=1 + 1000 * rank)
+    sid = api.osc_load_sample(c, sample)
+    point = synth.table1_point()[None, :]
+    out = torch.zeros((1, 1, NBINS), dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(prec):
+        api.osc_set_params(c, point)
+        api.osc_histogram(c, [sid], 0, 1, prec, LO, HI, NBINS, out=out)
+
+    def timed(prec, k, w, count_launches=False):
+        for _ in range(w):
+            step(prec)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        api.osc_timing_totals(c)  # reset
+        api.osc_enable_timing(c, True)
+        n0 = api.osc_launch_count(c)
+        for i in range(k):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(prec)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        n1 = api.osc_launch_count(c)
+        counts, sums = api.osc_timing_totals(c)
+        api.osc_enable_timing(c, False)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        return ms, counts, sums, n1 - n0
+
+    with ClockSampler(local) as clk:
+        time.sleep(1.0)  # let nvidia-smi start sampling before the timed region
+        t_clk0 = time.perf_counter()
+        ms32, counts, sums, launches = timed("fp32", args.steps, args.warmup)
+        t_clk1 = time.perf_counter()
+    clk.window(t_clk0, t_clk1)
+    clocks = clk.summary()
+    k64 = max(3, min(args.steps, 40))
+    ms64, c64, s64, _ = timed("fp64", k64, max(3, min(args.warmup, 5)))
+
+    tot32 = float(ms32.sum())
+    tot64 = float(ms64.sum())
+    if ws > 1:
+        t = torch.tensor([tot32, tot64], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot32, tot64 = float(t[0]), float(t[1])
+    value = ws * N_EVENTS * args.steps / (tot32 * 1e-3)
+    fp64_value = ws * N_EVENTS * k64 / (tot64 * 1e-3)
+    k_hist_ms = sums[1] / max(1, counts[1])
+
+    # end-to-end through the public API with host buffers: pinned point in, histogram out
+    pin_pt = torch.from_numpy(point.copy()).pin_memory()
+    host_out = torch.zeros((1, 1, NBINS), dtype=torch.float64).pin_memory()
+    pin_np = pin_pt.numpy()
+    out_np = host_out.numpy()
+    for _ in range(3):
+        api.osc_set_params(c, pin_np)
+        api.osc_histogram(c, [sid], 0, 1, "fp32", LO, HI, NBINS, out=out_np)
+    lat = []
+    k_e2e = args.steps
+    for i in range(k_e2e):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.osc_set_params(c, pin_np)
+        api.osc_histogram(c, [sid], 0, 1, "fp32", LO, HI, NBINS, out=out_np)
+        lat.append(time.perf_counter() - t0)
+    lat = np.array(lat)
+    e2e_tot = float(lat.sum())
+    if ws > 1:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t[0])
+    e2e_value = ws * N_EVENTS * k_e2e / e2e_tot
+
+    result = None
+    if rank == 0:
+        peaks, src = _measured_peaks()
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
+        achieved = FP32_FLOP_PER_EVPT * N_EVENTS / (k_hist_ms * 1e-3) / 1e12
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "k_hist_fp32_traffic.json")
+        if os.path.exists(tfile):
+            traffic = json.load(open(tfile)).get("bytes_per_launch_precision_10M")
+        # precision study + CPU baseline (rank 0, N = 1 semantics: its own sample)
+        p32 = np.zeros(N_EVENTS)
+        p64 = np.zeros(N_EVENTS)
+        api.osc_reweight(c, sid, 0, "fp32", out_prob=p32)
+        api.osc_reweight(c, sid, 0, "fp64", out_prob=p64)
+        cpu, prec_study, h_orc = (None, None, None)
+        if not args.no_cpu_baseline:
+            cpu, prec_study, h_orc = cpu_baseline_leg(sample, point[0], p32, p64, args.cpu_events)
+        h32 = api.osc_histogram(c, [sid], 0, 1, "fp32", LO, HI, NBINS)[0, 0]
+        h64 = api.osc_histogram(c, [sid], 0, 1, "fp64", LO, HI, NBINS)[0, 0]
+        if prec_study is not None:
+            # bin-wise relative error of the full-sample histograms, FP32 vs FP64 GPU path
+            nz = h64 != 0
+            prec_study["fp32_vs_fp64_hist_max_rel"] = float(np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": "precision study: 10M events x 1 point (Table 1), FP32-bulk, step = "
+                                   "set_params + histogram", "events": N_EVENTS, "points": 1, "nbins": NBINS,
+                       "baseline_km": 295.0, "density_gcc": 2.6, "ye": 0.5,
+                       "l2": "flushed between steps (256 MB write, outside the timed events)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "fp64_value": fp64_value, "fp32_over_fp64": value / fp64_value,
+            "latency_us": {"p50": float(np.percentile(lat, 50) * 1e6), "p99": float(np.percentile(lat, 99) * 1e6),
+                           "device_p50": float(np.percentile(ms32, 50) * 1e3),
+                           "device_p99": float(np.percentile(ms32, 99) * 1e3)},
+            "kernel_ms": {"hist_fp32": k_hist_ms, "final": sums[2] / max(1, counts[2]),
+                          "const": sums[0] / max(1, counts[0]), "hist_fp64": s64[1] / max(1, c64[1])},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": traffic,
+                         "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
+                                        % (n_sm, sm_mhz, src),
+                         "flop_per_evpt": FP32_FLOP_PER_EVPT,
+                         "hbm_gbs_event_stream": 13.0 * N_EVENTS / (k_hist_ms * 1e-3) / 1e9,
+                         "hbm_peak_gbs": peaks.get("hbm_gbs")},
+            "cpu_baseline": cpu,
+            "precision": prec_study,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64, "d2h_bytes_per_step": 8 * NBINS},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """Small fixed case for ncu captures: --events events of the beam-shaped
+    sample x --points scan points, --launches histogram launches with the given
+    points-per-block tile (0 = autotuned) and precision."""
+    import torch
+
+    from paper_1311_7579_gb300 import api, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, cuda_stream=stream.cuda_stream)
+    c = ctx.ptr
+    s = synth.precision_sample(args.events, seed=1)
+    sid = api.osc_load_sample(c, s)
+    pts = synth.table1_point()[None, :] if args.points == 1 else synth.scan_points(args.points)
+    api.osc_set_params(c, pts)
+    api.osc_set_tile(c, args.tile, 0)
+    out = torch.zeros((1, args.points, NBINS), dtype=torch.float64, device="cuda")
+    for _ in range(args.launches):
+        api.osc_histogram(c, [sid], 0, args.points, args.prec, LO, HI, NBINS, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": {"events": args.events, "points": args.points, "prec": args.prec,
+                                       "tile": args.tile, "launches": args.launches,
+                                       "checksum": float(out.sum())}}))
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-events", type=int, default=N_EVENTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="run the small ncu profiling case and exit")
+    ap.add_argument("--events", type=int, default=2_000_000)
+    ap.add_argument("--points", type=int, default=1)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--launches", type=int, default=2)
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

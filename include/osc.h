@@ -140,15 +140,22 @@ osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samp
                          double hi, int32_t nbins, double *out, int out_on_device);
 
 /* Launch-shape control.  points_per_block in {1, 4, 16, 64, 256}, or 0 to let
- * the autotuner choose per workload class (default).  Results never depend on it. */
+ * the autotuner choose per workload class (default); events_per_item a positive
+ * multiple of 64, or 0 for the default.  Results never depend on either. */
 osc_status osc_set_tile(osc_ctx *ctx, int32_t points_per_block, int32_t events_per_item);
 
-/* Enable (1) / disable (0) CUDA-event timing of each kernel; osc_last_timing
- * then reports the durations (ms) of the last constants, histogram and
- * finalize kernels (negative when not measured). */
+/* Enable (1) / disable (0) CUDA-event timing of each kernel.  Events are
+ * recorded on the context stream around every constants, histogram and
+ * finalize kernel without any host synchronisation (launches then bypass the
+ * CUDA graph).  osc_last_timing waits for the recorded events and reports the
+ * durations (ms) of the most recent kernel of each kind (negative when none);
+ * osc_timing_totals waits, returns the launch counts and summed durations of
+ * each kind since the last totals call (index 0 constants, 1 histogram,
+ * 2 finalize), and resets them. */
 osc_status osc_enable_timing(osc_ctx *ctx, int enable);
-osc_status osc_last_timing(const osc_ctx *ctx, double *k_const_ms, double *k_hist_ms,
+osc_status osc_last_timing(osc_ctx *ctx, double *k_const_ms, double *k_hist_ms,
                            double *k_final_ms);
+osc_status osc_timing_totals(osc_ctx *ctx, int64_t counts[3], double sums_ms[3]);
 
 /* Number of kernels this context has launched so far (graph replays count
  * each kernel node). */

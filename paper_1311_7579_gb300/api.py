@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": OSC_FP64, "fp32": OSC_FP32_BULK, OSC_FP64: OSC_FP64, OSC_F
 ENTRY_POINTS = [
     "osc_version", "osc_create", "osc_destroy", "osc_last_error", "osc_load_sample", "osc_unload_sample",
     "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
-    "osc_last_timing", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
+    "osc_last_timing", "osc_timing_totals", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
     "osc_serve_stop",
 ]
 
@@ -58,36 +58,41 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
-            L = ctypes.CDLL(path)
-            vp, i32, i64, d, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
-            sig = {
-                "osc_version": (ctypes.c_char_p, []),
-                "osc_create": (st, [ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
-                "osc_destroy": (None, [vp]),
-                "osc_last_error": (ctypes.c_char_p, [vp]),
-                "osc_load_sample": (st, [vp, ctypes.POINTER(OscSampleDesc), ctypes.POINTER(i32)]),
-                "osc_unload_sample": (st, [vp, i32]),
-                "osc_set_params": (st, [vp, ctypes.POINTER(OscPoint), i32]),
-                "osc_reweight": (st, [vp, i32, i32, ctypes.c_int, vp, vp, ctypes.c_int]),
-                "osc_histogram": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
-                                       ctypes.c_int]),
-                "osc_set_tile": (st, [vp, i32, i32]),
-                "osc_enable_timing": (st, [vp, ctypes.c_int]),
-                "osc_last_timing": (st, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
-                "osc_launch_count": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
-                "osc_sync": (st, [vp]),
-                "osc_serve_start": (st, [vp, i32, d, d, i32]),
-                "osc_submit": (st, [vp, i32, ctypes.POINTER(OscPoint), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
-                "osc_wait": (st, [vp, ctypes.c_uint64, vp, i32, ctypes.POINTER(d)]),
-                "osc_serve_stop": (st, [vp]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = load_library(_build.build())
     return _lib
+
+
+def load_library(path):
+    """Load a built copy of the library at ``path`` and declare its C signatures."""
+    L = ctypes.CDLL(path)
+    vp, i32, i64, d, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    sig = {
+        "osc_version": (ctypes.c_char_p, []),
+        "osc_create": (st, [ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+        "osc_destroy": (None, [vp]),
+        "osc_last_error": (ctypes.c_char_p, [vp]),
+        "osc_load_sample": (st, [vp, ctypes.POINTER(OscSampleDesc), ctypes.POINTER(i32)]),
+        "osc_unload_sample": (st, [vp, i32]),
+        "osc_set_params": (st, [vp, ctypes.POINTER(OscPoint), i32]),
+        "osc_reweight": (st, [vp, i32, i32, ctypes.c_int, vp, vp, ctypes.c_int]),
+        "osc_histogram": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
+                               ctypes.c_int]),
+        "osc_set_tile": (st, [vp, i32, i32]),
+        "osc_enable_timing": (st, [vp, ctypes.c_int]),
+        "osc_last_timing": (st, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
+        "osc_timing_totals": (st, [vp, ctypes.POINTER(i64), ctypes.POINTER(d)]),
+        "osc_launch_count": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "osc_sync": (st, [vp]),
+        "osc_serve_start": (st, [vp, i32, d, d, i32]),
+        "osc_submit": (st, [vp, i32, ctypes.POINTER(OscPoint), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+        "osc_wait": (st, [vp, ctypes.c_uint64, vp, i32, ctypes.POINTER(d)]),
+        "osc_serve_stop": (st, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def _check(ctx, status):
@@ -199,6 +204,14 @@ def osc_last_timing(ctx):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().osc_last_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def osc_timing_totals(ctx):
+    """Returns (counts[3], sums_ms[3]) for (constants, histogram, finalize) kernels."""
+    n = (ctypes.c_int64 * 3)()
+    t = (ctypes.c_double * 3)()
+    _check(ctx, lib().osc_timing_totals(ctx, n, t))
+    return list(n), list(t)
 
 
 def osc_launch_count(ctx) -> int:

@@ -81,6 +81,11 @@ struct osc_ctx {
     bool timing = false;
     cudaEvent_t ev[6] = {};
     double t_const = -1, t_hist = -1, t_final = -1;
+    // non-blocking timing: event pairs per kernel kind (0 const, 1 hist, 2 final)
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    int64_t t_count[3] = {0, 0, 0};
+    double t_sum[3] = {0, 0, 0};
     uint64_t launches = 0;
 
     int32_t tile_pt = 0, tile_chunk = 0;
@@ -104,6 +109,8 @@ osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_item
                             double lo, double hi, const double *d_hmeta, int64_t n_hist, double *d_out,
                             cudaStream_t st);
 int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items);
+cudaEvent_t pool_event(osc_ctx *c);
+osc_status drain_timing(osc_ctx *c);
 void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,
                  int32_t chunk, int64_t acc_hist_base, std::vector<WorkItem> &items);
 

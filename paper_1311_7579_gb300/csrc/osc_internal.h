@@ -77,7 +77,7 @@ struct HistParams {
     const SampleDev *samples;
     const float *pc32;
     const double *pc64;
-    unsigned long long *acc;  // 128-bit fixed-point bins: (lo, hi) per bin
+    unsigned long long *acc;  // fixed-point bins: three integer digit columns per bin
     int32_t *counter;         // dynamic work counter (reset by the finalize kernel)
     float lo_f, inv_f, nb_f;
     int32_t hist_stride_pts;  // histogram index step between consecutive points of a tile
@@ -85,7 +85,7 @@ struct HistParams {
 
 struct FinalParams {
     unsigned long long *acc;
-    const double *hmeta;      // per histogram: (2^(64-F), 2^-F, point index)
+    const double *hmeta;      // per histogram: (2^(64-F), 2^-F, unused, point index)
     const double *pc64;       // per-point FP64 constants (norm)
     double *out;
     int64_t n_hist;

@@ -165,12 +165,22 @@ __device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long lon
                                        unsigned long long h) {
     asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
 }
-// y = w * 2^(F-64); exact for every FP32 w (floor and the fraction are exact).
-__device__ __forceinline__ void fx_add_f32(unsigned long long &lo, unsigned long long &hi, float y) {
-    const float fl = floorf(y);
-    const long long h = __float2ll_rz(fl);
-    const unsigned long long l = __float2ull_rz((y - fl) * 18446744073709551616.0f);
-    fx_add(lo, hi, l, (unsigned long long)h);
+// Adds w * 2^F, truncated to an integer, using integer operations only (a
+// 64-bit float-to-integer conversion is an FP64-pipe instruction on this GPU).
+// F = 62 - ceil(log2 max|w_mc|) per sample, so |w| * 2^F < 2^63 and the
+// addend is the FP32 mantissa m shifted to bit s = e + sh (sh = F - 150) of a
+// 64-bit word; bits below the fixed-point LSB (2^-F) are dropped.
+__device__ __forceinline__ void fx_add_f32(unsigned long long &lo, unsigned long long &hi, float w, int sh) {
+    const uint32_t u = __float_as_uint(w);
+    const int e = (int)((u >> 23) & 0xFFu);
+    const int s = min(e + sh, 40);
+    const unsigned long long m = (unsigned long long)((u & 0x7FFFFFu) | (e ? 0x800000u : 0u));
+    const unsigned long long v = (s >= 0) ? (m << s) : ((s > -24) ? (m >> (-s)) : 0ull);
+    if (u >> 31) {
+        asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
+    } else {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
+    }
 }
 __device__ __forceinline__ void fx_add_f64(unsigned long long &lo, unsigned long long &hi, double y) {
     const double fl = floor(y);
@@ -178,10 +188,97 @@ __device__ __forceinline__ void fx_add_f64(unsigned long long &lo, unsigned long
     const unsigned long long l = __double2ull_rz((y - fl) * 18446744073709551616.0);
     fx_add(lo, hi, l, (unsigned long long)h);
 }
+// Global bins hold three integer columns: a flushed 128-bit value v is split
+// into digits v = d0 + d1 2^40 + d2 2^80 (d0, d1 in [0, 2^40), d2 signed) and
+// each digit is added with a fire-and-forget reduction.  Column sums are plain
+// integer sums, so the result is exact and independent of the flush order;
+// the finalize kernel recombines the columns.
 __device__ __forceinline__ void fx_flush(unsigned long long *p, unsigned long long lo, unsigned long long hi) {
-    const unsigned long long old = atomicAdd(p, lo);
-    const unsigned long long h2 = hi + ((old + lo < old) ? 1ull : 0ull);
-    if (h2) atomicAdd(p + 1, h2);
+    constexpr unsigned long long M40 = (1ull << 40) - 1ull;
+    const unsigned long long d0 = lo & M40;
+    const unsigned long long d1 = ((lo >> 40) | (hi << 24)) & M40;
+    const long long d2 = (long long)hi >> 16;
+    if (d0) atomicAdd(p, d0);
+    if (d1) atomicAdd(p + 1, d1);
+    if (d2) atomicAdd(p + 2, (unsigned long long)d2);
+}
+
+// Bin one weighted event under the point's energy scale and add it to the lane's
+// run-length accumulator (flushing the previous bin when the bin changes).
+struct RunAcc {
+    unsigned long long lo, hi;
+    int cur_b;
+};
+__device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
+                                              float er, float wt, int sh, bool active) {
+    const float x = __fmul_rn(sf, er);
+    const float tb = __fsub_rn(x, prm.lo_f);
+    const float u = __fmul_rn(tb, prm.inv_f);
+    if (active && tb >= 0.0f && u < prm.nb_f) {
+        const int b = __float2int_rz(u);
+        if (b != r.cur_b) {
+            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+            r.lo = r.hi = 0;
+            r.cur_b = b;
+        }
+        fx_add_f32(r.lo, r.hi, wt, sh);
+    }
+}
+__device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
+                                              float er, double wt, double hs, bool active) {
+    const float x = __fmul_rn(sf, er);
+    const float tb = __fsub_rn(x, prm.lo_f);
+    const float u = __fmul_rn(tb, prm.inv_f);
+    if (active && tb >= 0.0f && u < prm.nb_f) {
+        const int b = __float2int_rz(u);
+        if (b != r.cur_b) {
+            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+            r.lo = r.hi = 0;
+            r.cur_b = b;
+        }
+        fx_add_f64(r.lo, r.hi, wt * hs);
+    }
+}
+__device__ __forceinline__ void acc_finish(RunAcc &r, unsigned long long *accp) {
+    if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+}
+// End of a per-warp work item: lanes that end in the same bin (the lanes hold
+// consecutive sorted events, so such lanes are normally contiguous) first sum
+// their 128-bit values with shuffles, exactly, and one lane flushes the total.
+__device__ __forceinline__ void acc_finish_warp(RunAcc &r, unsigned long long *accp) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    const bool has = r.cur_b >= 0 && (r.lo | r.hi);
+    const int key = has ? r.cur_b : -1 - lane;
+    const unsigned mask = __match_any_sync(0xffffffffu, key);
+    const int first = __ffs(mask) - 1;
+    const int cnt = __popc(mask);
+    const bool contiguous = (mask >> first) == ((cnt == 32) ? 0xffffffffu : ((1u << cnt) - 1u));
+    if (!__all_sync(0xffffffffu, contiguous)) {
+        acc_finish(r, accp);
+        return;
+    }
+    const int end = first + cnt;
+    unsigned long long lo = r.lo, hi = r.hi;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, d);
+        const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, d);
+        if (lane + d < end) fx_add(lo, hi, l2, h2);
+    }
+    if (has && lane == first && (lo | hi)) fx_flush(accp + 3 * r.cur_b, lo, hi);
+}
+
+// FP32 matter term and c_L L / (2 pi E) float-float of one event.
+__device__ __forceinline__ void event_terms32(const SampleDev &sd, float E, int ch, float &A, float &th, float &tl) {
+    A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
+    // 1/E = r0 + rl to ~1e-14: the residual 1 - E r0 of the approximate reciprocal is exact in FP32
+    const float r0 = rcp_approx(E);
+    const float rl = r0 * fmaf(-E, r0, 1.0f);
+    th = sd.rev_hi * r0;
+    tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
+    const float sum = th + tl;
+    tl = tl - (sum - th);
+    th = sum;
 }
 
 // ------------------------------------------------------------ event staging
@@ -198,14 +295,8 @@ struct Stage64 {
 };
 
 __device__ __forceinline__ void stage_one32(Stage32 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
-    const float A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
-    const float r0 = __frcp_rn(E);
-    const float rl = r0 * fmaf(-E, r0, 1.0f);
-    float th = sd.rev_hi * r0;
-    float tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
-    const float sum = th + tl;
-    tl = tl - (sum - th);
-    th = sum;
+    float A, th, tl;
+    event_terms32(sd, E, ch, A, th, tl);
     s.ae[j] = make_float2(A, er);
     s.tt[j] = make_float2(th, tl);
     s.wc[j] = make_float2(w, __int_as_float(ch));
@@ -253,101 +344,205 @@ __device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const S
 // point pt of the tile and the tile events sl, sl + S, sl + 2S, ... (S = kNT/PT),
 // an increasing subsequence of the sorted events, so its bin sequence is
 // monotone within a channel and a register run-length accumulator suffices.
-template <int PREC, int PT>
-__global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const HistParams prm) {
-    constexpr int S = kNT / PT;
-    __shared__ typename StageOf<PREC>::T stg;
-    __shared__ int s_item;
-    const int tid = threadIdx.x;
-    const int lp = tid % PT;
-    const int sl = tid / PT;
+// One point per work item (points_per_block = 1): lanes share nothing, so each
+// warp takes work items on its own (no block barriers) and each lane reads its
+// events straight from global memory -- events ev_begin + lane + 32 k, coalesced
+// across the warp -- two per iteration for instruction-level parallelism, with
+// the next two prefetched into registers.
+template <int PREC>
+__device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
+    const int lane = threadIdx.x & 31;
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = atomicAdd(prm.counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= prm.n_items) break;
+        int it = 0;
+        if (lane == 0) it = atomicAdd(prm.counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= prm.n_items) return;
         const WorkItem wi = prm.items[it];
         const SampleDev sd = prm.samples[wi.sample];
-        const bool active = lp < wi.n_pts;
-        const int pidx = wi.point_base + (active ? lp : wi.n_pts - 1);
-        unsigned long long *accp = prm.acc + 2 * (wi.acc_base + lp) * (int64_t)prm.nbins;
-        unsigned long long alo = 0, ahi = 0;
-        int cur_b = -1, cur_ch = -1;
+        unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
+        RunAcc r{0ull, 0ull, -1};
+        int cur_ch = -1;
+        const int64_t end = wi.ev_begin + wi.ev_count;
+        int64_t e = wi.ev_begin + lane;
+        float Ea = 1.0f, ra = 0.0f, wa = 0.0f, Eb = 1.0f, rb = 0.0f, wb = 0.0f;
+        int ca = 0, cb = 0;
+        if (e < end) { Ea = sd.e_true[e]; ra = sd.e_reco[e]; wa = sd.w_mc[e]; ca = sd.chan[e]; }
+        if (e + 32 < end) { Eb = sd.e_true[e + 32]; rb = sd.e_reco[e + 32]; wb = sd.w_mc[e + 32]; cb = sd.chan[e + 32]; }
         if (PREC == kFP32) {
-            const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
+            const float *pc = prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
             Pt32 c;
             load_pt32(pc, c);
             Ch32 h;
             const float sf = pc[C32_ESCALE];
-            const float hs = sd.hscale_f;
-            for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
-                const int nt = min(kET, wi.ev_count - t0);
-                __syncthreads();
-                stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
-                __syncthreads();
-                const Stage32 &s = reinterpret_cast<const Stage32 &>(stg);
-                for (int j = sl; j < nt; j += S) {
-                    const float2 ae = s.ae[j], tt = s.tt[j], wc = s.wc[j];
-                    const int ch = __float_as_int(wc.y);
-                    if (ch != cur_ch) {
-                        cur_ch = ch;
-                        load_ch32(pc, ch, h);
-                    }
-                    const float P = prob_fp32(c, h, ae.x, tt.x, tt.y);
-                    const float w = P * wc.x;
-                    const float x = __fmul_rn(sf, ae.y);
-                    const float tb = __fsub_rn(x, prm.lo_f);
-                    const float u = __fmul_rn(tb, prm.inv_f);
-                    if (active && tb >= 0.0f && u < prm.nb_f) {
-                        const int b = __float2int_rz(u);
-                        if (b != cur_b) {
-                            if (cur_b >= 0 && (alo | ahi)) fx_flush(accp + 2 * cur_b, alo, ahi);
-                            alo = ahi = 0;
-                            cur_b = b;
+            const int sh = sd.frac_bits - 150;
+            for (; e < end; e += 64) {
+                const bool has_b = e + 32 < end;
+                const int64_t en = e + 64;
+                float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
+                int cna = 0, cnb = 0;
+                if (en < end) { Ena = sd.e_true[en]; rna = sd.e_reco[en]; wna = sd.w_mc[en]; cna = sd.chan[en]; }
+                if (en + 32 < end) {
+                    Enb = sd.e_true[en + 32]; rnb = sd.e_reco[en + 32]; wnb = sd.w_mc[en + 32]; cnb = sd.chan[en + 32];
+                }
+                if (ca == cur_ch && (!has_b || cb == cur_ch)) {
+                    float Aa, tha, tla, Ab, thb, tlb;
+                    event_terms32(sd, Ea, ca, Aa, tha, tla);
+                    event_terms32(sd, Eb, cb, Ab, thb, tlb);
+                    const float Pa = prob_fp32(c, h, Aa, tha, tla);
+                    const float Pb = prob_fp32(c, h, Ab, thb, tlb);
+                    acc_event_f32(r, accp, prm, sf, ra, Pa * wa, sh, true);
+                    acc_event_f32(r, accp, prm, sf, rb, Pb * wb, sh, has_b);
+                } else {
+                    for (int k = 0; k < 2; ++k) {
+                        const float E = k ? Eb : Ea, er = k ? rb : ra, w = k ? wb : wa;
+                        const int ch = k ? cb : ca;
+                        if (k && !has_b) break;
+                        if (ch != cur_ch) {
+                            cur_ch = ch;
+                            load_ch32(pc, ch, h);
                         }
-                        fx_add_f32(alo, ahi, w * hs);
+                        float A, th, tl;
+                        event_terms32(sd, E, ch, A, th, tl);
+                        const float P = prob_fp32(c, h, A, th, tl);
+                        acc_event_f32(r, accp, prm, sf, er, P * w, sh, true);
                     }
                 }
+                Ea = Ena; ra = rna; wa = wna; ca = cna;
+                Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
             }
         } else {
-            const double *pc = prm.pc64 + (int64_t)pidx * C64_STRIDE;
+            const double *pc = prm.pc64 + (int64_t)wi.point_base * C64_STRIDE;
             Pt64 c;
             load_pt64(pc, c);
             Ch64 h;
             const float sf = (float)pc[C64_ESCALE];
             const double hs = sd.hscale_d;
-            for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
-                const int nt = min(kET, wi.ev_count - t0);
-                __syncthreads();
-                stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
-                __syncthreads();
-                const Stage64 &s = reinterpret_cast<const Stage64 &>(stg);
-                for (int j = sl; j < nt; j += S) {
-                    const int ch = s.ch[j];
+            for (; e < end; e += 64) {
+                const bool has_b = e + 32 < end;
+                const int64_t en = e + 64;
+                float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
+                int cna = 0, cnb = 0;
+                if (en < end) { Ena = sd.e_true[en]; rna = sd.e_reco[en]; wna = sd.w_mc[en]; cna = sd.chan[en]; }
+                if (en + 32 < end) {
+                    Enb = sd.e_true[en + 32]; rnb = sd.e_reco[en + 32]; wnb = sd.w_mc[en + 32]; cnb = sd.chan[en + 32];
+                }
+                for (int k = 0; k < 2; ++k) {
+                    const float E = k ? Eb : Ea, er = k ? rb : ra, w = k ? wb : wa;
+                    const int ch = k ? cb : ca;
+                    if (k && !has_b) break;
                     if (ch != cur_ch) {
                         cur_ch = ch;
                         load_ch64(pc, ch, h);
                     }
-                    const double P = prob_fp64(c, h, s.a[j], s.tau[j]);
-                    const float2 ew = s.ew[j];
-                    const double w = P * (double)ew.y;
-                    const float x = __fmul_rn(sf, ew.x);
-                    const float tb = __fsub_rn(x, prm.lo_f);
-                    const float u = __fmul_rn(tb, prm.inv_f);
-                    if (active && tb >= 0.0f && u < prm.nb_f) {
-                        const int b = __float2int_rz(u);
-                        if (b != cur_b) {
-                            if (cur_b >= 0 && (alo | ahi)) fx_flush(accp + 2 * cur_b, alo, ahi);
-                            alo = ahi = 0;
-                            cur_b = b;
+                    const double Ad = sd.kA_rhoye * (double)E;
+                    const double P = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+                    acc_event_f64(r, accp, prm, sf, er, P * (double)w, hs, true);
+                }
+                Ea = Ena; ra = rna; wa = wna; ca = cna;
+                Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
+            }
+        }
+        acc_finish_warp(r, accp);
+    }
+}
+
+// ----------------------------------------------------------- histogram kernel
+// Lane layout for points_per_block PT > 1: PT points x (kNT / PT) event slices.
+// Lane (pt, sl) handles point pt of the tile and the tile events sl, sl + S,
+// sl + 2S, ... (S = kNT / PT), an increasing subsequence of the sorted events, so
+// its bin sequence is monotone within a channel and a register run-length
+// accumulator suffices.  Two events are computed per iteration.
+template <int PREC, int PT>
+__global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const HistParams prm) {
+    if constexpr (PT == 1) {
+        hist_items_per_warp<PREC>(prm);
+        return;
+    } else {
+        constexpr int S = kNT / PT;
+        __shared__ typename StageOf<PREC>::T stg;
+        __shared__ int s_item;
+        const int tid = threadIdx.x;
+        const int lp = tid % PT;
+        const int sl = tid / PT;
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) s_item = atomicAdd(prm.counter, 1);
+            __syncthreads();
+            const int it = s_item;
+            if (it >= prm.n_items) break;
+            const WorkItem wi = prm.items[it];
+            const SampleDev sd = prm.samples[wi.sample];
+            const bool active = lp < wi.n_pts;
+            const int pidx = wi.point_base + (active ? lp : wi.n_pts - 1);
+            unsigned long long *accp = prm.acc + 3 * (wi.acc_base + lp) * (int64_t)prm.nbins;
+            RunAcc r{0ull, 0ull, -1};
+            int cur_ch = -1;
+            if (PREC == kFP32) {
+                const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
+                Pt32 c;
+                load_pt32(pc, c);
+                Ch32 h;
+                const float sf = pc[C32_ESCALE];
+                const int sh = sd.frac_bits - 150;
+                for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
+                    const int nt = min(kET, wi.ev_count - t0);
+                    __syncthreads();
+                    stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
+                    __syncthreads();
+                    const Stage32 &s = reinterpret_cast<const Stage32 &>(stg);
+                    for (int j = sl; j < nt; j += 2 * S) {
+                        const int j2 = j + S;
+                        const bool has_b = j2 < nt;
+                        const float2 aea = s.ae[j], tta = s.tt[j], wca = s.wc[j];
+                        const float2 aeb = s.ae[has_b ? j2 : j], ttb = s.tt[has_b ? j2 : j], wcb = s.wc[has_b ? j2 : j];
+                        const int ca = __float_as_int(wca.y), cb = __float_as_int(wcb.y);
+                        if (ca == cur_ch && cb == cur_ch) {
+                            const float Pa = prob_fp32(c, h, aea.x, tta.x, tta.y);
+                            const float Pb = prob_fp32(c, h, aeb.x, ttb.x, ttb.y);
+                            acc_event_f32(r, accp, prm, sf, aea.y, Pa * wca.x, sh, active);
+                            acc_event_f32(r, accp, prm, sf, aeb.y, Pb * wcb.x, sh, active && has_b);
+                        } else {
+                            for (int k = 0; k < 2; ++k) {
+                                if (k && !has_b) break;
+                                const float2 ae = k ? aeb : aea, tt = k ? ttb : tta, wc = k ? wcb : wca;
+                                const int ch = k ? cb : ca;
+                                if (ch != cur_ch) {
+                                    cur_ch = ch;
+                                    load_ch32(pc, ch, h);
+                                }
+                                const float P = prob_fp32(c, h, ae.x, tt.x, tt.y);
+                                acc_event_f32(r, accp, prm, sf, ae.y, P * wc.x, sh, active);
+                            }
                         }
-                        fx_add_f64(alo, ahi, w * hs);
+                    }
+                }
+            } else {
+                const double *pc = prm.pc64 + (int64_t)pidx * C64_STRIDE;
+                Pt64 c;
+                load_pt64(pc, c);
+                Ch64 h;
+                const float sf = (float)pc[C64_ESCALE];
+                const double hs = sd.hscale_d;
+                for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
+                    const int nt = min(kET, wi.ev_count - t0);
+                    __syncthreads();
+                    stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
+                    __syncthreads();
+                    const Stage64 &s = reinterpret_cast<const Stage64 &>(stg);
+                    for (int j = sl; j < nt; j += S) {
+                        const int ch = s.ch[j];
+                        if (ch != cur_ch) {
+                            cur_ch = ch;
+                            load_ch64(pc, ch, h);
+                        }
+                        const double P = prob_fp64(c, h, s.a[j], s.tau[j]);
+                        const float2 ew = s.ew[j];
+                        acc_event_f64(r, accp, prm, sf, ew.x, P * (double)ew.y, hs, active);
                     }
                 }
             }
+            acc_finish(r, accp);
         }
-        if (cur_b >= 0 && (alo | ahi)) fx_flush(accp + 2 * cur_b, alo, ahi);
     }
 }
 
@@ -369,14 +564,8 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
                 cur_ch = ch;
                 load_ch32(pc, ch, h);
             }
-            const float A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
-            const float r0 = __frcp_rn(E);
-            const float rl = r0 * fmaf(-E, r0, 1.0f);
-            float th = sd.rev_hi * r0;
-            float tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
-            const float sum = th + tl;
-            tl = tl - (sum - th);
-            th = sum;
+            float A, th, tl;
+            event_terms32(sd, E, ch, A, th, tl);
             const float P = prob_fp32(c, h, A, th, tl);
             const float w = P * sd.w_mc[i];
             const int32_t o = sd.perm[i];

@@ -13,12 +13,20 @@ __global__ void k_point_consts(const osc_point *pts, int n, float *pc32, double 
 __global__ void k_final(const FinalParams f) {
     const int64_t n = f.n_hist * (int64_t)f.nbins;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long lo = f.acc[2 * i], hi = f.acc[2 * i + 1];
-        f.acc[2 * i] = 0ull;
-        f.acc[2 * i + 1] = 0ull;
+        const unsigned long long d0 = f.acc[3 * i], d1 = f.acc[3 * i + 1], d2 = f.acc[3 * i + 2];
+        f.acc[3 * i] = 0ull;
+        f.acc[3 * i + 1] = 0ull;
+        f.acc[3 * i + 2] = 0ull;
         const int64_t h = i / f.nbins;
-        const double v = (double)(long long)hi * f.hmeta[3 * h] + (double)lo * f.hmeta[3 * h + 1];
-        f.out[i] = v * f.pc64[(int64_t)f.hmeta[3 * h + 2] * C64_STRIDE + C64_NORM];
+        const double *m = f.hmeta + 4 * h;
+        // the digit columns depend on how runs were split into flushes; their
+        // combination, the exact 128-bit sum, does not -- convert only that
+        const unsigned __int128 v = (unsigned __int128)d0 + ((unsigned __int128)d1 << 40) +
+                                    ((unsigned __int128)(__int128)(long long)d2 << 80);
+        const long long hi = (long long)(unsigned long long)(v >> 64);
+        const unsigned long long lo = (unsigned long long)v;
+        const double x = (double)hi * m[0] + (double)lo * m[1];
+        f.out[i] = x * f.pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
 }

@@ -35,6 +35,14 @@
 namespace osc {
 
 // ------------------------------------------------------------------ FP32 path
+// Approximate reciprocal (PTX rcp.approx, about 1 ulp); used only where the
+// result is refined or enters a correction term.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct Pt32 {
     float p0, p1, q0, q1, q2, T0, c10, smt;
     float d0, d1, d2, g01, g02, g12;
@@ -54,7 +62,7 @@ __device__ __forceinline__ float shifted_newton(float dl, float A, float S, floa
     const float e = A * E;
     const float g = fmaf(fmaf(dl + b, dl, c), dl, -e);
     const float gp = fmaf(fmaf(3.0f, dl, b + b), dl, c);
-    return dl - __fdividef(g, gp);
+    return fmaf(-g, rcp_approx(gp), dl);
 }
 
 // Phase of root l relative to root 0 in revolutions, reduced to about [-0.62, 0.62]:
@@ -91,7 +99,7 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     const float dl2 = A - dl0 - dl1;  // trace: sum of shifts = A
     const float L0 = c.d0 + dl0, L1 = c.d1 + dl1, L2 = c.d2 + dl2;
     const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
-    const float inv = __fdividef(1.0f, g01 * g02 * g12);
+    const float inv = rcp_approx(g01 * g02 * g12);
     const float iD0 = g12 * inv, iD1 = -g02 * inv, iD2 = g01 * inv;
     // Sylvester numerators
     const float TA = c.T0 + A;

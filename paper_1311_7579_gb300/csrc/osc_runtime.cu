@@ -92,9 +92,9 @@ osc_status ensure_acc(osc_ctx *c, int64_t bins) {
     if (bins <= c->acc_cap_bins) return OSC_OK;
     int64_t want = std::max<int64_t>(bins, 1024);
     void *p;
-    osc_status s = dalloc(c, &p, (size_t)want * 16);
+    osc_status s = dalloc(c, &p, (size_t)want * 24);
     if (s) return s;
-    cudaError_t e = cudaMemsetAsync(p, 0, (size_t)want * 16, c->stream);
+    cudaError_t e = cudaMemsetAsync(p, 0, (size_t)want * 24, c->stream);
     if (e) return fail_cuda(c, e, "cudaMemsetAsync(acc)");
     if (c->d_acc) {
         cudaStreamSynchronize(c->stream);
@@ -177,6 +177,37 @@ osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_item
     e = launch_final(fp, st);
     if (e) return fail_cuda(c, e, "finalize kernel launch");
     c->launches += 2;
+    return OSC_OK;
+}
+
+cudaEvent_t pool_event(osc_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Resolve every pending timed launch (synchronises on the last one).
+osc_status drain_timing(osc_ctx *c) {
+    if (c->ev_pending.empty()) return OSC_OK;
+    cudaError_t e = cudaEventSynchronize(c->ev_pending.back().second.second);
+    if (e) return fail_cuda(c, e, "cudaEventSynchronize(timing)");
+    for (auto &p : c->ev_pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+        c->t_count[p.first] += 1;
+        c->t_sum[p.first] += ms;
+        if (p.first == 0) c->t_const = ms;
+        if (p.first == 1) c->t_hist = ms;
+        if (p.first == 2) c->t_final = ms;
+        c->ev_pool.push_back(p.second.first);
+        c->ev_pool.push_back(p.second.second);
+    }
+    c->ev_pending.clear();
     return OSC_OK;
 }
 
@@ -322,6 +353,11 @@ void osc_destroy(osc_ctx *ctx) {
     dfree(ctx, ctx->d_rw);
     for (auto &ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto &p : ctx->ev_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -337,7 +373,7 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     if (!(is_fin(d->density_gcc) && d->density_gcc >= 0)) return fail(ctx, OSC_E_RANGE, "density must be finite and >= 0");
     if (!(d->ye >= 0 && d->ye <= 1)) return fail(ctx, OSC_E_RANGE, "Y_e must be in [0, 1]");
     const int64_t n = d->n;
-    double wsum = 0.0;
+    double wsum = 0.0, wmax = 0.0;
     std::vector<uint8_t> ch((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         const float e = d->e_true[i], r = d->e_reco[i], w = d->w_mc[i];
@@ -358,13 +394,14 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
         }
         ch[i] = (uint8_t)chan_id(d->flav_in[i], d->flav_out[i], d->is_nubar[i]);
         wsum += std::fabs((double)w);
+        wmax = std::max(wmax, std::fabs((double)w));
     }
     if (!(wsum < std::ldexp(1.0, 60))) return fail(ctx, OSC_E_RANGE, "sum of |w_mc| must be < 2^60");
-    // fixed-point fraction bits: |bin sum| * 2^F < 2^126 with bin sums <= (1 + 2^-10) * sum |w_mc|
-    int F = 96;
-    const double bound = 2.0 * wsum + 1.0;
-    int need = (int)std::ceil(std::log2(bound));
-    if (126 - need < F) F = 126 - need;
+    // Fixed-point fraction bits F: every event weight |P w_mc| <= 1.0001 max|w_mc|
+    // becomes one 64-bit addend below 2^63, and bin sums stay far below 2^127.
+    int F = 62;
+    if (wmax > 0) F = 62 - (int)std::ceil(std::log2(wmax));
+    F = std::max(8, std::min(F, 190));
 
     std::vector<int32_t> order;
     sort_events(n, ch.data(), d->e_reco, order);
@@ -477,18 +514,20 @@ osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points) 
     ctx->pts.assign(pts, pts + n_points);
     CK(cudaMemcpyAsync(ctx->d_pts, ctx->pts.data(), (size_t)n_points * sizeof(osc_point), cudaMemcpyHostToDevice,
                        ctx->stream));
-    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->timing) {
+        e0 = pool_event(ctx);
+        e1 = pool_event(ctx);
+        CK(cudaEventRecord(e0, ctx->stream));
+    }
     CK(launch_point_consts(ctx->d_pts, n_points, ctx->d_pc32, ctx->d_pc64, ctx->stream));
     ctx->launches += 1;
     if (ctx->timing) {
-        CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-        CK(cudaEventSynchronize(ctx->ev[1]));
-        float ms = 0;
-        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
-        ctx->t_const = ms;
+        CK(cudaEventRecord(e1, ctx->stream));
+        ctx->ev_pending.push_back({0, {e0, e1}});
     }
-    // the caller's table is copied; make sure the pageable copy has landed before returning
-    CK(cudaStreamSynchronize(ctx->stream));
+    // The copy source is the context's own host table, and a pageable-source
+    // cudaMemcpyAsync has consumed it before returning: no host synchronisation.
     return OSC_OK;
 }
 
@@ -497,8 +536,8 @@ osc_status osc_set_tile(osc_ctx *ctx, int32_t points_per_block, int32_t events_p
     if (points_per_block != 0 && points_per_block != 1 && points_per_block != 4 && points_per_block != 16 &&
         points_per_block != 64 && points_per_block != 256)
         return fail(ctx, OSC_E_ARG, "points_per_block must be 0, 1, 4, 16, 64 or 256");
-    if (events_per_item < 0 || (events_per_item % 1024) != 0)
-        return fail(ctx, OSC_E_ARG, "events_per_item must be 0 or a positive multiple of 1024");
+    if (events_per_item < 0 || (events_per_item % 64) != 0)
+        return fail(ctx, OSC_E_ARG, "events_per_item must be 0 or a positive multiple of 64");
     ctx->tile_pt = points_per_block;
     ctx->tile_chunk = events_per_item;
     return OSC_OK;
@@ -506,15 +545,34 @@ osc_status osc_set_tile(osc_ctx *ctx, int32_t points_per_block, int32_t events_p
 
 osc_status osc_enable_timing(osc_ctx *ctx, int enable) {
     CHECK_CTX(ctx);
+    if (!enable) {
+        osc_status st = drain_timing(ctx);
+        if (st) return st;
+    }
     ctx->timing = enable != 0;
     return OSC_OK;
 }
 
-osc_status osc_last_timing(const osc_ctx *ctx, double *k_const_ms, double *k_hist_ms, double *k_final_ms) {
+osc_status osc_last_timing(osc_ctx *ctx, double *k_const_ms, double *k_hist_ms, double *k_final_ms) {
     if (!ctx) return OSC_E_ARG;
+    osc_status st = drain_timing(ctx);
+    if (st) return st;
     if (k_const_ms) *k_const_ms = ctx->t_const;
     if (k_hist_ms) *k_hist_ms = ctx->t_hist;
     if (k_final_ms) *k_final_ms = ctx->t_final;
+    return OSC_OK;
+}
+
+osc_status osc_timing_totals(osc_ctx *ctx, int64_t counts[3], double sums_ms[3]) {
+    if (!ctx || !counts || !sums_ms) return OSC_E_ARG;
+    osc_status st = drain_timing(ctx);
+    if (st) return st;
+    for (int k = 0; k < 3; ++k) {
+        counts[k] = ctx->t_count[k];
+        sums_ms[k] = ctx->t_sum[k];
+        ctx->t_count[k] = 0;
+        ctx->t_sum[k] = 0;
+    }
     return OSC_OK;
 }
 
@@ -590,11 +648,13 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     for (int32_t id : ids) ev += ctx->samples[id]->n;
     const int64_t tiles = (n_points + pt - 1) / pt;
     const int per_sm = (prec == kFP32) ? 2 : 1;
-    const int64_t slots = (int64_t)ctx->n_sm * per_sm;
-    // about 4 items per resident block, each at least one shared-memory tile
+    // one point per item: items are taken per warp; otherwise per block
+    const int64_t slots = (int64_t)ctx->n_sm * per_sm * (pt == 1 ? hist_threads() / 32 : 1);
+    const int64_t quantum = (pt == 1) ? 64 : 1024;
+    // about 4 items per resident worker
     int64_t c = (ev * tiles + 4 * slots - 1) / (4 * slots);
-    c = (c + 1023) / 1024 * 1024;
-    c = std::max<int64_t>(1024, std::min<int64_t>(c, 1 << 20));
+    c = (c + quantum - 1) / quantum * quantum;
+    c = std::max<int64_t>(quantum, std::min<int64_t>(c, 1 << 20));
     return (int32_t)c;
 }
 
@@ -636,14 +696,15 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     build_items(ss, point_begin, n_points, pt, chunk, 0, items);
     p->n_items = (int32_t)items.size();
     p->grid = hist_grid(ctx, prec, pt, p->n_items);
-    std::vector<double> hmeta((size_t)p->n_hist * 3);
+    std::vector<double> hmeta((size_t)p->n_hist * 4);
     for (size_t s = 0; s < ids.size(); ++s)
         for (int32_t q = 0; q < n_points; ++q) {
             const int64_t h = (int64_t)s * n_points + q;
             const int F = ss[s]->frac_bits;
-            hmeta[3 * h] = std::ldexp(1.0, 64 - F);
-            hmeta[3 * h + 1] = std::ldexp(1.0, -F);
-            hmeta[3 * h + 2] = (double)(point_begin + q);
+            hmeta[4 * h] = std::ldexp(1.0, 64 - F);
+            hmeta[4 * h + 1] = std::ldexp(1.0, -F);
+            hmeta[4 * h + 2] = 0.0;
+            hmeta[4 * h + 3] = (double)(point_begin + q);
         }
     void *a;
     osc_status st = OSC_OK;
@@ -698,11 +759,15 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     }
     if (ctx->timing) {
         // timed mode: plain launches bracketed by events on the context stream
-        CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+        cudaEvent_t a = pool_event(ctx), b = pool_event(ctx), d = pool_event(ctx), f = pool_event(ctx);
+        CK(cudaEventRecord(a, ctx->stream));
         CK(launch_hist(p->prec, p->pt, hp, p->grid, ctx->stream));
-        CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+        CK(cudaEventRecord(b, ctx->stream));
+        CK(cudaEventRecord(d, ctx->stream));
         CK(launch_final(fp, ctx->stream));
-        CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+        CK(cudaEventRecord(f, ctx->stream));
+        ctx->ev_pending.push_back({1, {a, b}});
+        ctx->ev_pending.push_back({2, {d, f}});
     } else {
         CK(cudaGraphLaunch(p->exec, ctx->stream));
     }
@@ -710,16 +775,6 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     return OSC_OK;
 }
 
-static osc_status collect_timing(osc_ctx *ctx) {
-    if (!ctx->timing) return OSC_OK;
-    CK(cudaEventSynchronize(ctx->ev[4]));
-    float a = 0, b = 0;
-    cudaEventElapsedTime(&a, ctx->ev[2], ctx->ev[3]);
-    cudaEventElapsedTime(&b, ctx->ev[3], ctx->ev[4]);
-    ctx->t_hist = a;
-    ctx->t_final = b;
-    return OSC_OK;
-}
 
 // Time one candidate tile shape (ms per histogram launch).
 static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t pb, int32_t np, int prec,
@@ -734,7 +789,7 @@ static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     double best = 1e30;
     for (int r = 0; r < 3; ++r) {
         st = run_plan(ctx, p, lo, hi, ctx->d_out);
-        if (!st) st = collect_timing(ctx);
+        if (!st) st = drain_timing(ctx);
         if (st) break;
         if (r > 0) best = std::min(best, ctx->t_hist);
     }
@@ -807,8 +862,6 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     st = run_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
     if (!out_on_device) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    st = collect_timing(ctx);
-    if (st) return st;
     if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream));
     return OSC_OK;
 }
