@@ -178,6 +178,47 @@ osc_status osc_wait(osc_ctx *ctx, uint64_t ticket, double *out_hist, int32_t tim
                     double *latency_us);
 osc_status osc_serve_stop(osc_ctx *ctx);
 
+/* One-point histogram that allocates nothing (the paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- for example a host
+ * framework that has reserved all device memory for its own allocator, or a
+ * fit loop in which an allocation, which may synchronise the device or fail
+ * under fragmentation, is not allowed in the middle of a step).
+ *
+ * Computes the same histogram as osc_histogram for one sample and one point,
+ * without a context: d_e_true, d_e_reco, d_w_mc (float) and d_flav_in,
+ * d_flav_out, d_is_nubar (uint8) are caller-owned DEVICE arrays of n events in
+ * any order (sorted by channel and E_reco is fastest; the bin sums are exact
+ * and do not depend on the order); baseline_km, density_gcc, ye as in
+ * osc_sample_desc; w_abs_max > 0 bounds |w_mc| and sets the fixed-point scale
+ * (F = 62 - ceil(log2 w_abs_max), as osc_load_sample derives it from the
+ * sample); *pt is a host point; d_out is a caller-owned DEVICE array of nbins
+ * doubles.  Work runs on cuda_stream (NULL = legacy default stream) on the
+ * current device, and the call returns after it has finished.
+ *
+ * Its working memory is one fixed file-scope device array of about 97 KB
+ * (point constants, 3 x 4096 accumulator words, a counter and an error flag),
+ * held by every GPU that loads this library until the process exits; nbins is
+ * therefore limited to 4096, and larger values are rejected with OSC_E_ARG.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  The first
+ * call on each device resolves the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the array: the call clears what must start at zero, and
+ * calls that overlap on the GPU (other threads, other streams) race and must
+ * not be issued.
+ *
+ * Errors: OSC_E_ARG (null pointer, bad precision, n outside [1, 2^31 - 1],
+ * nbins outside [1, 4096]), OSC_E_RANGE (invalid scalars or point; or, found
+ * on the device, an event with E_true <= 0 or non-finite, non-finite E_reco,
+ * |w_mc| > w_abs_max, or a bad flavour -- d_out is then left unwritten),
+ * OSC_E_CUDA.  A message goes to err (err_len bytes, may be NULL). */
+osc_status osc_histogram_noalloc(const float *d_e_true, const float *d_e_reco, const float *d_w_mc,
+                                 const uint8_t *d_flav_in, const uint8_t *d_flav_out,
+                                 const uint8_t *d_is_nubar, int64_t n, double baseline_km,
+                                 double density_gcc, double ye, double w_abs_max,
+                                 const osc_point *pt, osc_precision prec, double lo, double hi,
+                                 int32_t nbins, double *d_out, void *cuda_stream, char *err,
+                                 size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

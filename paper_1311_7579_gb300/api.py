@@ -26,7 +26,7 @@ ENTRY_POINTS = [
     "osc_version", "osc_create", "osc_destroy", "osc_last_error", "osc_load_sample", "osc_unload_sample",
     "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
     "osc_last_timing", "osc_timing_totals", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
-    "osc_serve_stop",
+    "osc_serve_stop", "osc_histogram_noalloc",
 ]
 
 
@@ -87,6 +87,8 @@ def load_library(path):
         "osc_submit": (st, [vp, i32, ctypes.POINTER(OscPoint), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
         "osc_wait": (st, [vp, ctypes.c_uint64, vp, i32, ctypes.POINTER(d)]),
         "osc_serve_stop": (st, [vp]),
+        "osc_histogram_noalloc": (st, [vp, vp, vp, vp, vp, vp, i64, d, d, d, d, ctypes.POINTER(OscPoint),
+                                       ctypes.c_int, d, d, i32, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -246,6 +248,22 @@ def osc_wait(ctx, ticket, nbins, timeout_ms=-1, out=None):
 
 def osc_serve_stop(ctx):
     _check(ctx, lib().osc_serve_stop(ctx))
+
+
+def osc_histogram_noalloc(e_true, e_reco, w_mc, flav_in, flav_out, is_nubar, baseline_km, density_gcc, ye,
+                          w_abs_max, point, prec, lo, hi, nbins, out, cuda_stream=None):
+    """One-point histogram with no allocation inside the library: every array
+    (inputs and the nbins-long float64 output) is a caller-owned torch CUDA tensor."""
+    arr, _ = _points(point)
+    buf = ctypes.create_string_buffer(256)
+    n = int(e_true.numel())
+    s = lib().osc_histogram_noalloc(_ptr(e_true), _ptr(e_reco), _ptr(w_mc), _ptr(flav_in), _ptr(flav_out),
+                                    _ptr(is_nubar), n, float(baseline_km), float(density_gcc), float(ye),
+                                    float(w_abs_max), arr, PRECISIONS[prec], float(lo), float(hi), int(nbins),
+                                    _ptr(out), cuda_stream, buf, 256)
+    if s != OSC_OK:
+        raise OscError(s, buf.value.decode())
+    return out
 
 
 class Context:
