@@ -55,6 +55,37 @@ def _dist():
     return ws, rank, local
 
 
+KERNEL_SOURCES = ("osc_internal.h", "osc_math.cuh", "osc_kernels.cuh", "osc_kernels_fp32.cu")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_hist_fp32_precision10M_1pt.md")
+
+
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1311_7579_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the bench kernel from its committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    fields = {}
+    for line in open(TRAFFIC_PROFILE):
+        if ":" in line and not line.startswith("|"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.split()[0] if v.split() else ""
+    if fields.get("kernel_source_sha256_16") != _kernel_source_hash():
+        return None
+    try:
+        return int(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -276,10 +307,7 @@ def run_ours(args):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
         achieved = FP32_FLOP_PER_EVPT * N_EVENTS / (k_hist_ms * 1e-3) / 1e12
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "k_hist_fp32_traffic.json")
-        if os.path.exists(tfile):
-            traffic = json.load(open(tfile)).get("bytes_per_launch_precision_10M")
+        traffic = _profiled_traffic()
         # precision study + CPU baseline (rank 0, N = 1 semantics: its own sample)
         p32 = np.zeros(N_EVENTS)
         p64 = np.zeros(N_EVENTS)

@@ -830,7 +830,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
             double best_ms = 1e30;
             const int32_t cands[] = {1, 4, 16, 64, 256};
             for (int32_t c : cands) {
-                if (c > 4 * n_points && c != 1) continue;  // too many idle lanes
+                if (c > n_points && c != 1) continue;  // idle lanes never pay off
                 for (int k = 0; k < 2; ++k) {
                     int32_t ch = default_chunk(ctx, ids, n_points, c, pr) * (k ? 4 : 1);
                     ch = std::min(ch, 1 << 20);
