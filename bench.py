@@ -169,6 +169,71 @@ def cpu_baseline_leg(sample, point_row, gpu_p32, gpu_p64, n_sample):
     return cpu, prec, h
 
 
+def serving_leg(api, synth, c, rates, seconds, prec="fp32"):
+    """Serving workload: requests (sample id uniform over the 8 uneven samples,
+    point from the scan distribution) arrive as a Poisson process at each rate for
+    `seconds`; a submitter thread follows the arrival schedule, a collector thread
+    waits on the tickets.  Reports achieved request and event-weight throughput and
+    the p50/p99 submit-to-completion latency measured inside the library."""
+    import threading
+    samples = synth.uneven_samples()
+    sids = [api.osc_load_sample(c, s) for s in samples]
+    sizes = np.array([s["n"] for s in samples], dtype=np.float64)
+    api.osc_serve_start(c, 256, LO, 20.0, NBINS)
+    out = {"samples_events": [int(x) for x in sizes], "max_slots": 256, "prec": prec, "rates": []}
+    try:
+        # warm-up
+        for k in range(16):
+            t = api.osc_submit(c, sids[k % len(sids)], synth.scan_points(1, seed=k)[0], prec)
+            api.osc_wait(c, t, NBINS)
+        for rate in rates:
+            t_arr, sid_idx, pts = synth.serving_requests(seconds, rate, n_samples=len(sids), seed=4004)
+            n = len(t_arr)
+            tickets = [None] * n
+            lat = np.zeros(n)
+            done = [0]
+
+            def collect():
+                buf = np.zeros(NBINS)
+                for i in range(n):
+                    while tickets[i] is None:
+                        time.sleep(0)
+                    _, lat[i] = api.osc_wait(c, tickets[i], NBINS, out=buf)
+                    done[0] += 1
+
+            th = threading.Thread(target=collect)
+            th.start()
+            t0 = time.perf_counter()
+            for i in range(n):
+                while time.perf_counter() - t0 < t_arr[i]:
+                    pass
+                tickets[i] = api.osc_submit(c, sids[sid_idx[i]], pts[i], prec)
+            th.join()
+            wall = time.perf_counter() - t0
+            evpt = float(sizes[sid_idx].sum())
+            out["rates"].append({"offered_req_s": rate, "requests": n, "achieved_req_s": n / wall,
+                                 "event_weights_s": evpt / wall, "p50_us": float(np.percentile(lat, 50)),
+                                 "p99_us": float(np.percentile(lat, 99))})
+        # saturation: everything queued at once
+        nsat = 2000 if prec == "fp32" else 100
+        rng = np.random.default_rng(5005)
+        sid_idx = rng.integers(0, len(sids), nsat)
+        pts = synth.scan_points(nsat, seed=5006)
+        t0 = time.perf_counter()
+        tk = [api.osc_submit(c, sids[sid_idx[i]], pts[i], prec) for i in range(nsat)]
+        buf = np.zeros(NBINS)
+        for t in tk:
+            api.osc_wait(c, t, NBINS, out=buf)
+        wall = time.perf_counter() - t0
+        out["saturation"] = {"requests": nsat, "req_s": nsat / wall,
+                             "event_weights_s": float(sizes[sid_idx].sum()) / wall}
+    finally:
+        api.osc_serve_stop(c)
+        for sid in sids:
+            api.osc_unload_sample(c, sid)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -322,6 +387,10 @@ def run_ours(args):
             # bin-wise relative error of the full-sample histograms, FP32 vs FP64 GPU path
             nz = h64 != 0
             prec_study["fp32_vs_fp64_hist_max_rel"] = float(np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
+        serving = None
+        if args.serve_seconds > 0:
+            serving = {"fp32": serving_leg(api, synth, c, (2000, 10000, 20000), args.serve_seconds, "fp32"),
+                       "fp64": serving_leg(api, synth, c, (100,), args.serve_seconds, "fp64")}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
@@ -349,6 +418,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64, "d2h_bytes_per_step": 8 * NBINS},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "serving": serving,
         }
         print(json.dumps(result), flush=True)
     ctx.close()
@@ -393,6 +463,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-events", type=int, default=N_EVENTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds per offered rate of the serving leg (0 skips it)")
     ap.add_argument("--profile", action="store_true", help="run the small ncu profiling case and exit")
     ap.add_argument("--events", type=int, default=2_000_000)
     ap.add_argument("--points", type=int, default=1)

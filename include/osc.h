@@ -114,7 +114,7 @@ const char *osc_last_error(const osc_ctx *ctx);
  * osc_reweight outputs is the caller's original order. */
 osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *desc, int32_t *sample_id);
 
-/* Free a resident sample. */
+/* Free a resident sample (OSC_E_STATE while serving runs). */
 osc_status osc_unload_sample(osc_ctx *ctx, int32_t sample_id);
 
 /* Replace the parameter-point table with n_points host points (copied), and
@@ -172,8 +172,13 @@ osc_status osc_sync(osc_ctx *ctx);
 osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi, int32_t nbins);
 osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_precision prec,
                       uint64_t *ticket);
-/* Wait for a ticket's histogram (host buffer of nbins doubles); latency_us (may
- * be NULL) receives submit-to-completion time.  timeout_ms < 0 waits forever. */
+/* osc_submit validates the point and sample on the calling thread and queues
+ * the request (OSC_E_BUSY beyond 2^20 queued requests); the ticket is > 0.
+ * osc_wait waits for a ticket's histogram (host buffer of nbins doubles) and
+ * releases it; latency_us (may be NULL) receives the submit-to-completion time.
+ * timeout_ms < 0 waits forever; OSC_E_TIMEOUT when the time runs out; OSC_E_ARG
+ * for a ticket never issued.  osc_serve_stop drops queued requests, lets the
+ * in-flight batches finish, and frees the serving buffers. */
 osc_status osc_wait(osc_ctx *ctx, uint64_t ticket, double *out_hist, int32_t timeout_ms,
                     double *latency_us);
 osc_status osc_serve_stop(osc_ctx *ctx);

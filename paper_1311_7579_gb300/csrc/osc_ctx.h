@@ -86,7 +86,7 @@ struct osc_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
     int64_t t_count[3] = {0, 0, 0};
     double t_sum[3] = {0, 0, 0};
-    uint64_t launches = 0;
+    std::atomic<uint64_t> launches{0};
 
     int32_t tile_pt = 0, tile_chunk = 0;
     std::map<std::string, std::pair<int32_t, int32_t>> tuned;

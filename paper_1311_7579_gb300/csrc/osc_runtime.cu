@@ -471,6 +471,7 @@ osc_status osc_unload_sample(osc_ctx *ctx, int32_t sample_id) {
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     auto it = ctx->samples.find(sample_id);
     if (it == ctx->samples.end()) return fail(ctx, OSC_E_ARG, "unknown sample id");
+    if (ctx->serve) return fail(ctx, OSC_E_STATE, "cannot unload a sample while serving runs");
     drop_plans(ctx);  // plans reference the sample's device arrays
     cudaStreamSynchronize(ctx->stream);
     free_sample(ctx, it->second);
@@ -578,7 +579,7 @@ osc_status osc_timing_totals(osc_ctx *ctx, int64_t counts[3], double sums_ms[3])
 
 osc_status osc_launch_count(const osc_ctx *ctx, uint64_t *count) {
     if (!ctx || !count) return OSC_E_ARG;
-    *count = ctx->launches;
+    *count = ctx->launches.load();
     return OSC_OK;
 }
 

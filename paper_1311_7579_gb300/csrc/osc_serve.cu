@@ -1,22 +1,390 @@
-// osc_serve.cu -- continuous-batching serving loop (placeholder until built out).
+// osc_serve.cu -- continuous-batching serving loop (one request = one MCMC
+// step's reweight of one sample at one parameter point, Sec. 2.2).
+//
+// A scheduler thread inside the library admits queued (sample, point) requests
+// into batches while at most max_slots requests are in flight and a batch slot
+// (preallocated device memory, charged to the workspace cap at serve start) is
+// free.  Each batch runs on its own stream -- constants kernel, histogram
+// kernel over (request, event range) work items, finalize kernel, copy-out --
+// so batches admitted while earlier ones run overlap on the device.  A host
+// callback marks the batch complete; osc_wait hands each request's histogram
+// back.  Bins are exact integer sums, so a request's result is bitwise the same
+// alone and in any mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
 #include "osc_ctx.h"
 
 using namespace osc;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+constexpr int kBatches = 3;          // batches in flight (one stream each)
+constexpr int kMaxItems = 1 << 16;   // work items per batch
+
+struct Request {
+    uint64_t ticket;
+    osc_point pt;
+    int prec;
+    SampleDev sd;
+    int32_t frac_bits;
+    Clock::time_point t_submit;
+};
+
+struct Result {
+    std::vector<double> hist;
+    double latency_us;
+};
+
+struct Batch {
+    cudaStream_t stream = nullptr;
+    // device
+    osc_point *d_pts = nullptr;
+    float *d_pc32 = nullptr;
+    double *d_pc64 = nullptr;
+    unsigned long long *d_acc = nullptr;
+    double *d_out = nullptr;
+    double *d_hmeta = nullptr;
+    WorkItem *d_items = nullptr;
+    SampleDev *d_samples = nullptr;
+    int32_t *d_counter = nullptr;
+    // pinned host staging
+    osc_point *h_pts = nullptr;
+    double *h_out = nullptr;
+    double *h_hmeta = nullptr;
+    WorkItem *h_items = nullptr;
+    SampleDev *h_samples = nullptr;
+    // state
+    std::vector<Request> reqs;
+    bool busy = false;
+    bool done = false;
+};
+
+}  // namespace
+
+struct osc_serve {
+    osc_ctx *ctx = nullptr;
+    int32_t max_slots = 0, nbins = 0;
+    double lo = 0, hi = 0;
+    std::mutex mu;
+    std::condition_variable cv;       // scheduler wake-ups
+    std::condition_variable cv_done;  // waiters
+    std::deque<Request> pending;
+    std::unordered_map<uint64_t, Result> results;
+    uint64_t next_ticket = 1;
+    int32_t inflight = 0;
+    bool stop = false;
+    std::string thread_error;
+    Batch batch[kBatches];
+    std::thread th;
+};
+
+namespace {
+
+void CUDART_CB on_batch_done(void *arg) {
+    auto *pr = static_cast<std::pair<osc_serve *, Batch *> *>(arg);
+    osc_serve *sv = pr->first;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        pr->second->done = true;
+    }
+    sv->cv.notify_all();
+}
+
+// Build and enqueue one batch (called by the scheduler thread without the lock).
+osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *> *cb_arg) {
+    osc_ctx *ctx = sv->ctx;
+    const int n = (int)b.reqs.size();
+    const int prec = b.reqs[0].prec;
+    // distinct samples, per-request point rows, histogram metadata
+    int n_samp = 0;
+    std::vector<int> samp_of(n);
+    for (int r = 0; r < n; ++r) {
+        int s = -1;
+        for (int k = 0; k < n_samp; ++k)
+            if (b.h_samples[k].e_true == b.reqs[r].sd.e_true) s = k;
+        if (s < 0) {
+            s = n_samp++;
+            b.h_samples[s] = b.reqs[r].sd;
+        }
+        samp_of[r] = s;
+        b.h_pts[r] = b.reqs[r].pt;
+        const int F = b.reqs[r].frac_bits;
+        b.h_hmeta[4 * r] = std::ldexp(1.0, 64 - F);
+        b.h_hmeta[4 * r + 1] = std::ldexp(1.0, -F);
+        b.h_hmeta[4 * r + 2] = 0.0;
+        b.h_hmeta[4 * r + 3] = (double)r;
+    }
+    // one point per item; chunk so that items fill the GPU's warps about four times
+    int64_t total = 0;
+    for (int r = 0; r < n; ++r) total += b.reqs[r].sd.n;
+    const int64_t warps = (int64_t)ctx->n_sm * 2 * (hist_threads() / 32);
+    int64_t chunk = std::max<int64_t>((total + 4 * warps - 1) / (4 * warps), 1024);
+    chunk = std::max<int64_t>(chunk, (total + kMaxItems - n - 1) / (kMaxItems - n));
+    chunk = (chunk + 63) / 64 * 64;
+    int n_items = 0;
+    for (int r = 0; r < n; ++r)
+        for (int64_t e = 0; e < b.reqs[r].sd.n; e += chunk) {
+            WorkItem &w = b.h_items[n_items++];
+            w.sample = samp_of[r];
+            w.point_base = r;
+            w.n_pts = 1;
+            w.ev_count = (int32_t)std::min<int64_t>(chunk, b.reqs[r].sd.n - e);
+            w.ev_begin = e;
+            w.acc_base = r;
+        }
+    std::stable_sort(b.h_items, b.h_items + n_items,
+                     [](const WorkItem &x, const WorkItem &y) { return x.ev_count > y.ev_count; });
+    cudaStream_t st = b.stream;
+    cudaError_t e = cudaMemcpyAsync(b.d_pts, b.h_pts, n * sizeof(osc_point), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(b.d_hmeta, b.h_hmeta, n * 4 * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(b.d_items, b.h_items, n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(b.d_samples, b.h_samples, n_samp * sizeof(SampleDev), cudaMemcpyHostToDevice, st);
+    if (!e) e = launch_point_consts(b.d_pts, n, b.d_pc32, b.d_pc64, st);
+    if (e) return fail_cuda(ctx, e, "serving batch set-up");
+    HistParams hp;
+    hp.items = b.d_items;
+    hp.n_items = n_items;
+    hp.nbins = sv->nbins;
+    hp.samples = b.d_samples;
+    hp.pc32 = b.d_pc32;
+    hp.pc64 = b.d_pc64;
+    hp.acc = b.d_acc;
+    hp.counter = b.d_counter;
+    hp.lo_f = (float)sv->lo;
+    hp.inv_f = (float)((double)sv->nbins / (sv->hi - sv->lo));
+    hp.nb_f = (float)sv->nbins;
+    hp.hist_stride_pts = 1;
+    e = launch_hist(prec, 1, hp, hist_grid(ctx, prec, 1, (n_items + 7) / 8), st);
+    FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
+    if (!e) e = launch_final(fp, st);
+    if (!e) e = cudaMemcpyAsync(b.h_out, b.d_out, (size_t)n * sv->nbins * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaLaunchHostFunc(st, on_batch_done, cb_arg);
+    if (e) return fail_cuda(ctx, e, "serving batch launch");
+    ctx->launches += 3;
+    return OSC_OK;
+}
+
+void scheduler(osc_serve *sv) {
+    cudaSetDevice(sv->ctx->device);
+    std::pair<osc_serve *, Batch *> cb[kBatches];
+    for (int k = 0; k < kBatches; ++k) cb[k] = {sv, &sv->batch[k]};
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        sv->cv.wait(lk, [&] {
+            bool any_busy = false;
+            for (auto &b : sv->batch) {
+                if (b.busy && b.done) return true;
+                any_busy |= b.busy;
+            }
+            if (sv->stop) return !any_busy;
+            if (sv->pending.empty() || sv->inflight >= sv->max_slots) return false;
+            return !(sv->batch[0].busy && sv->batch[1].busy && sv->batch[2].busy);
+        });
+        // publish finished batches
+        bool published = false;
+        for (auto &b : sv->batch) {
+            if (!(b.busy && b.done)) continue;
+            const auto now = Clock::now();
+            for (size_t r = 0; r < b.reqs.size(); ++r) {
+                Result res;
+                res.hist.assign(b.h_out + r * sv->nbins, b.h_out + (r + 1) * sv->nbins);
+                res.latency_us = std::chrono::duration<double, std::micro>(now - b.reqs[r].t_submit).count();
+                sv->results[b.reqs[r].ticket] = std::move(res);
+            }
+            sv->inflight -= (int32_t)b.reqs.size();
+            b.reqs.clear();
+            b.busy = b.done = false;
+            published = true;
+        }
+        if (published) sv->cv_done.notify_all();
+        if (sv->stop) {
+            bool any = false;
+            for (auto &b : sv->batch) any |= b.busy;
+            if (!any) break;
+            continue;  // let in-flight batches finish
+        }
+        // admit: one free batch slot, up to the free request slots, one precision per batch
+        Batch *free_b = nullptr;
+        int free_k = 0;
+        for (int k = 0; k < kBatches; ++k)
+            if (!sv->batch[k].busy) {
+                free_b = &sv->batch[k];
+                free_k = k;
+                break;
+            }
+        if (!free_b || sv->pending.empty() || sv->inflight >= sv->max_slots) continue;
+        const int take_max = sv->max_slots - sv->inflight;
+        const int prec = sv->pending.front().prec;
+        while ((int)free_b->reqs.size() < take_max && !sv->pending.empty() && sv->pending.front().prec == prec) {
+            free_b->reqs.push_back(sv->pending.front());
+            sv->pending.pop_front();
+        }
+        sv->inflight += (int32_t)free_b->reqs.size();
+        free_b->busy = true;
+        free_b->done = false;
+        lk.unlock();
+        osc_status st = launch_batch(sv, *free_b, &cb[free_k]);
+        lk.lock();
+        if (st != OSC_OK) {
+            sv->thread_error = sv->ctx->err;
+            sv->stop = true;
+            free_b->busy = false;
+            sv->inflight -= (int32_t)free_b->reqs.size();
+            free_b->reqs.clear();
+            sv->cv_done.notify_all();
+        }
+    }
+}
+
+void free_serve(osc_ctx *ctx, osc_serve *sv) {
+    for (auto &b : sv->batch) {
+        if (b.stream) {
+            cudaStreamSynchronize(b.stream);
+            cudaStreamDestroy(b.stream);
+        }
+        dfree(ctx, b.d_pts);
+        dfree(ctx, b.d_pc32);
+        dfree(ctx, b.d_pc64);
+        dfree(ctx, b.d_acc);
+        dfree(ctx, b.d_out);
+        dfree(ctx, b.d_hmeta);
+        dfree(ctx, b.d_items);
+        dfree(ctx, b.d_samples);
+        dfree(ctx, b.d_counter);
+        cudaFreeHost(b.h_pts);
+        cudaFreeHost(b.h_out);
+        cudaFreeHost(b.h_hmeta);
+        cudaFreeHost(b.h_items);
+        cudaFreeHost(b.h_samples);
+    }
+    delete sv;
+}
+
+}  // namespace
 
 extern "C" {
 
 osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi, int32_t nbins) {
-    (void)max_slots; (void)lo; (void)hi; (void)nbins;
-    return ctx ? fail(ctx, OSC_E_STATE, "serving not available") : OSC_E_ARG;
+    if (!ctx) return OSC_E_ARG;
+    if (ctx->poisoned) return fail(ctx, OSC_E_STATE, "context poisoned: " + ctx->err);
+    if (ctx->serve) return fail(ctx, OSC_E_STATE, "serving already running");
+    if (max_slots < 1 || max_slots > 4096) return fail(ctx, OSC_E_ARG, "max_slots must be in [1, 4096]");
+    if (nbins < 1 || nbins > (1 << 16)) return fail(ctx, OSC_E_ARG, "nbins must be in [1, 65536]");
+    if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo)) return fail(ctx, OSC_E_RANGE, "need finite lo < hi");
+    std::lock_guard<std::mutex> api(ctx->api_mu);
+    osc_serve *sv = new osc_serve();
+    sv->ctx = ctx;
+    sv->max_slots = max_slots;
+    sv->lo = lo;
+    sv->hi = hi;
+    sv->nbins = nbins;
+    const size_t S = (size_t)max_slots, B = (size_t)nbins;
+    osc_status st = OSC_OK;
+    for (auto &b : sv->batch) {
+        void *p;
+        cudaError_t e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
+        if (e) st = fail_cuda(ctx, e, "cudaStreamCreate");
+        if (!st && !(st = dalloc(ctx, &p, S * sizeof(osc_point)))) b.d_pts = (osc_point *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * C32_STRIDE * 4))) b.d_pc32 = (float *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * C64_STRIDE * 8))) b.d_pc64 = (double *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * B * 24))) b.d_acc = (unsigned long long *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * B * 8))) b.d_out = (double *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * 4 * 8))) b.d_hmeta = (double *)p;
+        if (!st && !(st = dalloc(ctx, &p, (size_t)kMaxItems * sizeof(WorkItem)))) b.d_items = (WorkItem *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * sizeof(SampleDev)))) b.d_samples = (SampleDev *)p;
+        if (!st && !(st = dalloc(ctx, &p, 64))) b.d_counter = (int32_t *)p;
+        if (!st) {
+            e = cudaMemsetAsync(b.d_acc, 0, S * B * 24, b.stream);
+            if (!e) e = cudaMemsetAsync(b.d_counter, 0, 64, b.stream);
+            if (!e) e = cudaHostAlloc((void **)&b.h_pts, S * sizeof(osc_point), 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_out, S * B * 8, 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_hmeta, S * 4 * 8, 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_items, (size_t)kMaxItems * sizeof(WorkItem), 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_samples, S * sizeof(SampleDev), 0);
+            if (!e) e = cudaStreamSynchronize(b.stream);
+            if (e) st = fail_cuda(ctx, e, "serving buffers");
+        }
+        if (st) break;
+    }
+    if (st) {
+        free_serve(ctx, sv);
+        return st;
+    }
+    ctx->serve = sv;
+    sv->th = std::thread(scheduler, sv);
+    return OSC_OK;
 }
+
 osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_precision prec, uint64_t *ticket) {
-    (void)sample_id; (void)pt; (void)prec; (void)ticket;
-    return ctx ? fail(ctx, OSC_E_STATE, "serving not running") : OSC_E_ARG;
+    if (!ctx || !pt || !ticket) return OSC_E_ARG;
+    osc_serve *sv = ctx->serve;
+    if (!sv) return OSC_E_STATE;
+    if (prec != OSC_FP64 && prec != OSC_FP32_BULK) return OSC_E_ARG;
+    Request r;
+    {
+        std::lock_guard<std::mutex> api(ctx->api_mu);
+        if (validate_point(nullptr, *pt, 0) != OSC_OK) return OSC_E_RANGE;
+        auto it = ctx->samples.find(sample_id);
+        if (it == ctx->samples.end()) return OSC_E_ARG;
+        r.sd = it->second->dev;
+        r.frac_bits = it->second->frac_bits;
+    }
+    r.pt = *pt;
+    r.prec = prec == OSC_FP32_BULK ? kFP32 : kFP64;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stop) return OSC_E_STATE;
+        if (sv->pending.size() >= (size_t)1 << 20) return OSC_E_BUSY;
+        r.ticket = sv->next_ticket++;
+        r.t_submit = Clock::now();
+        sv->pending.push_back(r);
+        *ticket = r.ticket;
+    }
+    sv->cv.notify_all();
+    return OSC_OK;
 }
+
 osc_status osc_wait(osc_ctx *ctx, uint64_t ticket, double *out_hist, int32_t timeout_ms, double *latency_us) {
-    (void)ticket; (void)out_hist; (void)timeout_ms; (void)latency_us;
-    return ctx ? fail(ctx, OSC_E_STATE, "serving not running") : OSC_E_ARG;
+    if (!ctx || !out_hist) return OSC_E_ARG;
+    osc_serve *sv = ctx->serve;
+    if (!sv) return OSC_E_STATE;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (ticket == 0 || ticket >= sv->next_ticket) return OSC_E_ARG;
+    auto ready = [&] { return sv->results.count(ticket) > 0 || (sv->stop && !sv->thread_error.empty()); };
+    if (timeout_ms < 0)
+        sv->cv_done.wait(lk, ready);
+    else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return OSC_E_TIMEOUT;
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return OSC_E_CUDA;
+    std::memcpy(out_hist, it->second.hist.data(), sizeof(double) * sv->nbins);
+    if (latency_us) *latency_us = it->second.latency_us;
+    sv->results.erase(it);
+    return OSC_OK;
 }
-osc_status osc_serve_stop(osc_ctx *ctx) { return ctx ? OSC_OK : OSC_E_ARG; }
+
+osc_status osc_serve_stop(osc_ctx *ctx) {
+    if (!ctx) return OSC_E_ARG;
+    osc_serve *sv = ctx->serve;
+    if (!sv) return OSC_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->pending.clear();
+    }
+    sv->cv.notify_all();
+    if (sv->th.joinable()) sv->th.join();
+    sv->cv_done.notify_all();
+    const std::string terr = sv->thread_error;
+    ctx->serve = nullptr;
+    free_serve(ctx, sv);
+    if (!terr.empty()) return fail(ctx, OSC_E_CUDA, "serving thread: " + terr);
+    return OSC_OK;
+}
 
 }  // extern "C"
