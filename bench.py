@@ -411,7 +411,7 @@ def run_ours(args):
                          "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
                                         % (n_sm, sm_mhz, src),
                          "flop_per_evpt": FP32_FLOP_PER_EVPT,
-                         "hbm_gbs_event_stream": 13.0 * N_EVENTS / (k_hist_ms * 1e-3) / 1e9,
+                         "hbm_gbs_event_stream": 16.0 * N_EVENTS / (k_hist_ms * 1e-3) / 1e9,
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "cpu_baseline": cpu,
             "precision": prec_study,

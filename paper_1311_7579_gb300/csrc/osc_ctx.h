@@ -24,8 +24,7 @@ struct Sample {
     int64_t n = 0, n_pad = 0;
     double L = 0, rho = 0, ye = 0;
     int32_t frac_bits = 96;
-    float *e_true = nullptr, *e_reco = nullptr, *w_mc = nullptr;
-    uint8_t *chan = nullptr;
+    float4 *ev = nullptr;
     int32_t *perm = nullptr;
     SampleDev dev{};
 };
@@ -109,6 +108,7 @@ osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_item
                             double lo, double hi, const double *d_hmeta, int64_t n_hist, double *d_out,
                             cudaStream_t st);
 int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items);
+bool fuse_finalize(int64_t n_hist, int32_t nbins);
 cudaEvent_t pool_event(osc_ctx *c);
 osc_status drain_timing(osc_ctx *c);
 void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,

@@ -44,10 +44,7 @@ enum PC64 : int {
 
 // ---- resident sample as seen by a kernel ----------------------------------
 struct SampleDev {
-    const float *e_true;      // sorted by (channel, e_reco)
-    const float *e_reco;
-    const float *w_mc;
-    const uint8_t *chan;      // channel id
+    const float4 *ev;         // per event (e_true, e_reco, w_mc, channel id bits), sorted by (channel, e_reco)
     const int32_t *perm;      // sorted position -> caller's event index
     int64_t n;
     double kA_rhoye;          // k_A * rho * Y_e  [eV^2 / GeV]
@@ -81,6 +78,18 @@ struct HistParams {
     int32_t *counter;         // dynamic work counter (reset by the finalize kernel)
     float lo_f, inv_f, nb_f;
     int32_t hist_stride_pts;  // histogram index step between consecutive points of a tile
+    // fused finalize (small outputs): the last block converts the bins
+    int32_t fuse_final;
+    int64_t fin_n_hist;
+    const double *fin_hmeta;
+    double *fin_out;
+};
+
+// Points passed to the constants kernel by value (no host-to-device copy).
+constexpr int kPointsByValue = 256;
+struct PointsByValue {
+    int32_t n;
+    osc_point p[kPointsByValue];
 };
 
 struct FinalParams {
@@ -106,6 +115,7 @@ struct ReweightParams {
 // Launch helpers implemented in the kernel translation units.
 enum Prec { kFP64 = 0, kFP32 = 1 };
 cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
+cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st);
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);

@@ -36,94 +36,124 @@ __device__ __forceinline__ void split_ff(double v, float *hi, float *lo) {
     *lo = (float)(v - (double)h);
 }
 
-__device__ inline void point_consts_one(const osc_point &P, float *c32, double *c64) {
-    const double s12 = sqrt(P.s2_12), c12 = sqrt(1.0 - P.s2_12);
-    const double s13 = sqrt(P.s2_13), c13 = sqrt(1.0 - P.s2_13);
-    const double s23 = sqrt(P.s2_23), c23 = sqrt(1.0 - P.s2_23);
-    double sd, cd;
-    sincos(P.dcp, &sd, &cd);
-    // PDG PMNS U[flavour][mass]: U_e3 = s13 e^{-i delta}, e^{+i delta} in the mu, tau rows
-    cplx64 U[3][3];
-    U[0][0] = {c12 * c13, 0.0};
-    U[0][1] = {s12 * c13, 0.0};
-    U[0][2] = {s13 * cd, -s13 * sd};
-    U[1][0] = {-s12 * c23 - c12 * s23 * s13 * cd, -c12 * s23 * s13 * sd};
-    U[1][1] = {c12 * c23 - s12 * s23 * s13 * cd, -s12 * s23 * s13 * sd};
-    U[1][2] = {s23 * c13, 0.0};
-    U[2][0] = {s12 * s23 - c12 * c23 * s13 * cd, -c12 * c23 * s13 * sd};
-    U[2][1] = {-c12 * s23 - s12 * c23 * s13 * cd, -s12 * c23 * s13 * sd};
-    U[2][2] = {c23 * c13, 0.0};
+// One warp per point.  The FP64 work is spread over lanes so that its
+// dependent chain stays short: lanes 0-6 form the six square roots and the
+// sine/cosine of delta; lanes 0-8 each form one entry of H0 = U diag(m) U^dagger
+// and of H0^2, shared through shuffles; then lane 9 writes the cubic
+// coefficients, lane 10 the sorted vacuum spectrum and shifted-cubic constants,
+// lane 11 the systematics, and lanes 0-8 one channel each.
+__device__ inline void point_consts_warp(const osc_point &P, float *c32, double *c64, int lane) {
+    double tv = 0.0;
+    if (lane < 6) {
+        const double x = (lane == 0) ? P.s2_12 : (lane == 1) ? 1.0 - P.s2_12 : (lane == 2) ? P.s2_13
+                       : (lane == 3) ? 1.0 - P.s2_13 : (lane == 4) ? P.s2_23 : 1.0 - P.s2_23;
+        tv = sqrt(x);
+    }
+    double sd = 0.0, cd = 0.0;
+    if (lane == 6) sincos(P.dcp, &sd, &cd);
+    const double s12 = __shfl_sync(0xffffffffu, tv, 0), c12 = __shfl_sync(0xffffffffu, tv, 1);
+    const double s13 = __shfl_sync(0xffffffffu, tv, 2), c13 = __shfl_sync(0xffffffffu, tv, 3);
+    const double s23 = __shfl_sync(0xffffffffu, tv, 4), c23 = __shfl_sync(0xffffffffu, tv, 5);
+    sd = __shfl_sync(0xffffffffu, sd, 6);
+    cd = __shfl_sync(0xffffffffu, cd, 6);
     const double dm21 = P.dm21, dm31 = P.dm32 + P.dm21;
-    const double m[3] = {0.0, dm21, dm31};
-    // H0 = U diag(m) U^dagger, H2 = H0^2 = U diag(m^2) U^dagger, entries [beta][alpha]
-    cplx64 H[3][3], H2[3][3];
-    for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) {
-            cplx64 h = {0, 0}, h2 = {0, 0};
-            for (int k = 1; k < 3; ++k) {
-                const cplx64 t = cmul_conj(U[b][k], m[k], U[a][k]);
-                h.re += t.re; h.im += t.im;
-                h2.re += t.re * m[k]; h2.im += t.im * m[k];
+    // H0 and H0^2 entries [beta][alpha]; lane l < 9 forms entry (l / 3, l % 3) from
+    // columns 1, 2 of the PDG PMNS rows it needs (U_e3 = s13 e^{-i delta},
+    // e^{+i delta} in the mu and tau rows; column 0 carries m = 0)
+    cplx64 h = {0, 0}, h2 = {0, 0};
+    if (lane < 9) {
+        const int b = lane / 3, a = lane % 3;
+        cplx64 Ub[3], Ua[3];
+        for (int side = 0; side < 2; ++side) {
+            const int f = side ? a : b;
+            cplx64 *u = side ? Ua : Ub;
+            if (f == 0) {
+                u[1] = {s12 * c13, 0.0};
+                u[2] = {s13 * cd, -s13 * sd};
+            } else if (f == 1) {
+                u[1] = {c12 * c23 - s12 * s23 * s13 * cd, -s12 * s23 * s13 * sd};
+                u[2] = {s23 * c13, 0.0};
+            } else {
+                u[1] = {-c12 * s23 - s12 * c23 * s13 * cd, -s12 * c23 * s13 * sd};
+                u[2] = {c23 * c13, 0.0};
             }
-            H[b][a] = h;
-            H2[b][a] = h2;
         }
+        const double m[3] = {0.0, dm21, dm31};
+        for (int k = 1; k < 3; ++k) {
+            const cplx64 t = cmul_conj(Ub[k], m[k], Ua[k]);
+            h.re += t.re; h.im += t.im;
+            h2.re += t.re * m[k]; h2.im += t.im * m[k];
+        }
+    }
+    cplx64 H[3][3], H2[3][3];
+    for (int j = 0; j < 9; ++j) {
+        H[j / 3][j % 3] = {__shfl_sync(0xffffffffu, h.re, j), __shfl_sync(0xffffffffu, h.im, j)};
+        H2[j / 3][j % 3] = {__shfl_sync(0xffffffffu, h2.re, j), __shfl_sync(0xffffffffu, h2.im, j)};
+    }
     const double T0 = dm21 + dm31;
     const double c10 = dm21 * dm31;
-    const double smt = H[1][1].re + H[2][2].re;
-    const double mee = H[1][1].re * H[2][2].re - (H[1][2].re * H[1][2].re + H[1][2].im * H[1][2].im);
-    // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
-    //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee
-    const double p0 = c10 - T0 * T0 / 3.0, p1 = smt - 2.0 * T0 / 3.0;
-    const double q0 = -2.0 * T0 * T0 * T0 / 27.0 + c10 * T0 / 3.0;
-    const double q1 = -2.0 * T0 * T0 / 9.0 + c10 / 3.0 + smt * T0 / 3.0 - mee;
-    const double q2 = -2.0 * T0 / 9.0 + smt / 3.0;
-    // sorted vacuum spectrum and |U_e|^2 in the same order
-    const double ze[3] = {U[0][0].re * U[0][0].re, U[0][1].re * U[0][1].re,
-                          U[0][2].re * U[0][2].re + U[0][2].im * U[0][2].im};
-    double d[3], z[3];
-    if (dm31 > 0) {
-        d[0] = 0.0; d[1] = dm21; d[2] = dm31;
-        z[0] = ze[0]; z[1] = ze[1]; z[2] = ze[2];
-    } else {
-        d[0] = dm31; d[1] = 0.0; d[2] = dm21;
-        z[0] = ze[2]; z[1] = ze[0]; z[2] = ze[1];
+    if (lane == 9) {
+        // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
+        //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee
+        constexpr double k3 = 1.0 / 3.0, k9 = 1.0 / 9.0, k27 = 1.0 / 27.0;
+        const double smt = H[1][1].re + H[2][2].re;
+        const double mee = H[1][1].re * H[2][2].re - (H[1][2].re * H[1][2].re + H[1][2].im * H[1][2].im);
+        const double p0 = c10 - T0 * T0 * k3, p1 = smt - 2.0 * T0 * k3;
+        const double q0 = -2.0 * T0 * T0 * T0 * k27 + c10 * T0 * k3;
+        const double q1 = -2.0 * T0 * T0 * k9 + c10 * k3 + smt * T0 * k3 - mee;
+        const double q2 = -2.0 * T0 * k9 + smt * k3;
+        c32[C32_P0] = (float)p0; c32[C32_P1] = (float)p1;
+        c32[C32_Q0] = (float)q0; c32[C32_Q1] = (float)q1; c32[C32_Q2] = (float)q2;
+        c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10; c32[C32_SMT] = (float)smt;
+        c64[C64_P0] = p0; c64[C64_P1] = p1; c64[C64_Q0] = q0; c64[C64_Q1] = q1; c64[C64_Q2] = q2;
+        c64[C64_T0] = T0; c64[C64_C10] = c10; c64[C64_SMT] = smt;
     }
-    double S[2], PI[2], W[2], E[2];
-    for (int l = 0; l < 2; ++l) {
-        const int j = (l + 1) % 3, k = (l + 2) % 3;
-        const double aj = d[l] - d[j], ak = d[l] - d[k];
-        S[l] = aj + ak;
-        PI[l] = aj * ak;
-        W[l] = z[l] * (aj + ak) + z[j] * ak + z[k] * aj;
-        E[l] = z[l] * aj * ak;
-    }
-    c32[C32_P0] = (float)p0; c32[C32_P1] = (float)p1;
-    c32[C32_Q0] = (float)q0; c32[C32_Q1] = (float)q1; c32[C32_Q2] = (float)q2;
-    c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10; c32[C32_SMT] = (float)smt;
-    c32[C32_D0] = (float)d[0]; c32[C32_D1] = (float)d[1]; c32[C32_D2] = (float)d[2];
-    c32[C32_G01] = (float)(d[0] - d[1]); c32[C32_G02] = (float)(d[0] - d[2]); c32[C32_G12] = (float)(d[1] - d[2]);
-    split_ff(d[1] - d[0], &c32[C32_V1H], &c32[C32_V1L]);
-    split_ff(d[2] - d[0], &c32[C32_V2H], &c32[C32_V2L]);
-    c32[C32_S0] = (float)S[0]; c32[C32_PI0] = (float)PI[0]; c32[C32_W0] = (float)W[0]; c32[C32_E0] = (float)E[0];
-    c32[C32_S1] = (float)S[1]; c32[C32_PI1] = (float)PI[1]; c32[C32_W1] = (float)W[1]; c32[C32_E1] = (float)E[1];
-    c32[C32_ESCALE] = (float)P.escale;
-    c64[C64_P0] = p0; c64[C64_P1] = p1; c64[C64_Q0] = q0; c64[C64_Q1] = q1; c64[C64_Q2] = q2;
-    c64[C64_T0] = T0; c64[C64_C10] = c10; c64[C64_SMT] = smt;
-    c64[C64_ESCALE] = P.escale; c64[C64_NORM] = P.norm;
-    // channel (alpha -> beta): X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            const int o = 6 * (a * 3 + b);
-            double Zr = 0, Zi = 0;
-            if (a == 0) { Zr += H[b][0].re; Zi += H[b][0].im; }
-            if (b == 0) { Zr += H[0][a].re; Zi += H[0][a].im; }
-            const double v[6] = {H[b][a].re, H[b][a].im, H2[b][a].re, H2[b][a].im, Zr, Zi};
-            for (int t = 0; t < 6; ++t) {
-                c32[C32_CH + o + t] = (float)v[t];
-                c64[C64_CH + o + t] = v[t];
-            }
+    if (lane == 10) {
+        // sorted vacuum spectrum and |U_e|^2 in the same order
+        const double ze[3] = {c12 * c12 * c13 * c13, s12 * s12 * c13 * c13, s13 * s13};
+        double d[3], z[3];
+        if (dm31 > 0) {
+            d[0] = 0.0; d[1] = dm21; d[2] = dm31;
+            z[0] = ze[0]; z[1] = ze[1]; z[2] = ze[2];
+        } else {
+            d[0] = dm31; d[1] = 0.0; d[2] = dm21;
+            z[0] = ze[2]; z[1] = ze[0]; z[2] = ze[1];
         }
+        double S[2], PI[2], W[2], E[2];
+        for (int l = 0; l < 2; ++l) {
+            const int j = (l + 1) % 3, k = (l + 2) % 3;
+            const double aj = d[l] - d[j], ak = d[l] - d[k];
+            S[l] = aj + ak;
+            PI[l] = aj * ak;
+            W[l] = z[l] * (aj + ak) + z[j] * ak + z[k] * aj;
+            E[l] = z[l] * aj * ak;
+        }
+        c32[C32_D0] = (float)d[0]; c32[C32_D1] = (float)d[1]; c32[C32_D2] = (float)d[2];
+        c32[C32_G01] = (float)(d[0] - d[1]); c32[C32_G02] = (float)(d[0] - d[2]); c32[C32_G12] = (float)(d[1] - d[2]);
+        split_ff(d[1] - d[0], &c32[C32_V1H], &c32[C32_V1L]);
+        split_ff(d[2] - d[0], &c32[C32_V2H], &c32[C32_V2L]);
+        c32[C32_S0] = (float)S[0]; c32[C32_PI0] = (float)PI[0]; c32[C32_W0] = (float)W[0]; c32[C32_E0] = (float)E[0];
+        c32[C32_S1] = (float)S[1]; c32[C32_PI1] = (float)PI[1]; c32[C32_W1] = (float)W[1]; c32[C32_E1] = (float)E[1];
+    }
+    if (lane == 11) {
+        c32[C32_ESCALE] = (float)P.escale;
+        c64[C64_ESCALE] = P.escale;
+        c64[C64_NORM] = P.norm;
+    }
+    // channel (alpha -> beta) = lane (alpha * 3 + beta):
+    // X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
+    if (lane < 9) {
+        const int a = lane / 3, b = lane % 3;
+        const int o = 6 * lane;
+        double Zr = 0, Zi = 0;
+        if (a == 0) { Zr += H[b][0].re; Zi += H[b][0].im; }
+        if (b == 0) { Zr += H[0][a].re; Zi += H[0][a].im; }
+        const double v[6] = {H[b][a].re, H[b][a].im, H2[b][a].re, H2[b][a].im, Zr, Zi};
+        for (int t = 0; t < 6; ++t) {
+            c32[C32_CH + o + t] = (float)v[t];
+            c64[C64_CH + o + t] = v[t];
+        }
+    }
 }
 
 // ------------------------------------------------------------ lane constants
@@ -201,6 +231,45 @@ __device__ __forceinline__ void fx_flush(unsigned long long *p, unsigned long lo
     if (d0) atomicAdd(p, d0);
     if (d1) atomicAdd(p + 1, d1);
     if (d2) atomicAdd(p + 2, (unsigned long long)d2);
+}
+
+// Value of bin i: the three digit columns depend on how runs were split into
+// flushes; their combination, the exact 128-bit sum, does not, and only that
+// is converted (times 2^-F and the point's norm).
+__device__ __forceinline__ double final_bin(unsigned long long d0, unsigned long long d1, unsigned long long d2,
+                                            const double *m, const double *pc64) {
+    const unsigned __int128 v = (unsigned __int128)d0 + ((unsigned __int128)d1 << 40) +
+                                ((unsigned __int128)(__int128)(long long)d2 << 80);
+    const long long hi = (long long)(unsigned long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    const double x = (double)hi * m[0] + (double)lo * m[1];
+    return x * pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM];
+}
+
+// Small outputs: the last block of the histogram kernel to finish converts the
+// bins (instead of a separate finalize launch).  Every thread fences its own
+// flushes before the block takes its completion ticket.
+__device__ __forceinline__ void fused_final(const HistParams &prm) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(prm.counter + 1, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long d0 = __ldcg(prm.acc + 3 * i), d1 = __ldcg(prm.acc + 3 * i + 1),
+                                 d2 = __ldcg(prm.acc + 3 * i + 2);
+        prm.acc[3 * i] = 0ull;
+        prm.acc[3 * i + 1] = 0ull;
+        prm.acc[3 * i + 2] = 0ull;
+        prm.fin_out[i] = final_bin(d0, d1, d2, prm.fin_hmeta + 4 * (i / prm.nbins), prm.pc64);
+    }
+    if (threadIdx.x == 0) {
+        prm.counter[0] = 0;
+        prm.counter[1] = 0;
+    }
 }
 
 // Bin one weighted event under the point's energy scale and add it to the lane's
@@ -314,36 +383,23 @@ struct StageOf { using T = Stage32; };
 template <>
 struct StageOf<kFP64> { using T = Stage64; };
 
-// Load tile [base, base + nt) of the item into shared memory, 4 events per
-// thread with 128-bit loads (sample arrays are padded to a multiple of 4).
+// Load tile [base, base + nt) of the item into shared memory: one 16-byte event
+// record per load, consecutive threads on consecutive events.
 template <int PREC>
 __device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const SampleDev &sd, int64_t base, int nt) {
-    const int j = 4 * threadIdx.x;
-    if (j >= nt) return;
-    const float4 e = *reinterpret_cast<const float4 *>(sd.e_true + base + j);
-    const float4 r = *reinterpret_cast<const float4 *>(sd.e_reco + base + j);
-    const float4 w = *reinterpret_cast<const float4 *>(sd.w_mc + base + j);
-    const uchar4 c = *reinterpret_cast<const uchar4 *>(sd.chan + base + j);
-    if (PREC == kFP32) {
-        Stage32 &t = reinterpret_cast<Stage32 &>(s);
-        stage_one32(t, j + 0, sd, e.x, r.x, w.x, c.x);
-        stage_one32(t, j + 1, sd, e.y, r.y, w.y, c.y);
-        stage_one32(t, j + 2, sd, e.z, r.z, w.z, c.z);
-        stage_one32(t, j + 3, sd, e.w, r.w, w.w, c.w);
-    } else {
-        Stage64 &t = reinterpret_cast<Stage64 &>(s);
-        stage_one64(t, j + 0, sd, e.x, r.x, w.x, c.x);
-        stage_one64(t, j + 1, sd, e.y, r.y, w.y, c.y);
-        stage_one64(t, j + 2, sd, e.z, r.z, w.z, c.z);
-        stage_one64(t, j + 3, sd, e.w, r.w, w.w, c.w);
+#pragma unroll
+    for (int k = 0; k < kET / kNT; ++k) {
+        const int j = threadIdx.x + k * kNT;
+        if (j < nt) {
+            const float4 r = sd.ev[base + j];
+            if (PREC == kFP32)
+                stage_one32(reinterpret_cast<Stage32 &>(s), j, sd, r.x, r.y, r.z, __float_as_int(r.w));
+            else
+                stage_one64(reinterpret_cast<Stage64 &>(s), j, sd, r.x, r.y, r.z, __float_as_int(r.w));
+        }
     }
 }
 
-// ----------------------------------------------------------- histogram kernel
-// Lane layout: PT points x (kNT / PT) event slices.  Lane (pt, sl) handles
-// point pt of the tile and the tile events sl, sl + S, sl + 2S, ... (S = kNT/PT),
-// an increasing subsequence of the sorted events, so its bin sequence is
-// monotone within a channel and a register run-length accumulator suffices.
 // One point per work item (points_per_block = 1): lanes share nothing, so each
 // warp takes work items on its own (no block barriers) and each lane reads its
 // events straight from global memory -- events ev_begin + lane + 32 k, coalesced
@@ -366,8 +422,14 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
         int64_t e = wi.ev_begin + lane;
         float Ea = 1.0f, ra = 0.0f, wa = 0.0f, Eb = 1.0f, rb = 0.0f, wb = 0.0f;
         int ca = 0, cb = 0;
-        if (e < end) { Ea = sd.e_true[e]; ra = sd.e_reco[e]; wa = sd.w_mc[e]; ca = sd.chan[e]; }
-        if (e + 32 < end) { Eb = sd.e_true[e + 32]; rb = sd.e_reco[e + 32]; wb = sd.w_mc[e + 32]; cb = sd.chan[e + 32]; }
+        if (e < end) {
+            const float4 q = sd.ev[e];
+            Ea = q.x; ra = q.y; wa = q.z; ca = __float_as_int(q.w);
+        }
+        if (e + 32 < end) {
+            const float4 q = sd.ev[e + 32];
+            Eb = q.x; rb = q.y; wb = q.z; cb = __float_as_int(q.w);
+        }
         if (PREC == kFP32) {
             const float *pc = prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
             Pt32 c;
@@ -380,9 +442,13 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 const int64_t en = e + 64;
                 float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
                 int cna = 0, cnb = 0;
-                if (en < end) { Ena = sd.e_true[en]; rna = sd.e_reco[en]; wna = sd.w_mc[en]; cna = sd.chan[en]; }
+                if (en < end) {
+                    const float4 q = sd.ev[en];
+                    Ena = q.x; rna = q.y; wna = q.z; cna = __float_as_int(q.w);
+                }
                 if (en + 32 < end) {
-                    Enb = sd.e_true[en + 32]; rnb = sd.e_reco[en + 32]; wnb = sd.w_mc[en + 32]; cnb = sd.chan[en + 32];
+                    const float4 q = sd.ev[en + 32];
+                    Enb = q.x; rnb = q.y; wnb = q.z; cnb = __float_as_int(q.w);
                 }
                 if (ca == cur_ch && (!has_b || cb == cur_ch)) {
                     float Aa, tha, tla, Ab, thb, tlb;
@@ -422,9 +488,13 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 const int64_t en = e + 64;
                 float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
                 int cna = 0, cnb = 0;
-                if (en < end) { Ena = sd.e_true[en]; rna = sd.e_reco[en]; wna = sd.w_mc[en]; cna = sd.chan[en]; }
+                if (en < end) {
+                    const float4 q = sd.ev[en];
+                    Ena = q.x; rna = q.y; wna = q.z; cna = __float_as_int(q.w);
+                }
                 if (en + 32 < end) {
-                    Enb = sd.e_true[en + 32]; rnb = sd.e_reco[en + 32]; wnb = sd.w_mc[en + 32]; cnb = sd.chan[en + 32];
+                    const float4 q = sd.ev[en + 32];
+                    Enb = q.x; rnb = q.y; wnb = q.z; cnb = __float_as_int(q.w);
                 }
                 for (int k = 0; k < 2; ++k) {
                     const float E = k ? Eb : Ea, er = k ? rb : ra, w = k ? wb : wa;
@@ -456,6 +526,7 @@ template <int PREC, int PT>
 __global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const HistParams prm) {
     if constexpr (PT == 1) {
         hist_items_per_warp<PREC>(prm);
+        if (prm.fuse_final) fused_final(prm);
         return;
     } else {
         constexpr int S = kNT / PT;
@@ -543,6 +614,7 @@ __global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const His
             }
             acc_finish(r, accp);
         }
+        if (prm.fuse_final) fused_final(prm);
     }
 }
 
@@ -558,8 +630,9 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
         Ch32 h;
         int cur_ch = -1;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sd.n; i += stride) {
-            const float E = sd.e_true[i];
-            const int ch = sd.chan[i];
+            const float4 q = sd.ev[i];
+            const float E = q.x;
+            const int ch = __float_as_int(q.w);
             if (ch != cur_ch) {
                 cur_ch = ch;
                 load_ch32(pc, ch, h);
@@ -567,7 +640,7 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
             float A, th, tl;
             event_terms32(sd, E, ch, A, th, tl);
             const float P = prob_fp32(c, h, A, th, tl);
-            const float w = P * sd.w_mc[i];
+            const float w = P * q.z;
             const int32_t o = sd.perm[i];
             if (r.out_prob) r.out_prob[o] = (double)P;
             if (r.out_weight) r.out_weight[o] = (double)w * r.norm;
@@ -579,15 +652,16 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
         Ch64 h;
         int cur_ch = -1;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sd.n; i += stride) {
-            const float E = sd.e_true[i];
-            const int ch = sd.chan[i];
+            const float4 q = sd.ev[i];
+            const float E = q.x;
+            const int ch = __float_as_int(q.w);
             if (ch != cur_ch) {
                 cur_ch = ch;
                 load_ch64(pc, ch, h);
             }
             const double Ad = sd.kA_rhoye * (double)E;
             const double P = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
-            const double w = P * (double)sd.w_mc[i];
+            const double w = P * (double)q.z;
             const int32_t o = sd.perm[i];
             if (r.out_prob) r.out_prob[o] = P;
             if (r.out_weight) r.out_weight[o] = w * r.norm;

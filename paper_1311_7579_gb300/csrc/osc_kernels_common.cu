@@ -4,9 +4,15 @@
 namespace osc {
 
 __global__ void k_point_consts(const osc_point *pts, int n, float *pc32, double *pc64) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    point_consts_one(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // whole warps
+    point_consts_warp(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE, threadIdx.x & 31);
+}
+
+__global__ void k_point_consts_v(const PointsByValue pv, float *pc32, double *pc64) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= pv.n) return;
+    point_consts_warp(pv.p[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------- finalize
@@ -17,16 +23,7 @@ __global__ void k_final(const FinalParams f) {
         f.acc[3 * i] = 0ull;
         f.acc[3 * i + 1] = 0ull;
         f.acc[3 * i + 2] = 0ull;
-        const int64_t h = i / f.nbins;
-        const double *m = f.hmeta + 4 * h;
-        // the digit columns depend on how runs were split into flushes; their
-        // combination, the exact 128-bit sum, does not -- convert only that
-        const unsigned __int128 v = (unsigned __int128)d0 + ((unsigned __int128)d1 << 40) +
-                                    ((unsigned __int128)(__int128)(long long)d2 << 80);
-        const long long hi = (long long)(unsigned long long)(v >> 64);
-        const unsigned long long lo = (unsigned long long)v;
-        const double x = (double)hi * m[0] + (double)lo * m[1];
-        f.out[i] = x * f.pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM];
+        f.out[i] = final_bin(d0, d1, d2, f.hmeta + 4 * (i / f.nbins), f.pc64);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
 }
@@ -47,7 +44,16 @@ const void *hist_kernel_fn(int prec, int pt) {
 const void *final_kernel_fn() { return (const void *)k_final; }
 
 cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
-    k_point_consts<<<(n + 127) / 128, 128, 0, st>>>(d_pts, n, pc32, pc64);
+    k_point_consts<<<(n + 3) / 4, 128, 0, st>>>(d_pts, n, pc32, pc64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
+    if (n < 1 || n > kPointsByValue) return cudaErrorInvalidValue;
+    PointsByValue pv;
+    pv.n = n;
+    for (int i = 0; i < n; ++i) pv.p[i] = h_pts[i];
+    k_point_consts_v<<<(n + 3) / 4, 128, 0, st>>>(pv, pc32, pc64);
     return cudaGetLastError();
 }
 

@@ -163,7 +163,14 @@ static void fill_hist_params(HistParams &hp, const WorkItem *d_items, int32_t n_
     hp.inv_f = (float)((double)nbins / (hi - lo));
     hp.nb_f = (float)nbins;
     hp.hist_stride_pts = 1;
+    hp.fuse_final = 0;
+    hp.fin_n_hist = 0;
+    hp.fin_hmeta = nullptr;
+    hp.fin_out = nullptr;
 }
+
+// Outputs this small are converted by the histogram kernel's last block.
+bool fuse_finalize(int64_t n_hist, int32_t nbins) { return n_hist * (int64_t)nbins <= 4096; }
 
 osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_items, int32_t n_items, int grid,
                             const SampleDev *d_samples, const float *pc32, const double *pc64, int32_t nbins,
@@ -256,10 +263,7 @@ static void sort_events(int64_t n, const uint8_t *ch, const float *er, std::vect
 }
 
 static void free_sample(osc_ctx *c, Sample *s) {
-    dfree(c, s->e_true);
-    dfree(c, s->e_reco);
-    dfree(c, s->w_mc);
-    dfree(c, s->chan);
+    dfree(c, s->ev);
     dfree(c, s->perm);
     delete s;
 }
@@ -406,14 +410,13 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     std::vector<int32_t> order;
     sort_events(n, ch.data(), d->e_reco, order);
     const int64_t n_pad = (n + 3) / 4 * 4 + 4;
-    std::vector<float> et((size_t)n_pad, 1.0f), er((size_t)n_pad, 0.0f), w((size_t)n_pad, 0.0f);
-    std::vector<uint8_t> cs((size_t)n_pad, 0);
+    std::vector<float4> rec((size_t)n_pad, make_float4(1.0f, 0.0f, 0.0f, 0.0f));
     for (int64_t k = 0; k < n; ++k) {
         const int32_t i = order[k];
-        et[k] = d->e_true[i];
-        er[k] = d->e_reco[i];
-        w[k] = d->w_mc[i];
-        cs[k] = ch[i];
+        int32_t cbits = ch[i];
+        float cf;
+        std::memcpy(&cf, &cbits, 4);
+        rec[k] = make_float4(d->e_true[i], d->e_reco[i], d->w_mc[i], cf);
     }
     Sample *s = new Sample();
     s->n = n;
@@ -424,30 +427,20 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     s->frac_bits = F;
     osc_status st = OSC_OK;
     void *p;
-    if ((st = dalloc(ctx, &p, n_pad * 4)) == OSC_OK) s->e_true = (float *)p;
-    if (!st && (st = dalloc(ctx, &p, n_pad * 4)) == OSC_OK) s->e_reco = (float *)p;
-    if (!st && (st = dalloc(ctx, &p, n_pad * 4)) == OSC_OK) s->w_mc = (float *)p;
-    if (!st && (st = dalloc(ctx, &p, n_pad)) == OSC_OK) s->chan = (uint8_t *)p;
+    if ((st = dalloc(ctx, &p, n_pad * sizeof(float4))) == OSC_OK) s->ev = (float4 *)p;
     if (!st && (st = dalloc(ctx, &p, n * 4)) == OSC_OK) s->perm = (int32_t *)p;
     if (st) {
         free_sample(ctx, s);
         return st;
     }
-    cudaError_t e = cudaSuccess;
-    if (!e) e = cudaMemcpy(s->e_true, et.data(), n_pad * 4, cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(s->e_reco, er.data(), n_pad * 4, cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(s->w_mc, w.data(), n_pad * 4, cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(s->chan, cs.data(), n_pad, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(s->ev, rec.data(), n_pad * sizeof(float4), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(s->perm, order.data(), n * 4, cudaMemcpyHostToDevice);
     if (e) {
         free_sample(ctx, s);
         return fail_cuda(ctx, e, "cudaMemcpy(sample)");
     }
     SampleDev &sd = s->dev;
-    sd.e_true = s->e_true;
-    sd.e_reco = s->e_reco;
-    sd.w_mc = s->w_mc;
-    sd.chan = s->chan;
+    sd.ev = s->ev;
     sd.perm = s->perm;
     sd.n = n;
     sd.kA_rhoye = matter_k_A() * s->rho * s->ye;
@@ -513,15 +506,21 @@ osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points) 
         ctx->pts_cap = cap;
     }
     ctx->pts.assign(pts, pts + n_points);
-    CK(cudaMemcpyAsync(ctx->d_pts, ctx->pts.data(), (size_t)n_points * sizeof(osc_point), cudaMemcpyHostToDevice,
-                       ctx->stream));
+    // small tables travel as kernel parameters; larger ones through a copy
+    const bool by_value = n_points <= kPointsByValue;
+    if (!by_value)
+        CK(cudaMemcpyAsync(ctx->d_pts, ctx->pts.data(), (size_t)n_points * sizeof(osc_point), cudaMemcpyHostToDevice,
+                           ctx->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->timing) {
         e0 = pool_event(ctx);
         e1 = pool_event(ctx);
         CK(cudaEventRecord(e0, ctx->stream));
     }
-    CK(launch_point_consts(ctx->d_pts, n_points, ctx->d_pc32, ctx->d_pc64, ctx->stream));
+    if (by_value)
+        CK(launch_point_consts_host(ctx->pts.data(), n_points, ctx->d_pc32, ctx->d_pc64, ctx->stream));
+    else
+        CK(launch_point_consts(ctx->d_pts, n_points, ctx->d_pc32, ctx->d_pc64, ctx->stream));
     ctx->launches += 1;
     if (ctx->timing) {
         CK(cudaEventRecord(e1, ctx->stream));
@@ -749,30 +748,40 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     kf.gridDim = dim3((unsigned)fb);
     kf.blockDim = dim3(256);
     kf.kernelParams = fargs;
+    const bool fused = fuse_finalize(p->n_hist, p->nbins);
+    if (fused) {
+        hp.fuse_final = 1;
+        hp.fin_n_hist = p->n_hist;
+        hp.fin_hmeta = p->d_hmeta;
+        hp.fin_out = d_out;
+    }
     if (!p->exec) {
         CK(cudaGraphCreate(&p->graph, 0));
         CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, nullptr, 0, &kh));
-        CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
+        if (!fused) CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
         CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
     } else {
         CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_hist_node, &kh));
-        CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
+        if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
     }
     if (ctx->timing) {
         // timed mode: plain launches bracketed by events on the context stream
-        cudaEvent_t a = pool_event(ctx), b = pool_event(ctx), d = pool_event(ctx), f = pool_event(ctx);
+        cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
         CK(cudaEventRecord(a, ctx->stream));
         CK(launch_hist(p->prec, p->pt, hp, p->grid, ctx->stream));
         CK(cudaEventRecord(b, ctx->stream));
-        CK(cudaEventRecord(d, ctx->stream));
-        CK(launch_final(fp, ctx->stream));
-        CK(cudaEventRecord(f, ctx->stream));
         ctx->ev_pending.push_back({1, {a, b}});
-        ctx->ev_pending.push_back({2, {d, f}});
+        if (!fused) {
+            cudaEvent_t d = pool_event(ctx), f = pool_event(ctx);
+            CK(cudaEventRecord(d, ctx->stream));
+            CK(launch_final(fp, ctx->stream));
+            CK(cudaEventRecord(f, ctx->stream));
+            ctx->ev_pending.push_back({2, {d, f}});
+        }
     } else {
         CK(cudaGraphLaunch(p->exec, ctx->stream));
     }
-    ctx->launches += 2;
+    ctx->launches += fused ? 1 : 2;
     return OSC_OK;
 }
 

@@ -106,7 +106,7 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     for (int r = 0; r < n; ++r) {
         int s = -1;
         for (int k = 0; k < n_samp; ++k)
-            if (b.h_samples[k].e_true == b.reqs[r].sd.e_true) s = k;
+            if (b.h_samples[k].ev == b.reqs[r].sd.ev) s = k;
         if (s < 0) {
             s = n_samp++;
             b.h_samples[s] = b.reqs[r].sd;
@@ -159,13 +159,18 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     hp.inv_f = (float)((double)sv->nbins / (sv->hi - sv->lo));
     hp.nb_f = (float)sv->nbins;
     hp.hist_stride_pts = 1;
+    const bool fused = fuse_finalize(n, sv->nbins);
+    hp.fuse_final = fused ? 1 : 0;
+    hp.fin_n_hist = n;
+    hp.fin_hmeta = b.d_hmeta;
+    hp.fin_out = b.d_out;
     e = launch_hist(prec, 1, hp, hist_grid(ctx, prec, 1, (n_items + 7) / 8), st);
     FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
-    if (!e) e = launch_final(fp, st);
+    if (!e && !fused) e = launch_final(fp, st);
     if (!e) e = cudaMemcpyAsync(b.h_out, b.d_out, (size_t)n * sv->nbins * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaLaunchHostFunc(st, on_batch_done, cb_arg);
     if (e) return fail_cuda(ctx, e, "serving batch launch");
-    ctx->launches += 3;
+    ctx->launches += fused ? 2 : 3;
     return OSC_OK;
 }
 
