@@ -203,9 +203,14 @@ __device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long lon
 __device__ __forceinline__ void fx_add_f32(unsigned long long &lo, unsigned long long &hi, float w, int sh) {
     const uint32_t u = __float_as_uint(w);
     const int e = (int)((u >> 23) & 0xFFu);
-    const int s = min(e + sh, 40);
-    const unsigned long long m = (unsigned long long)((u & 0x7FFFFFu) | (e ? 0x800000u : 0u));
-    const unsigned long long v = (s >= 0) ? (m << s) : ((s > -24) ? (m >> (-s)) : 0ull);
+    const int s = e + sh;
+    unsigned long long v;
+    if (s >= 0 && s <= 40) {
+        v = (unsigned long long)((u & 0x7FFFFFu) | 0x800000u) << s;  // every normal weight in range
+    } else {
+        const unsigned long long m = (unsigned long long)((u & 0x7FFFFFu) | (e ? 0x800000u : 0u));
+        v = (s > 40) ? (m << 40) : ((s > -24) ? (m >> (-s)) : 0ull);
+    }
     if (u >> 31) {
         asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
     } else {

@@ -55,13 +55,22 @@ struct Ch32 {
     float diag;  // 1 for alpha == beta, else 0
 };
 
+// Approximate reciprocal square root (PTX rsqrt.approx); only seeds use it.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float shifted_newton(float dl, float A, float S, float PI, float W, float E) {
-    // one Newton step on g(delta) = delta^3 + b delta^2 + c delta - e
+    // one Newton step on g(delta) = delta^3 + b delta^2 + c delta - e, with
+    // t = delta (delta + b) + c:  g = t delta - e,  g' = t + delta (2 delta + b)
     const float b = S - A;
     const float c = fmaf(-A, W, PI);
     const float e = A * E;
-    const float g = fmaf(fmaf(dl + b, dl, c), dl, -e);
-    const float gp = fmaf(fmaf(3.0f, dl, b + b), dl, c);
+    const float t = fmaf(dl + b, dl, c);
+    const float g = fmaf(t, dl, -e);
+    const float gp = fmaf(dl, fmaf(2.0f, dl, b), t);
     return fmaf(-g, rcp_approx(gp), dl);
 }
 
@@ -82,7 +91,7 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     const float p = fmaf(fmaf(A, -1.0f / 3.0f, c.p1), A, c.p0);
     const float q = fmaf(fmaf(fmaf(A, -2.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
     const float mp3 = fmaxf(p * (-1.0f / 3.0f), 1e-30f);
-    const float ir = rsqrtf(mp3);
+    const float ir = rsqrt_approx(mp3);
     const float r = mp3 * ir;
     float cth = -0.5f * q * (ir * ir * ir);
     cth = fminf(fmaxf(cth, -1.0f), 1.0f);
@@ -99,29 +108,33 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     const float dl2 = A - dl0 - dl1;  // trace: sum of shifts = A
     const float L0 = c.d0 + dl0, L1 = c.d1 + dl1, L2 = c.d2 + dl2;
     const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
+    // Sylvester coefficients C_l = N_l / D_l; the projectors sum to the identity,
+    // so S = delta_ba + sum_{l=1,2} C_l (e^{-i phi_l} - 1) needs no C_0, and
+    // e^{-i phi} - 1 = -2 sin(phi/2) (sin(phi/2) + i cos(phi/2)) keeps small
+    // phase differences accurate.  The factor -2 is folded into 1/D_l:
+    // D_1 = (L1 - L0)(L1 - L2) = -g01 g12, D_2 = (L2 - L0)(L2 - L1) = g02 g12.
     const float inv = rcp_approx(g01 * g02 * g12);
-    const float iD0 = g12 * inv, iD1 = -g02 * inv, iD2 = g01 * inv;
-    // Sylvester numerators
+    const float iD1 = 2.0f * g02 * inv, iD2 = -2.0f * g01 * inv;
     const float TA = c.T0 + A;
     const float c1 = fmaf(A, c.smt, c.c10);
     const float Kr = fmaf(A, fmaf(A, h.ee, h.Zr), h.Yr), Ki = fmaf(A, h.Zi, h.Yi);
     const float Gr = fmaf(A, h.ee, h.Xr), Gi = h.Xi;
     float sg, pp;
-    sg = TA - L0; pp = fmaf(-L0, sg, c1);
-    const float C0r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD0, C0i = fmaf(-sg, Gi, Ki) * iD0;
     sg = TA - L1; pp = fmaf(-L1, sg, c1);
     const float C1r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD1, C1i = fmaf(-sg, Gi, Ki) * iD1;
     sg = TA - L2; pp = fmaf(-L2, sg, c1);
     const float C2r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD2, C2i = fmaf(-sg, Gi, Ki) * iD2;
-    // phases relative to root 0
+    (void)L0;
+    // half phases relative to root 0, in radians: pi * revolutions
     const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dl1 - dl0);
     const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dl2 - dl0);
     float s1, k1, s2, k2;
-    __sincosf(6.28318530717958647692f * f1, &s1, &k1);
-    __sincosf(6.28318530717958647692f * f2, &s2, &k2);
-    // S = C0 + C1 e^{-i phi1} + C2 e^{-i phi2}
-    const float Sr = C0r + fmaf(C1r, k1, C1i * s1) + fmaf(C2r, k2, C2i * s2);
-    const float Si = C0i + fmaf(C1i, k1, -C1r * s1) + fmaf(C2i, k2, -C2r * s2);
+    __sincosf(3.14159265358979323846f * f1, &s1, &k1);
+    __sincosf(3.14159265358979323846f * f2, &s2, &k2);
+    const float a1 = s1 * s1, b1 = s1 * k1, a2 = s2 * s2, b2 = s2 * k2;
+    // S = delta_ba + sum_l C'_l (a_l + i b_l), C'_l = -2 C_l
+    const float Sr = h.diag + fmaf(C1r, a1, -C1i * b1) + fmaf(C2r, a2, -C2i * b2);
+    const float Si = fmaf(C1r, b1, C1i * a1) + fmaf(C2r, b2, C2i * a2);
     return fmaf(Sr, Sr, Si * Si);
 }
 
