@@ -87,9 +87,10 @@ struct HistParams {
 
 // Points passed to the constants kernel by value (no host-to-device copy).
 constexpr int kPointsByValue = 256;
-struct PointsByValue {
+template <int N>
+struct PointsByValueT {
     int32_t n;
-    osc_point p[kPointsByValue];
+    osc_point p[N];
 };
 
 struct FinalParams {

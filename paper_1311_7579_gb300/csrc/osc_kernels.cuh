@@ -36,32 +36,32 @@ __device__ __forceinline__ void split_ff(double v, float *hi, float *lo) {
     *lo = (float)(v - (double)h);
 }
 
-// One warp per point.  The FP64 work is spread over lanes so that its
-// dependent chain stays short: lanes 0-6 form the six square roots and the
-// sine/cosine of delta; lanes 0-8 each form one entry of H0 = U diag(m) U^dagger
-// and of H0^2, shared through shuffles; then lane 9 writes the cubic
-// coefficients, lane 10 the sorted vacuum spectrum and shifted-cubic constants,
-// lane 11 the systematics, and lanes 0-8 one channel each.
-__device__ inline void point_consts_warp(const osc_point &P, float *c32, double *c64, int lane) {
-    double tv = 0.0;
-    if (lane < 6) {
+// One block of three warps per point.  Independent FP64 chains run on different
+// warps so that they overlap (divergent lanes of one warp would serialise):
+//   1. warp 0 lanes 0-5: the six square roots | warp 1: sine/cosine of delta
+//   2. warp 0 lanes 0-8: one entry each of H0 = U diag(m) U^dagger and H0^2
+//      | warp 1: sorted vacuum spectrum, |U_e|^2 and shifted-cubic constants
+//      | warp 2: trace, c1(0) and the systematics
+//   3. warp 0 lanes 0-8: one channel each | warp 2: depressed-cubic coefficients
+constexpr int kConstThreads = 96;
+__device__ inline void point_consts_block(const osc_point &P, float *c32, double *c64) {
+    __shared__ double t[8];
+    __shared__ double Hs[4][9];  // H re, H im, H2 re, H2 im, entry (b, a) at 3 b + a
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0 && lane < 6) {
         const double x = (lane == 0) ? P.s2_12 : (lane == 1) ? 1.0 - P.s2_12 : (lane == 2) ? P.s2_13
                        : (lane == 3) ? 1.0 - P.s2_13 : (lane == 4) ? P.s2_23 : 1.0 - P.s2_23;
-        tv = sqrt(x);
+        t[lane] = sqrt(x);
     }
-    double sd = 0.0, cd = 0.0;
-    if (lane == 6) sincos(P.dcp, &sd, &cd);
-    const double s12 = __shfl_sync(0xffffffffu, tv, 0), c12 = __shfl_sync(0xffffffffu, tv, 1);
-    const double s13 = __shfl_sync(0xffffffffu, tv, 2), c13 = __shfl_sync(0xffffffffu, tv, 3);
-    const double s23 = __shfl_sync(0xffffffffu, tv, 4), c23 = __shfl_sync(0xffffffffu, tv, 5);
-    sd = __shfl_sync(0xffffffffu, sd, 6);
-    cd = __shfl_sync(0xffffffffu, cd, 6);
+    if (warp == 1 && lane == 0) sincos(P.dcp, &t[6], &t[7]);
+    __syncthreads();
+    const double s12 = t[0], c12 = t[1], s13 = t[2], c13 = t[3], s23 = t[4], c23 = t[5], sd = t[6], cd = t[7];
     const double dm21 = P.dm21, dm31 = P.dm32 + P.dm21;
-    // H0 and H0^2 entries [beta][alpha]; lane l < 9 forms entry (l / 3, l % 3) from
-    // columns 1, 2 of the PDG PMNS rows it needs (U_e3 = s13 e^{-i delta},
-    // e^{+i delta} in the mu and tau rows; column 0 carries m = 0)
-    cplx64 h = {0, 0}, h2 = {0, 0};
-    if (lane < 9) {
+    const double T0 = dm21 + dm31;
+    const double c10 = dm21 * dm31;
+    if (warp == 0 && lane < 9) {
+        // columns 1, 2 of the PDG PMNS rows needed (U_e3 = s13 e^{-i delta},
+        // e^{+i delta} in the mu and tau rows; column 0 carries m = 0)
         const int b = lane / 3, a = lane % 3;
         cplx64 Ub[3], Ua[3];
         for (int side = 0; side < 2; ++side) {
@@ -79,37 +79,15 @@ __device__ inline void point_consts_warp(const osc_point &P, float *c32, double 
             }
         }
         const double m[3] = {0.0, dm21, dm31};
+        cplx64 h = {0, 0}, h2 = {0, 0};
         for (int k = 1; k < 3; ++k) {
-            const cplx64 t = cmul_conj(Ub[k], m[k], Ua[k]);
-            h.re += t.re; h.im += t.im;
-            h2.re += t.re * m[k]; h2.im += t.im * m[k];
+            const cplx64 q = cmul_conj(Ub[k], m[k], Ua[k]);
+            h.re += q.re; h.im += q.im;
+            h2.re += q.re * m[k]; h2.im += q.im * m[k];
         }
+        Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
     }
-    cplx64 H[3][3], H2[3][3];
-    for (int j = 0; j < 9; ++j) {
-        H[j / 3][j % 3] = {__shfl_sync(0xffffffffu, h.re, j), __shfl_sync(0xffffffffu, h.im, j)};
-        H2[j / 3][j % 3] = {__shfl_sync(0xffffffffu, h2.re, j), __shfl_sync(0xffffffffu, h2.im, j)};
-    }
-    const double T0 = dm21 + dm31;
-    const double c10 = dm21 * dm31;
-    if (lane == 9) {
-        // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
-        //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee
-        constexpr double k3 = 1.0 / 3.0, k9 = 1.0 / 9.0, k27 = 1.0 / 27.0;
-        const double smt = H[1][1].re + H[2][2].re;
-        const double mee = H[1][1].re * H[2][2].re - (H[1][2].re * H[1][2].re + H[1][2].im * H[1][2].im);
-        const double p0 = c10 - T0 * T0 * k3, p1 = smt - 2.0 * T0 * k3;
-        const double q0 = -2.0 * T0 * T0 * T0 * k27 + c10 * T0 * k3;
-        const double q1 = -2.0 * T0 * T0 * k9 + c10 * k3 + smt * T0 * k3 - mee;
-        const double q2 = -2.0 * T0 * k9 + smt * k3;
-        c32[C32_P0] = (float)p0; c32[C32_P1] = (float)p1;
-        c32[C32_Q0] = (float)q0; c32[C32_Q1] = (float)q1; c32[C32_Q2] = (float)q2;
-        c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10; c32[C32_SMT] = (float)smt;
-        c64[C64_P0] = p0; c64[C64_P1] = p1; c64[C64_Q0] = q0; c64[C64_Q1] = q1; c64[C64_Q2] = q2;
-        c64[C64_T0] = T0; c64[C64_C10] = c10; c64[C64_SMT] = smt;
-    }
-    if (lane == 10) {
-        // sorted vacuum spectrum and |U_e|^2 in the same order
+    if (warp == 1 && lane == 0) {
         const double ze[3] = {c12 * c12 * c13 * c13, s12 * s12 * c13 * c13, s13 * s13};
         double d[3], z[3];
         if (dm31 > 0) {
@@ -119,40 +97,58 @@ __device__ inline void point_consts_warp(const osc_point &P, float *c32, double 
             d[0] = dm31; d[1] = 0.0; d[2] = dm21;
             z[0] = ze[2]; z[1] = ze[0]; z[2] = ze[1];
         }
-        double S[2], PI[2], W[2], E[2];
         for (int l = 0; l < 2; ++l) {
             const int j = (l + 1) % 3, k = (l + 2) % 3;
             const double aj = d[l] - d[j], ak = d[l] - d[k];
-            S[l] = aj + ak;
-            PI[l] = aj * ak;
-            W[l] = z[l] * (aj + ak) + z[j] * ak + z[k] * aj;
-            E[l] = z[l] * aj * ak;
+            const int o = l ? (C32_S1 - C32_S0) : 0;
+            c32[C32_S0 + o] = (float)(aj + ak);
+            c32[C32_PI0 + o] = (float)(aj * ak);
+            c32[C32_W0 + o] = (float)(z[l] * (aj + ak) + z[j] * ak + z[k] * aj);
+            c32[C32_E0 + o] = (float)(z[l] * aj * ak);
         }
         c32[C32_D0] = (float)d[0]; c32[C32_D1] = (float)d[1]; c32[C32_D2] = (float)d[2];
         c32[C32_G01] = (float)(d[0] - d[1]); c32[C32_G02] = (float)(d[0] - d[2]); c32[C32_G12] = (float)(d[1] - d[2]);
         split_ff(d[1] - d[0], &c32[C32_V1H], &c32[C32_V1L]);
         split_ff(d[2] - d[0], &c32[C32_V2H], &c32[C32_V2L]);
-        c32[C32_S0] = (float)S[0]; c32[C32_PI0] = (float)PI[0]; c32[C32_W0] = (float)W[0]; c32[C32_E0] = (float)E[0];
-        c32[C32_S1] = (float)S[1]; c32[C32_PI1] = (float)PI[1]; c32[C32_W1] = (float)W[1]; c32[C32_E1] = (float)E[1];
     }
-    if (lane == 11) {
+    if (warp == 2 && lane == 0) {
+        c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10;
+        c64[C64_T0] = T0; c64[C64_C10] = c10;
         c32[C32_ESCALE] = (float)P.escale;
         c64[C64_ESCALE] = P.escale;
         c64[C64_NORM] = P.norm;
     }
-    // channel (alpha -> beta) = lane (alpha * 3 + beta):
-    // X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
-    if (lane < 9) {
+    __syncthreads();
+    if (warp == 0 && lane < 9) {
+        // channel (alpha -> beta) = lane (alpha * 3 + beta):
+        // X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
         const int a = lane / 3, b = lane % 3;
         const int o = 6 * lane;
         double Zr = 0, Zi = 0;
-        if (a == 0) { Zr += H[b][0].re; Zi += H[b][0].im; }
-        if (b == 0) { Zr += H[0][a].re; Zi += H[0][a].im; }
-        const double v[6] = {H[b][a].re, H[b][a].im, H2[b][a].re, H2[b][a].im, Zr, Zi};
-        for (int t = 0; t < 6; ++t) {
-            c32[C32_CH + o + t] = (float)v[t];
-            c64[C64_CH + o + t] = v[t];
+        if (a == 0) { Zr += Hs[0][3 * b]; Zi += Hs[1][3 * b]; }
+        if (b == 0) { Zr += Hs[0][a]; Zi += Hs[1][a]; }
+        const int ba = 3 * b + a;
+        const double v[6] = {Hs[0][ba], Hs[1][ba], Hs[2][ba], Hs[3][ba], Zr, Zi};
+        for (int k = 0; k < 6; ++k) {
+            c32[C32_CH + o + k] = (float)v[k];
+            c64[C64_CH + o + k] = v[k];
         }
+    }
+    if (warp == 2 && lane == 0) {
+        // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
+        //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee
+        constexpr double k3 = 1.0 / 3.0, k9 = 1.0 / 9.0, k27 = 1.0 / 27.0;
+        const double smt = Hs[0][4] + Hs[0][8];
+        const double mee = Hs[0][4] * Hs[0][8] - (Hs[0][5] * Hs[0][5] + Hs[1][5] * Hs[1][5]);
+        const double p0 = c10 - T0 * T0 * k3, p1 = smt - 2.0 * T0 * k3;
+        const double q0 = -2.0 * T0 * T0 * T0 * k27 + c10 * T0 * k3;
+        const double q1 = -2.0 * T0 * T0 * k9 + c10 * k3 + smt * T0 * k3 - mee;
+        const double q2 = -2.0 * T0 * k9 + smt * k3;
+        c32[C32_P0] = (float)p0; c32[C32_P1] = (float)p1;
+        c32[C32_Q0] = (float)q0; c32[C32_Q1] = (float)q1; c32[C32_Q2] = (float)q2;
+        c32[C32_SMT] = (float)smt;
+        c64[C64_P0] = p0; c64[C64_P1] = p1; c64[C64_Q0] = q0; c64[C64_Q1] = q1; c64[C64_Q2] = q2;
+        c64[C64_SMT] = smt;
     }
 }
 

@@ -3,19 +3,19 @@
 
 namespace osc {
 
-__global__ void k_point_consts(const osc_point *pts, int n, float *pc32, double *pc64) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;  // whole warps
-    point_consts_warp(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE, threadIdx.x & 31);
+__global__ void __launch_bounds__(kConstThreads) k_point_consts(const osc_point *pts, int n, float *pc32, double *pc64) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    point_consts_block(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
 }
 
-__global__ void k_point_consts_v(const PointsByValue pv, float *pc32, double *pc64) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+template <int N>
+__global__ void __launch_bounds__(kConstThreads) k_point_consts_v(const PointsByValueT<N> pv, float *pc32, double *pc64) {
+    const int i = blockIdx.x;
     if (i >= pv.n) return;
-    point_consts_warp(pv.p[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE, threadIdx.x & 31);
+    point_consts_block(pv.p[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
 }
 
-// ---------------------------------------------------------------- finalize
 __global__ void k_final(const FinalParams f) {
     const int64_t n = f.n_hist * (int64_t)f.nbins;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -44,17 +44,23 @@ const void *hist_kernel_fn(int prec, int pt) {
 const void *final_kernel_fn() { return (const void *)k_final; }
 
 cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
-    k_point_consts<<<(n + 3) / 4, 128, 0, st>>>(d_pts, n, pc32, pc64);
+    k_point_consts<<<n, kConstThreads, 0, st>>>(d_pts, n, pc32, pc64);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_by_value(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
+    PointsByValueT<N> pv;
+    pv.n = n;
+    for (int i = 0; i < n; ++i) pv.p[i] = h_pts[i];
+    k_point_consts_v<N><<<n, kConstThreads, 0, st>>>(pv, pc32, pc64);
     return cudaGetLastError();
 }
 
 cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
     if (n < 1 || n > kPointsByValue) return cudaErrorInvalidValue;
-    PointsByValue pv;
-    pv.n = n;
-    for (int i = 0; i < n; ++i) pv.p[i] = h_pts[i];
-    k_point_consts_v<<<(n + 3) / 4, 128, 0, st>>>(pv, pc32, pc64);
-    return cudaGetLastError();
+    // a small parameter block launches faster than the full one
+    return n <= 8 ? launch_by_value<8>(h_pts, n, pc32, pc64, st) : launch_by_value<kPointsByValue>(h_pts, n, pc32, pc64, st);
 }
 
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st) {

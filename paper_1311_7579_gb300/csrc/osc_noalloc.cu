@@ -45,8 +45,8 @@ struct NoAllocParams {
     NoAllocScratch *s;
 };
 
-__global__ void k_noalloc_consts(osc_point P, NoAllocScratch *s) {
-    if (blockIdx.x == 0 && threadIdx.x < 32) point_consts_warp(P, s->pc32, s->pc64, threadIdx.x);
+__global__ void __launch_bounds__(kConstThreads) k_noalloc_consts(osc_point P, NoAllocScratch *s) {
+    point_consts_block(P, s->pc32, s->pc64);
 }
 
 // Same per-warp scheme as the one-point histogram path, over events in the
@@ -237,7 +237,7 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
         put_err(err, err_len, "cudaMemsetAsync on the scratch array failed");
         return OSC_E_CUDA;
     }
-    k_noalloc_consts<<<1, 32, 0, st>>>(P, s);
+    k_noalloc_consts<<<1, kConstThreads, 0, st>>>(P, s);
     if (prec == OSC_FP32_BULK)
         k_noalloc_hist<kFP32><<<grid, kNT, 0, st>>>(p);
     else
