@@ -146,8 +146,8 @@ osc_status osc_set_tile(osc_ctx *ctx, int32_t points_per_block, int32_t events_p
 
 /* Enable (1) / disable (0) CUDA-event timing of each kernel.  Events are
  * recorded on the context stream around every constants, histogram and
- * finalize kernel without any host synchronisation (launches then bypass the
- * CUDA graph).  osc_last_timing waits for the recorded events and reports the
+ * finalize kernel without any host synchronisation (the histogram step runs as
+ * the same CUDA graph, with event-record nodes around its kernels).  osc_last_timing waits for the recorded events and reports the
  * durations (ms) of the most recent kernel of each kind (negative when none);
  * osc_timing_totals waits, returns the launch counts and summed durations of
  * each kind since the last totals call (index 0 constants, 1 histogram,

@@ -41,6 +41,10 @@ struct Plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t n_hist_node = nullptr, n_final_node = nullptr;
+    // the same step with event-record nodes around each kernel (timing mode)
+    cudaGraph_t graph_t = nullptr;
+    cudaGraphExec_t exec_t = nullptr;
+    cudaGraphNode_t t_hist_node = nullptr, t_final_node = nullptr, t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     uint64_t last_use = 0;
 };
 

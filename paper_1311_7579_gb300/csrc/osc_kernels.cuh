@@ -419,16 +419,18 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
         unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
         RunAcc r{0ull, 0ull, -1};
         int cur_ch = -1;
-        const int64_t end = wi.ev_begin + wi.ev_count;
-        int64_t e = wi.ev_begin + lane;
+        // 32-bit offsets within the item (items hold fewer than 2^31 events)
+        const float4 *ev = sd.ev + wi.ev_begin;
+        const int end = wi.ev_count;
+        int e = lane;
         float Ea = 1.0f, ra = 0.0f, wa = 0.0f, Eb = 1.0f, rb = 0.0f, wb = 0.0f;
         int ca = 0, cb = 0;
         if (e < end) {
-            const float4 q = sd.ev[e];
+            const float4 q = ev[e];
             Ea = q.x; ra = q.y; wa = q.z; ca = __float_as_int(q.w);
         }
         if (e + 32 < end) {
-            const float4 q = sd.ev[e + 32];
+            const float4 q = ev[e + 32];
             Eb = q.x; rb = q.y; wb = q.z; cb = __float_as_int(q.w);
         }
         if (PREC == kFP32) {
@@ -440,15 +442,15 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             const int sh = sd.frac_bits - 150;
             for (; e < end; e += 64) {
                 const bool has_b = e + 32 < end;
-                const int64_t en = e + 64;
+                const int en = e + 64;
                 float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
                 int cna = 0, cnb = 0;
                 if (en < end) {
-                    const float4 q = sd.ev[en];
+                    const float4 q = ev[en];
                     Ena = q.x; rna = q.y; wna = q.z; cna = __float_as_int(q.w);
                 }
                 if (en + 32 < end) {
-                    const float4 q = sd.ev[en + 32];
+                    const float4 q = ev[en + 32];
                     Enb = q.x; rnb = q.y; wnb = q.z; cnb = __float_as_int(q.w);
                 }
                 if (ca == cur_ch && (!has_b || cb == cur_ch)) {
@@ -486,15 +488,15 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             const double hs = sd.hscale_d;
             for (; e < end; e += 64) {
                 const bool has_b = e + 32 < end;
-                const int64_t en = e + 64;
+                const int en = e + 64;
                 float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
                 int cna = 0, cnb = 0;
                 if (en < end) {
-                    const float4 q = sd.ev[en];
+                    const float4 q = ev[en];
                     Ena = q.x; rna = q.y; wna = q.z; cna = __float_as_int(q.w);
                 }
                 if (en + 32 < end) {
-                    const float4 q = sd.ev[en + 32];
+                    const float4 q = ev[en + 32];
                     Enb = q.x; rnb = q.y; wnb = q.z; cnb = __float_as_int(q.w);
                 }
                 for (int k = 0; k < 2; ++k) {

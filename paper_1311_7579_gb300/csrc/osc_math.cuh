@@ -43,6 +43,26 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// arccos on [-1, 1] from Abramowitz & Stegun, Handbook of Mathematical
+// Functions, formula 4.4.46: acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7)
+// for 0 <= x <= 1 with |error| <= 2e-8, and acos(-x) = pi - acos(x).  Branch-free;
+// it only seeds the Newton-refined eigenvalues, which need ~1e-5 relative accuracy.
+__device__ __forceinline__ float acos_seed(float x) {
+    const float ax = fabsf(x);
+    float p = -0.0012624911f;
+    p = fmaf(p, ax, 0.0066700901f);
+    p = fmaf(p, ax, -0.0170881256f);
+    p = fmaf(p, ax, 0.0308918810f);
+    p = fmaf(p, ax, -0.0501743046f);
+    p = fmaf(p, ax, 0.0889789874f);
+    p = fmaf(p, ax, -0.2145988016f);
+    p = fmaf(p, ax, 1.5707963050f);
+    float sq;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(1.0f - ax));
+    const float r = sq * p;
+    return x < 0.0f ? 3.14159265358979323846f - r : r;
+}
+
 struct Pt32 {
     float p0, p1, q0, q1, q2, T0, c10, smt;
     float d0, d1, d2, g01, g02, g12;
@@ -95,7 +115,7 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     const float r = mp3 * ir;
     float cth = -0.5f * q * (ir * ir * ir);
     cth = fminf(fmaxf(cth, -1.0f), 1.0f);
-    const float th3 = acosf(cth) * (1.0f / 3.0f);
+    const float th3 = acos_seed(cth) * (1.0f / 3.0f);
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;

@@ -271,6 +271,8 @@ static void free_sample(osc_ctx *c, Sample *s) {
 static void free_plan(osc_ctx *c, Plan *p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->exec_t) cudaGraphExecDestroy(p->exec_t);
+    if (p->graph_t) cudaGraphDestroy(p->graph_t);
     dfree(c, p->d_items);
     dfree(c, p->d_samples);
     dfree(c, p->d_hmeta);
@@ -755,31 +757,44 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
         hp.fin_hmeta = p->d_hmeta;
         hp.fin_out = d_out;
     }
-    if (!p->exec) {
-        CK(cudaGraphCreate(&p->graph, 0));
-        CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, nullptr, 0, &kh));
-        if (!fused) CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
-        CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
-    } else {
-        CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_hist_node, &kh));
-        if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
-    }
-    if (ctx->timing) {
-        // timed mode: plain launches bracketed by events on the context stream
-        cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
-        CK(cudaEventRecord(a, ctx->stream));
-        CK(launch_hist(p->prec, p->pt, hp, p->grid, ctx->stream));
-        CK(cudaEventRecord(b, ctx->stream));
-        ctx->ev_pending.push_back({1, {a, b}});
-        if (!fused) {
-            cudaEvent_t d = pool_event(ctx), f = pool_event(ctx);
-            CK(cudaEventRecord(d, ctx->stream));
-            CK(launch_final(fp, ctx->stream));
-            CK(cudaEventRecord(f, ctx->stream));
-            ctx->ev_pending.push_back({2, {d, f}});
+    if (!ctx->timing) {
+        if (!p->exec) {
+            CK(cudaGraphCreate(&p->graph, 0));
+            CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, nullptr, 0, &kh));
+            if (!fused) CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
+            CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
+        } else {
+            CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_hist_node, &kh));
+            if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
         }
-    } else {
         CK(cudaGraphLaunch(p->exec, ctx->stream));
+    } else {
+        // timing mode: the same graph with event-record nodes around each kernel,
+        // fresh events swapped in per launch (read later without blocking the stream)
+        cudaEvent_t ev[4] = {pool_event(ctx), pool_event(ctx), nullptr, nullptr};
+        if (!fused) {
+            ev[2] = pool_event(ctx);
+            ev[3] = pool_event(ctx);
+        }
+        if (!p->exec_t) {
+            CK(cudaGraphCreate(&p->graph_t, 0));
+            CK(cudaGraphAddEventRecordNode(&p->t_ev[0], p->graph_t, nullptr, 0, ev[0]));
+            CK(cudaGraphAddKernelNode(&p->t_hist_node, p->graph_t, &p->t_ev[0], 1, &kh));
+            CK(cudaGraphAddEventRecordNode(&p->t_ev[1], p->graph_t, &p->t_hist_node, 1, ev[1]));
+            if (!fused) {
+                CK(cudaGraphAddEventRecordNode(&p->t_ev[2], p->graph_t, &p->t_ev[1], 1, ev[2]));
+                CK(cudaGraphAddKernelNode(&p->t_final_node, p->graph_t, &p->t_ev[2], 1, &kf));
+                CK(cudaGraphAddEventRecordNode(&p->t_ev[3], p->graph_t, &p->t_final_node, 1, ev[3]));
+            }
+            CK(cudaGraphInstantiate(&p->exec_t, p->graph_t, 0));
+        } else {
+            CK(cudaGraphExecKernelNodeSetParams(p->exec_t, p->t_hist_node, &kh));
+            if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec_t, p->t_final_node, &kf));
+            for (int k = 0; k < (fused ? 2 : 4); ++k) CK(cudaGraphExecEventRecordNodeSetEvent(p->exec_t, p->t_ev[k], ev[k]));
+        }
+        CK(cudaGraphLaunch(p->exec_t, ctx->stream));
+        ctx->ev_pending.push_back({1, {ev[0], ev[1]}});
+        if (!fused) ctx->ev_pending.push_back({2, {ev[2], ev[3]}});
     }
     ctx->launches += fused ? 1 : 2;
     return OSC_OK;
