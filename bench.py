@@ -234,6 +234,28 @@ def serving_leg(api, synth, c, rates, seconds, prec="fp32"):
     return out
 
 
+def mcmc_leg(api, synth, c, sid, sample, n_steps, prec="fp32"):
+    """Toy fit (Sec. 2.2): Metropolis-Hastings over (sin^2 theta23, dm32) on the
+    bench sample, each step one set_params + histogram + Eq. (2) likelihood on the
+    host.  Reports the steps per second of the whole fit loop (wall clock)."""
+    from paper_1311_7579_gb300 import fit
+    expo = fit.exposure_for(sample, 20000, LO, HI)
+    truth = fit.ToyFit(c, sid, np.zeros(NBINS), expo, LO, HI, NBINS, "fp64")
+    data = fit.fake_data(truth.expected(np.array([0.5, 2.4e-3])), seed=92)
+    f = fit.ToyFit(c, sid, data, expo, LO, HI, NBINS, prec)
+    lower, upper = np.array([0.3, 2.0e-3]), np.array([0.7, 3.0e-3])
+    fit.metropolis(f.loglike, [0.45, 2.3e-3], [0.02, 3e-5], 20, np.random.default_rng(1), lower, upper)
+    t0 = time.perf_counter()
+    chain, _, acc = fit.metropolis(f.loglike, [0.45, 2.3e-3], [0.02, 3e-5], n_steps, np.random.default_rng(2),
+                                   lower, upper)
+    dt = time.perf_counter() - t0
+    post = chain[n_steps // 5:]
+    return {"prec": prec, "steps": n_steps, "steps_per_s": n_steps / dt, "ms_per_step": 1e3 * dt / n_steps,
+            "events_per_step": int(sample["n"]), "acceptance": acc,
+            "posterior_mean": [float(x) for x in post.mean(axis=0)],
+            "posterior_sd": [float(x) for x in post.std(axis=0)]}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -387,6 +409,7 @@ def run_ours(args):
             # bin-wise relative error of the full-sample histograms, FP32 vs FP64 GPU path
             nz = h64 != 0
             prec_study["fp32_vs_fp64_hist_max_rel"] = float(np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
+        mcmc = mcmc_leg(api, synth, c, sid, sample, args.mcmc_steps) if args.mcmc_steps > 0 else None
         serving = None
         if args.serve_seconds > 0:
             serving = {"fp32": serving_leg(api, synth, c, (2000, 10000, 20000), args.serve_seconds, "fp32"),
@@ -419,6 +442,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "serving": serving,
+            "mcmc": mcmc,
         }
         print(json.dumps(result), flush=True)
     ctx.close()
@@ -463,6 +487,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-events", type=int, default=N_EVENTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mcmc-steps", type=int, default=2000, help="toy-fit steps (0 skips)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds per offered rate of the serving leg (0 skips it)")
     ap.add_argument("--profile", action="store_true", help="run the small ncu profiling case and exit")
