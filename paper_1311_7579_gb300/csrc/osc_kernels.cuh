@@ -273,6 +273,33 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
     }
 }
 
+// Per-warp variant for one-point items: every warp fences its lanes' flushes and
+// takes a completion ticket; the last warp of the grid converts the bins, so
+// warps that finish early exit without waiting at a block barrier.
+__device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
+    const int lane = threadIdx.x & 31;
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = (atomicAdd(prm.counter + 1, 1) == (int)(gridDim.x * (blockDim.x >> 5)) - 1);
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
+    for (int64_t i = lane; i < n; i += 32) {
+        const unsigned long long d0 = __ldcg(prm.acc + 3 * i), d1 = __ldcg(prm.acc + 3 * i + 1),
+                                 d2 = __ldcg(prm.acc + 3 * i + 2);
+        prm.acc[3 * i] = 0ull;
+        prm.acc[3 * i + 1] = 0ull;
+        prm.acc[3 * i + 2] = 0ull;
+        prm.fin_out[i] = final_bin(d0, d1, d2, prm.fin_hmeta + 4 * (i / prm.nbins), prm.pc64);
+    }
+    if (lane == 0) {
+        prm.counter[0] = 0;
+        prm.counter[1] = 0;
+    }
+}
+
 // Bin one weighted event under the point's energy scale and add it to the lane's
 // run-length accumulator (flushing the previous bin when the bin changes).
 struct RunAcc {
@@ -344,11 +371,8 @@ __device__ __forceinline__ void event_terms32(const SampleDev &sd, float E, int 
     // 1/E = r0 + rl to ~1e-14: the residual 1 - E r0 of the approximate reciprocal is exact in FP32
     const float r0 = rcp_approx(E);
     const float rl = r0 * fmaf(-E, r0, 1.0f);
-    th = sd.rev_hi * r0;
+    th = sd.rev_hi * r0;  // |tl| stays below ulp(th): no renormalisation needed
     tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
-    const float sum = th + tl;
-    tl = tl - (sum - th);
-    th = sum;
 }
 
 // ------------------------------------------------------------ event staging
@@ -405,20 +429,51 @@ __device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const S
 // warp takes work items on its own (no block barriers) and each lane reads its
 // events straight from global memory -- events ev_begin + lane + 32 k, coalesced
 // across the warp -- two per iteration for instruction-level parallelism, with
-// the next two prefetched into registers.
+// the next two prefetched into registers.  The ticket of the warp's next item is
+// fetched a whole item ahead, and the sample scalars and point constants are
+// reloaded only when the item's sample or point changes.
 template <int PREC>
 __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(prm.counter, 1);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= prm.n_items) return;
+    // prefetch a second ticket only when items are plentiful (a warp holding two
+    // tickets of a scarce list would leave other warps idle)
+    const bool ahead = prm.n_items >= 3 * (int)(gridDim.x * (blockDim.x >> 5));
+    int it = 0, nxt = 0;
+    if (lane == 0) {
+        it = atomicAdd(prm.counter, 1);
+        if (ahead) nxt = atomicAdd(prm.counter, 1);
+    }
+    it = __shfl_sync(0xffffffffu, it, 0);
+    int cur_sample = -1, cur_point = -1, cur_ch = -1;
+    SampleDev sd;
+    Pt32 c32;
+    Ch32 h32;
+    Pt64 c64;
+    Ch64 h64;
+    const float *pc32 = nullptr;
+    const double *pc64 = nullptr;
+    float sf = 1.0f;
+    while (it < prm.n_items) {
         const WorkItem wi = prm.items[it];
-        const SampleDev sd = prm.samples[wi.sample];
+        if (wi.sample != cur_sample) {
+            cur_sample = wi.sample;
+            sd = prm.samples[wi.sample];
+        }
+        if (wi.point_base != cur_point) {
+            cur_point = wi.point_base;
+            cur_ch = -1;
+            if (PREC == kFP32) {
+                pc32 = prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
+                load_pt32(pc32, c32);
+                sf = pc32[C32_ESCALE];
+            } else {
+                pc64 = prm.pc64 + (int64_t)wi.point_base * C64_STRIDE;
+                load_pt64(pc64, c64);
+                sf = (float)pc64[C64_ESCALE];
+            }
+        }
         unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
         RunAcc r{0ull, 0ull, -1};
-        int cur_ch = -1;
         // 32-bit offsets within the item (items hold fewer than 2^31 events)
         const float4 *ev = sd.ev + wi.ev_begin;
         const int end = wi.ev_count;
@@ -434,11 +489,6 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             Eb = q.x; rb = q.y; wb = q.z; cb = __float_as_int(q.w);
         }
         if (PREC == kFP32) {
-            const float *pc = prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
-            Pt32 c;
-            load_pt32(pc, c);
-            Ch32 h;
-            const float sf = pc[C32_ESCALE];
             const int sh = sd.frac_bits - 150;
             for (; e < end; e += 64) {
                 const bool has_b = e + 32 < end;
@@ -457,8 +507,8 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                     float Aa, tha, tla, Ab, thb, tlb;
                     event_terms32(sd, Ea, ca, Aa, tha, tla);
                     event_terms32(sd, Eb, cb, Ab, thb, tlb);
-                    const float Pa = prob_fp32(c, h, Aa, tha, tla);
-                    const float Pb = prob_fp32(c, h, Ab, thb, tlb);
+                    const float Pa = prob_fp32(c32, h32, Aa, tha, tla);
+                    const float Pb = prob_fp32(c32, h32, Ab, thb, tlb);
                     acc_event_f32(r, accp, prm, sf, ra, Pa * wa, sh, true);
                     acc_event_f32(r, accp, prm, sf, rb, Pb * wb, sh, has_b);
                 } else {
@@ -468,11 +518,11 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                         if (k && !has_b) break;
                         if (ch != cur_ch) {
                             cur_ch = ch;
-                            load_ch32(pc, ch, h);
+                            load_ch32(pc32, ch, h32);
                         }
                         float A, th, tl;
                         event_terms32(sd, E, ch, A, th, tl);
-                        const float P = prob_fp32(c, h, A, th, tl);
+                        const float P = prob_fp32(c32, h32, A, th, tl);
                         acc_event_f32(r, accp, prm, sf, er, P * w, sh, true);
                     }
                 }
@@ -480,11 +530,6 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
             }
         } else {
-            const double *pc = prm.pc64 + (int64_t)wi.point_base * C64_STRIDE;
-            Pt64 c;
-            load_pt64(pc, c);
-            Ch64 h;
-            const float sf = (float)pc[C64_ESCALE];
             const double hs = sd.hscale_d;
             for (; e < end; e += 64) {
                 const bool has_b = e + 32 < end;
@@ -505,10 +550,10 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                     if (k && !has_b) break;
                     if (ch != cur_ch) {
                         cur_ch = ch;
-                        load_ch64(pc, ch, h);
+                        load_ch64(pc64, ch, h64);
                     }
                     const double Ad = sd.kA_rhoye * (double)E;
-                    const double P = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+                    const double P = prob_fp64(c64, h64, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
                     acc_event_f64(r, accp, prm, sf, er, P * (double)w, hs, true);
                 }
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
@@ -516,6 +561,15 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             }
         }
         acc_finish_warp(r, accp);
+        // move to the ticket fetched an item ago and fetch the one after it, or
+        // (few items) take the next ticket now
+        if (ahead) {
+            it = __shfl_sync(0xffffffffu, nxt, 0);
+            if (lane == 0 && it < prm.n_items) nxt = atomicAdd(prm.counter, 1);
+        } else {
+            if (lane == 0) it = atomicAdd(prm.counter, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+        }
     }
 }
 
@@ -529,7 +583,7 @@ template <int PREC, int PT>
 __global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const HistParams prm) {
     if constexpr (PT == 1) {
         hist_items_per_warp<PREC>(prm);
-        if (prm.fuse_final) fused_final(prm);
+        if (prm.fuse_final) fused_final_warp(prm);
         return;
     } else {
         constexpr int S = kNT / PT;

@@ -856,9 +856,13 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
             const int32_t cands[] = {1, 4, 16, 64, 256};
             for (int32_t c : cands) {
                 if (c > n_points && c != 1) continue;  // idle lanes never pay off
-                for (int k = 0; k < 2; ++k) {
-                    int32_t ch = default_chunk(ctx, ids, n_points, c, pr) * (k ? 4 : 1);
+                for (int k = 0; k < 3; ++k) {
+                    // default item size, a quarter of it (shorter tail), four times it (less overhead)
+                    const int32_t q = (c == 1) ? 64 : 1024;
+                    const int32_t d0 = default_chunk(ctx, ids, n_points, c, pr);
+                    int32_t ch = (k == 0) ? d0 : (k == 1) ? std::max(q, (d0 / 4 + q - 1) / q * q) : d0 * 4;
                     ch = std::min(ch, 1 << 20);
+                    if (k == 1 && ch == d0) continue;
                     double ms;
                     st = time_shape(ctx, ids, point_begin, n_points, pr, nbins, lo, hi, c, ch, &ms);
                     if (st) return st;
