@@ -82,7 +82,6 @@ struct osc_ctx {
     uint64_t plan_clock = 0;
 
     bool timing = false;
-    cudaEvent_t ev[6] = {};
     double t_const = -1, t_hist = -1, t_final = -1;
     // non-blocking timing: event pairs per kernel kind (0 const, 1 hist, 2 final)
     std::vector<cudaEvent_t> ev_pool;
@@ -106,11 +105,7 @@ osc_status dalloc(osc_ctx *c, void **p, size_t bytes);
 void dfree(osc_ctx *c, void *p);
 osc_status validate_point(osc_ctx *c, const osc_point &p, int index);
 osc_status ensure_acc(osc_ctx *c, int64_t bins);
-// Histogram launch over explicit work (used by osc_histogram and serving).
-osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_items, int32_t n_items, int grid,
-                            const SampleDev *d_samples, const float *pc32, const double *pc64, int32_t nbins,
-                            double lo, double hi, const double *d_hmeta, int64_t n_hist, double *d_out,
-                            cudaStream_t st);
+// grid of the persistent histogram kernel; finalize fusion rule
 int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items);
 bool fuse_finalize(int64_t n_hist, int32_t nbins);
 cudaEvent_t pool_event(osc_ctx *c);

@@ -77,7 +77,6 @@ struct HistParams {
     unsigned long long *acc;  // fixed-point bins: three integer digit columns per bin
     int32_t *counter;         // dynamic work counter (reset by the finalize kernel)
     float lo_f, inv_f, nb_f;
-    int32_t hist_stride_pts;  // histogram index step between consecutive points of a tile
     // fused finalize (small outputs): the last block converts the bins
     int32_t fuse_final;
     int64_t fin_n_hist;

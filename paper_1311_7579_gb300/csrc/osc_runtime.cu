@@ -162,7 +162,6 @@ static void fill_hist_params(HistParams &hp, const WorkItem *d_items, int32_t n_
     hp.lo_f = (float)lo;
     hp.inv_f = (float)((double)nbins / (hi - lo));
     hp.nb_f = (float)nbins;
-    hp.hist_stride_pts = 1;
     hp.fuse_final = 0;
     hp.fin_n_hist = 0;
     hp.fin_hmeta = nullptr;
@@ -171,21 +170,6 @@ static void fill_hist_params(HistParams &hp, const WorkItem *d_items, int32_t n_
 
 // Outputs this small are converted by the histogram kernel's last block.
 bool fuse_finalize(int64_t n_hist, int32_t nbins) { return n_hist * (int64_t)nbins <= 4096; }
-
-osc_status launch_hist_work(osc_ctx *c, int prec, int pt, const WorkItem *d_items, int32_t n_items, int grid,
-                            const SampleDev *d_samples, const float *pc32, const double *pc64, int32_t nbins,
-                            double lo, double hi, const double *d_hmeta, int64_t n_hist, double *d_out,
-                            cudaStream_t st) {
-    HistParams hp;
-    fill_hist_params(hp, d_items, n_items, d_samples, pc32, pc64, c->d_acc, c->d_counter, nbins, lo, hi);
-    cudaError_t e = launch_hist(prec, pt, hp, grid, st);
-    if (e) return fail_cuda(c, e, "histogram kernel launch");
-    FinalParams fp{c->d_acc, d_hmeta, pc64, d_out, n_hist, nbins, c->d_counter};
-    e = launch_final(fp, st);
-    if (e) return fail_cuda(c, e, "finalize kernel launch");
-    c->launches += 2;
-    return OSC_OK;
-}
 
 cudaEvent_t pool_event(osc_ctx *c) {
     if (!c->ev_pool.empty()) {
@@ -325,7 +309,6 @@ osc_status osc_create(int device, size_t workspace_cap_bytes, void *cuda_stream,
         }
         ctx->own_stream = true;
     }
-    for (auto &ev : ctx->ev) cudaEventCreate(&ev);
     void *p;
     if (dalloc(ctx, &p, 64) != OSC_OK) {
         osc_destroy(ctx);
@@ -357,8 +340,6 @@ void osc_destroy(osc_ctx *ctx) {
     dfree(ctx, ctx->d_counter);
     dfree(ctx, ctx->d_out);
     dfree(ctx, ctx->d_rw);
-    for (auto &ev : ctx->ev)
-        if (ev) cudaEventDestroy(ev);
     for (auto &p : ctx->ev_pending) {
         cudaEventDestroy(p.second.first);
         cudaEventDestroy(p.second.second);

@@ -158,7 +158,6 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     hp.lo_f = (float)sv->lo;
     hp.inv_f = (float)((double)sv->nbins / (sv->hi - sv->lo));
     hp.nb_f = (float)sv->nbins;
-    hp.hist_stride_pts = 1;
     const bool fused = fuse_finalize(n, sv->nbins);
     hp.fuse_final = fused ? 1 : 0;
     hp.fin_n_hist = n;
