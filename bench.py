@@ -351,15 +351,20 @@ def run_ours(args):
     clocks = clk.summary()
     k64 = max(3, min(args.steps, 40))
     ms64, c64, s64, _ = timed("fp64", k64, max(3, min(args.warmup, 5)))
+    # the FP64-eigen-solve variant (FP64 eigenvalues and phases, FP32 amplitude) on the same workload
+    kmx = max(3, min(args.steps, 200))
+    msmx, cmx, smx, _ = timed("fp32_f64eig", kmx, max(3, min(args.warmup, 5)))
 
     tot32 = float(ms32.sum())
     tot64 = float(ms64.sum())
+    totmx = float(msmx.sum())
     if ws > 1:
-        t = torch.tensor([tot32, tot64], dtype=torch.float64, device=dev)
+        t = torch.tensor([tot32, tot64, totmx], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot32, tot64 = float(t[0]), float(t[1])
+        tot32, tot64, totmx = float(t[0]), float(t[1]), float(t[2])
     value = ws * N_EVENTS * args.steps / (tot32 * 1e-3)
     fp64_value = ws * N_EVENTS * k64 / (tot64 * 1e-3)
+    f64eig_value = ws * N_EVENTS * kmx / (totmx * 1e-3)
     k_hist_ms = sums[1] / max(1, counts[1])
 
     # end-to-end through the public API with host buffers: pinned point in, histogram out
@@ -424,11 +429,13 @@ def run_ours(args):
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "fp64_value": fp64_value, "fp32_over_fp64": value / fp64_value,
+            "fp32_f64eig_value": f64eig_value,
             "latency_us": {"p50": float(np.percentile(lat, 50) * 1e6), "p99": float(np.percentile(lat, 99) * 1e6),
                            "device_p50": float(np.percentile(ms32, 50) * 1e3),
                            "device_p99": float(np.percentile(ms32, 99) * 1e3)},
             "kernel_ms": {"hist_fp32": k_hist_ms, "final": sums[2] / max(1, counts[2]),
-                          "const": sums[0] / max(1, counts[0]), "hist_fp64": s64[1] / max(1, c64[1])},
+                          "const": sums[0] / max(1, counts[0]), "hist_fp64": s64[1] / max(1, c64[1]),
+                          "hist_fp32_f64eig": smx[1] / max(1, cmx[1])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": traffic,
                          "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"

@@ -60,8 +60,10 @@ typedef enum {
 } osc_status;
 
 typedef enum {
-    OSC_FP64 = 0,      /* all-FP64 path: closed-form cubic eigenvalues, FP64 amplitude */
-    OSC_FP32_BULK = 1  /* FP32 bulk with FP64-derived per-point constants (see DESIGN) */
+    OSC_FP64 = 0,         /* all-FP64 path: closed-form cubic eigenvalues, FP64 amplitude */
+    OSC_FP32_BULK = 1,    /* FP32 bulk with FP64-derived per-point constants: eigenvalues as
+                             vacuum value + FP32 matter shift, float-float vacuum phases */
+    OSC_FP32_F64EIG = 2   /* FP64 cubic eigen-solve and phase reduction, FP32 amplitude */
 } osc_precision;
 
 typedef enum { OSC_NU_E = 0, OSC_NU_MU = 1, OSC_NU_TAU = 2 } osc_flavour;
@@ -210,6 +212,8 @@ osc_status osc_serve_stop(osc_ctx *ctx);
  * Every call shares the array: the call clears what must start at zero, and
  * calls that overlap on the GPU (other threads, other streams) race and must
  * not be issued.
+ *
+ * prec is OSC_FP64 or OSC_FP32_BULK.
  *
  * Errors: OSC_E_ARG (null pointer, bad precision, n outside [1, 2^31 - 1],
  * nbins outside [1, 4096]), OSC_E_RANGE (invalid scalars or point; or, found

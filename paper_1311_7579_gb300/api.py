@@ -18,8 +18,9 @@ from . import build as _build
 OSC_OK, OSC_E_ARG, OSC_E_RANGE, OSC_E_NOMEM, OSC_E_CUDA, OSC_E_STATE, OSC_E_TIMEOUT, OSC_E_BUSY = range(8)
 STATUS_NAMES = ["OSC_OK", "OSC_E_ARG", "OSC_E_RANGE", "OSC_E_NOMEM", "OSC_E_CUDA", "OSC_E_STATE",
                 "OSC_E_TIMEOUT", "OSC_E_BUSY"]
-OSC_FP64, OSC_FP32_BULK = 0, 1
-PRECISIONS = {"fp64": OSC_FP64, "fp32": OSC_FP32_BULK, OSC_FP64: OSC_FP64, OSC_FP32_BULK: OSC_FP32_BULK}
+OSC_FP64, OSC_FP32_BULK, OSC_FP32_F64EIG = 0, 1, 2
+PRECISIONS = {"fp64": OSC_FP64, "fp32": OSC_FP32_BULK, "fp32_f64eig": OSC_FP32_F64EIG,
+              OSC_FP64: OSC_FP64, OSC_FP32_BULK: OSC_FP32_BULK, OSC_FP32_F64EIG: OSC_FP32_F64EIG}
 
 # Every entry point declared in include/osc.h, in declaration order.
 ENTRY_POINTS = [

@@ -108,6 +108,7 @@ osc_status ensure_acc(osc_ctx *c, int64_t bins);
 // grid of the persistent histogram kernel; finalize fusion rule
 int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items);
 bool fuse_finalize(int64_t n_hist, int32_t nbins);
+int prec_kind(osc_precision p);
 cudaEvent_t pool_event(osc_ctx *c);
 osc_status drain_timing(osc_ctx *c);
 void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,

@@ -113,7 +113,7 @@ struct ReweightParams {
 };
 
 // Launch helpers implemented in the kernel translation units.
-enum Prec { kFP64 = 0, kFP32 = 1 };
+enum Prec { kFP64 = 0, kFP32 = 1, kMix = 2 };  // kMix: FP64 eigen-solve and phases, FP32 amplitude
 cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
 cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st);
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);

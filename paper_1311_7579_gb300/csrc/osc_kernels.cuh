@@ -407,6 +407,8 @@ template <int PREC>
 struct StageOf { using T = Stage32; };
 template <>
 struct StageOf<kFP64> { using T = Stage64; };
+template <>
+struct StageOf<kMix> { using T = Stage64; };
 
 // Load tile [base, base + nt) of the item into shared memory: one 16-byte event
 // record per load, consecutive threads on consecutive events.
@@ -462,11 +464,12 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
         if (wi.point_base != cur_point) {
             cur_point = wi.point_base;
             cur_ch = -1;
-            if (PREC == kFP32) {
+            if (PREC != kFP64) {
                 pc32 = prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
                 load_pt32(pc32, c32);
                 sf = pc32[C32_ESCALE];
-            } else {
+            }
+            if (PREC != kFP32) {
                 pc64 = prm.pc64 + (int64_t)wi.point_base * C64_STRIDE;
                 load_pt64(pc64, c64);
                 sf = (float)pc64[C64_ESCALE];
@@ -529,6 +532,38 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
             }
+        } else if (PREC == kMix) {
+            const int sh = sd.frac_bits - 150;
+            for (; e < end; e += 64) {
+                const bool has_b = e + 32 < end;
+                const int en = e + 64;
+                float Ena = 1.0f, rna = 0.0f, wna = 0.0f, Enb = 1.0f, rnb = 0.0f, wnb = 0.0f;
+                int cna = 0, cnb = 0;
+                if (en < end) {
+                    const float4 q = ev[en];
+                    Ena = q.x; rna = q.y; wna = q.z; cna = __float_as_int(q.w);
+                }
+                if (en + 32 < end) {
+                    const float4 q = ev[en + 32];
+                    Enb = q.x; rnb = q.y; wnb = q.z; cnb = __float_as_int(q.w);
+                }
+                for (int k = 0; k < 2; ++k) {
+                    const float E = k ? Eb : Ea, er = k ? rb : ra, w = k ? wb : wa;
+                    const int ch = k ? cb : ca;
+                    if (k && !has_b) break;
+                    if (ch != cur_ch) {
+                        cur_ch = ch;
+                        load_ch32(pc32, ch, h32);
+                    }
+                    float A, th, tl;
+                    event_terms32(sd, E, ch, A, th, tl);
+                    const double Ad = sd.kA_rhoye * (double)E;
+                    const float P = prob_mix(c32, h32, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl);
+                    acc_event_f32(r, accp, prm, sf, er, P * w, sh, true);
+                }
+                Ea = Ena; ra = rna; wa = wna; ca = cna;
+                Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
+            }
         } else {
             const double hs = sd.hscale_d;
             for (; e < end; e += 64) {
@@ -580,7 +615,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
 // its bin sequence is monotone within a channel and a register run-length
 // accumulator suffices.  Two events are computed per iteration.
 template <int PREC, int PT>
-__global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const HistParams prm) {
+__global__ void __launch_bounds__(kNT, (PREC == kFP64) ? 1 : 2) k_hist(const HistParams prm) {
     if constexpr (PT == 1) {
         hist_items_per_warp<PREC>(prm);
         if (prm.fuse_final) fused_final_warp(prm);
@@ -644,6 +679,33 @@ __global__ void __launch_bounds__(kNT, (PREC == kFP32) ? 2 : 1) k_hist(const His
                         }
                     }
                 }
+            } else if (PREC == kMix) {
+                const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
+                Pt32 c;
+                load_pt32(pc, c);
+                Pt64 c64;
+                load_pt64(prm.pc64 + (int64_t)pidx * C64_STRIDE, c64);
+                Ch32 h;
+                const float sf = pc[C32_ESCALE];
+                const int sh = sd.frac_bits - 150;
+                constexpr double inv2pi = 0.15915494309189533577;
+                for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
+                    const int nt = min(kET, wi.ev_count - t0);
+                    __syncthreads();
+                    stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
+                    __syncthreads();
+                    const Stage64 &s = reinterpret_cast<const Stage64 &>(stg);
+                    for (int j = sl; j < nt; j += S) {
+                        const int ch = s.ch[j];
+                        if (ch != cur_ch) {
+                            cur_ch = ch;
+                            load_ch32(pc, ch, h);
+                        }
+                        const float P = prob_mix(c, h, c64, s.a[j], s.tau[j] * inv2pi);
+                        const float2 ew = s.ew[j];
+                        acc_event_f32(r, accp, prm, sf, ew.x, P * ew.y, sh, active);
+                    }
+                }
             } else {
                 const double *pc = prm.pc64 + (int64_t)pidx * C64_STRIDE;
                 Pt64 c;
@@ -697,6 +759,31 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
             float A, th, tl;
             event_terms32(sd, E, ch, A, th, tl);
             const float P = prob_fp32(c, h, A, th, tl);
+            const float w = P * q.z;
+            const int32_t o = sd.perm[i];
+            if (r.out_prob) r.out_prob[o] = (double)P;
+            if (r.out_weight) r.out_weight[o] = (double)w * r.norm;
+        }
+    } else if (PREC == kMix) {
+        const float *pc = r.pc32 + (int64_t)r.point * C32_STRIDE;
+        Pt32 c;
+        load_pt32(pc, c);
+        Pt64 c64;
+        load_pt64(r.pc64 + (int64_t)r.point * C64_STRIDE, c64);
+        Ch32 h;
+        int cur_ch = -1;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sd.n; i += stride) {
+            const float4 q = sd.ev[i];
+            const float E = q.x;
+            const int ch = __float_as_int(q.w);
+            if (ch != cur_ch) {
+                cur_ch = ch;
+                load_ch32(pc, ch, h);
+            }
+            float A, th, tl;
+            event_terms32(sd, E, ch, A, th, tl);
+            const double Ad = sd.kA_rhoye * (double)E;
+            const float P = prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl);
             const float w = P * q.z;
             const int32_t o = sd.perm[i];
             if (r.out_prob) r.out_prob[o] = (double)P;

@@ -30,6 +30,9 @@ __global__ void k_final(const FinalParams f) {
 
 const void *hist_kernel_fn_fp32(int pt);
 const void *hist_kernel_fn_fp64(int pt);
+const void *hist_kernel_fn_mix(int pt);
+cudaError_t launch_hist_mix(int pt, const HistParams &p, int grid, cudaStream_t st);
+cudaError_t launch_reweight_mix(const ReweightParams &p, cudaStream_t st);
 cudaError_t launch_hist_fp32(int pt, const HistParams &p, int grid, cudaStream_t st);
 cudaError_t launch_hist_fp64(int pt, const HistParams &p, int grid, cudaStream_t st);
 cudaError_t launch_reweight_fp32(const ReweightParams &p, cudaStream_t st);
@@ -38,7 +41,7 @@ cudaError_t launch_reweight_fp64(const ReweightParams &p, cudaStream_t st);
 int hist_threads() { return kNT; }
 
 const void *hist_kernel_fn(int prec, int pt) {
-    return prec == kFP32 ? hist_kernel_fn_fp32(pt) : hist_kernel_fn_fp64(pt);
+    return prec == kFP32 ? hist_kernel_fn_fp32(pt) : prec == kMix ? hist_kernel_fn_mix(pt) : hist_kernel_fn_fp64(pt);
 }
 
 const void *final_kernel_fn() { return (const void *)k_final; }
@@ -64,7 +67,9 @@ cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32,
 }
 
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st) {
-    return prec == kFP32 ? launch_hist_fp32(pt, p, grid, st) : launch_hist_fp64(pt, p, grid, st);
+    return prec == kFP32 ? launch_hist_fp32(pt, p, grid, st)
+           : prec == kMix ? launch_hist_mix(pt, p, grid, st)
+                          : launch_hist_fp64(pt, p, grid, st);
 }
 
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st) {
@@ -77,7 +82,7 @@ cudaError_t launch_final(const FinalParams &p, cudaStream_t st) {
 }
 
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st) {
-    return prec == kFP32 ? launch_reweight_fp32(p, st) : launch_reweight_fp64(p, st);
+    return prec == kFP32 ? launch_reweight_fp32(p, st) : prec == kMix ? launch_reweight_mix(p, st) : launch_reweight_fp64(p, st);
 }
 
 }  // namespace osc

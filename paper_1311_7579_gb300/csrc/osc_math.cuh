@@ -104,10 +104,9 @@ __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float v
     return fr + fmaf(th, dd, e1 + e2);
 }
 
-// P(alpha -> beta) for one event and one point.  A: signed matter term [eV^2];
-// (th, tl): c_L L / (2 pi E_true) as float-float.
-__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl) {
-    // trigonometric seed of the three sorted roots (depressed cubic in FP32)
+// Trigonometric FP32 seed of the two lower sorted roots of the characteristic
+// cubic, as roots mu of the depressed cubic (lambda = mu + (T0 + A) / 3).
+__device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3) {
     const float p = fmaf(fmaf(A, -1.0f / 3.0f, c.p1), A, c.p0);
     const float q = fmaf(fmaf(fmaf(A, -2.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
     const float mp3 = fmaxf(p * (-1.0f / 3.0f), 1e-30f);
@@ -119,20 +118,20 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;
-    const float t3 = (c.T0 + A) * (1.0f / 3.0f);
-    const float l0 = t3 - rc - rsn;  // smallest root
-    const float l1 = t3 - rc + rsn;  // middle root
-    // matter shifts from the vacuum eigenvalues: Newton on the shifted cubics
-    const float dl0 = shifted_newton(l0 - c.d0, A, c.S0, c.PI0, c.W0, c.E0);
-    const float dl1 = shifted_newton(l1 - c.d1, A, c.S1, c.PI1, c.W1, c.E1);
-    const float dl2 = A - dl0 - dl1;  // trace: sum of shifts = A
-    const float L0 = c.d0 + dl0, L1 = c.d1 + dl1, L2 = c.d2 + dl2;
-    const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
-    // Sylvester coefficients C_l = N_l / D_l; the projectors sum to the identity,
-    // so S = delta_ba + sum_{l=1,2} C_l (e^{-i phi_l} - 1) needs no C_0, and
-    // e^{-i phi} - 1 = -2 sin(phi/2) (sin(phi/2) + i cos(phi/2)) keeps small
-    // phase differences accurate.  The factor -2 is folded into 1/D_l:
-    // D_1 = (L1 - L0)(L1 - L2) = -g01 g12, D_2 = (L2 - L0)(L2 - L1) = g02 g12.
+    t3 = (c.T0 + A) * (1.0f / 3.0f);
+    m0 = -rc - rsn;  // smallest root
+    m1 = -rc + rsn;  // middle root
+}
+
+// |S_ba|^2 from the eigenvalues L1, L2 (FP32), the gaps g_ij = L_i - L_j and the
+// half phases h_l = (phi_l - phi_0) / 2 relative to root 0 [rad].  Sylvester
+// coefficients C_l = N_l / D_l; the projectors sum to the identity, so
+// S = delta_ba + sum_{l=1,2} C_l (e^{-i phi_l} - 1) needs no C_0, and
+// e^{-i phi} - 1 = -2 sin(phi/2) (sin(phi/2) + i cos(phi/2)) keeps small phase
+// differences accurate.  The factor -2 is folded into 1/D_l:
+// D_1 = (L1 - L0)(L1 - L2) = -g01 g12, D_2 = (L2 - L0)(L2 - L1) = g02 g12.
+__device__ __forceinline__ float amplitude2_32(const Pt32 &c, const Ch32 &h, float A, float L1, float L2, float g01,
+                                              float g02, float g12, float h1, float h2) {
     const float inv = rcp_approx(g01 * g02 * g12);
     const float iD1 = 2.0f * g02 * inv, iD2 = -2.0f * g01 * inv;
     const float TA = c.T0 + A;
@@ -144,18 +143,32 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     const float C1r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD1, C1i = fmaf(-sg, Gi, Ki) * iD1;
     sg = TA - L2; pp = fmaf(-L2, sg, c1);
     const float C2r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD2, C2i = fmaf(-sg, Gi, Ki) * iD2;
-    (void)L0;
-    // half phases relative to root 0, in radians: pi * revolutions
-    const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dl1 - dl0);
-    const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dl2 - dl0);
     float s1, k1, s2, k2;
-    __sincosf(3.14159265358979323846f * f1, &s1, &k1);
-    __sincosf(3.14159265358979323846f * f2, &s2, &k2);
+    __sincosf(h1, &s1, &k1);
+    __sincosf(h2, &s2, &k2);
     const float a1 = s1 * s1, b1 = s1 * k1, a2 = s2 * s2, b2 = s2 * k2;
     // S = delta_ba + sum_l C'_l (a_l + i b_l), C'_l = -2 C_l
     const float Sr = h.diag + fmaf(C1r, a1, -C1i * b1) + fmaf(C2r, a2, -C2i * b2);
     const float Si = fmaf(C1r, b1, C1i * a1) + fmaf(C2r, b2, C2i * a2);
     return fmaf(Sr, Sr, Si * Si);
+}
+
+// P(alpha -> beta) for one event and one point, FP32 bulk.  A: signed matter
+// term [eV^2]; (th, tl): c_L L / (2 pi E_true) as float-float.
+__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl) {
+    float m0, m1, t3;
+    seed_roots32(c, A, m0, m1, t3);
+    // matter shifts from the vacuum eigenvalues: Newton on the shifted cubics
+    const float dl0 = shifted_newton(t3 + m0 - c.d0, A, c.S0, c.PI0, c.W0, c.E0);
+    const float dl1 = shifted_newton(t3 + m1 - c.d1, A, c.S1, c.PI1, c.W1, c.E1);
+    const float dl2 = A - dl0 - dl1;  // trace: sum of shifts = A
+    const float L1 = c.d1 + dl1, L2 = c.d2 + dl2;
+    const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
+    // half phases relative to root 0: pi * revolutions
+    const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dl1 - dl0);
+    const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dl2 - dl0);
+    return amplitude2_32(c, h, A, L1, L2, g01, g02, g12, 3.14159265358979323846f * f1,
+                         3.14159265358979323846f * f2);
 }
 
 // ------------------------------------------------------------------ FP64 path
@@ -203,6 +216,31 @@ __device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double
     const double Sr = C0r + C1r * k1 + C1i * s1 + C2r * k2 + C2i * s2;
     const double Si = C0i + C1i * k1 - C1r * s1 + C2i * k2 - C2r * s2;
     return Sr * Sr + Si * Si;
+}
+
+// The FP64-eigenvalue variant (FP64 for the cubic eigen-solve and the phases,
+// FP32 for the amplitude): FP32 seed, one FP64 Newton step per root on the
+// depressed cubic, FP64 phase differences tau (mu_l - mu_0) reduced modulo 2 pi
+// in FP64, then the same FP32 amplitude.  Ad: signed matter term [eV^2];
+// trev = c_L L / (2 pi E) [revolutions per eV^2].
+__device__ __forceinline__ float prob_mix(const Pt32 &c, const Ch32 &h, const Pt64 &c64, double Ad, double trev) {
+    const float A = (float)Ad;
+    float s0, s1, t3f;
+    seed_roots32(c, A, s0, s1, t3f);
+    const double p = fma(fma(Ad, -1.0 / 3.0, c64.p1), Ad, c64.p0);
+    const double q = fma(fma(fma(Ad, -2.0 / 27.0, c64.q2), Ad, c64.q1), Ad, c64.q0);
+    double m0 = (double)s0, m1 = (double)s1;
+    m0 -= (double)((float)fma(fma(m0, m0, p), m0, q) / (float)fma(3.0 * m0, m0, p));
+    m1 -= (double)((float)fma(fma(m1, m1, p), m1, q) / (float)fma(3.0 * m1, m1, p));
+    const double m2 = -m0 - m1;  // depressed roots sum to zero
+    const double t3 = (c64.T0 + Ad) * (1.0 / 3.0);
+    const float L1 = (float)(m1 + t3), L2 = (float)(m2 + t3);
+    const float g01 = (float)(m0 - m1), g02 = (float)(m0 - m2), g12 = (float)(m1 - m2);
+    // phase differences in revolutions, reduced in FP64, then half angles [rad]
+    const double r1 = trev * (m1 - m0), r2 = trev * (m2 - m0);
+    const float f1 = (float)(r1 - rint(r1)), f2 = (float)(r2 - rint(r2));
+    return amplitude2_32(c, h, A, L1, L2, g01, g02, g12, 3.14159265358979323846f * f1,
+                         3.14159265358979323846f * f2);
 }
 
 }  // namespace osc

@@ -72,6 +72,8 @@ void dfree(osc_ctx *c, void *p) {
 
 static bool is_fin(double x) { return std::isfinite(x); }
 
+int prec_kind(osc_precision p) { return p == OSC_FP32_BULK ? kFP32 : p == OSC_FP32_F64EIG ? kMix : kFP64; }
+
 osc_status validate_point(osc_ctx *c, const osc_point &p, int i) {
     std::ostringstream o;
     o << "point " << i << ": ";
@@ -574,7 +576,8 @@ osc_status osc_sync(osc_ctx *ctx) {
 osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_precision prec, double *out_prob,
                         double *out_weight, int out_on_device) {
     CHECK_CTX(ctx);
-    if (prec != OSC_FP64 && prec != OSC_FP32_BULK) return fail(ctx, OSC_E_ARG, "bad precision");
+    if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
+        return fail(ctx, OSC_E_ARG, "bad precision");
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     auto it = ctx->samples.find(sample_id);
     if (it == ctx->samples.end()) return fail(ctx, OSC_E_ARG, "unknown sample id");
@@ -596,7 +599,7 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
     rp.norm = ctx->pts[point].norm;
     rp.out_prob = dp;
     rp.out_weight = dw;
-    CK(launch_reweight(prec == OSC_FP32_BULK ? kFP32 : kFP64, rp, ctx->stream));
+    CK(launch_reweight(prec_kind(prec), rp, ctx->stream));
     ctx->launches += 1;
     if (!out_on_device) {
         if (out_prob) CK(cudaMemcpyAsync(out_prob, dp, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -630,7 +633,7 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     int64_t ev = 0;
     for (int32_t id : ids) ev += ctx->samples[id]->n;
     const int64_t tiles = (n_points + pt - 1) / pt;
-    const int per_sm = (prec == kFP32) ? 2 : 1;
+    const int per_sm = (prec == kFP64) ? 1 : 2;
     // one point per item: items are taken per warp; otherwise per block
     const int64_t slots = (int64_t)ctx->n_sm * per_sm * (pt == 1 ? hist_threads() / 32 : 1);
     const int64_t quantum = (pt == 1) ? 64 : 1024;
@@ -809,7 +812,8 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
                                     double *out, int out_on_device) {
     CHECK_CTX(ctx);
     if (!sample_ids || !out) return fail(ctx, OSC_E_ARG, "null argument");
-    if (prec != OSC_FP64 && prec != OSC_FP32_BULK) return fail(ctx, OSC_E_ARG, "bad precision");
+    if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
+        return fail(ctx, OSC_E_ARG, "bad precision");
     if (n_samples < 1 || n_samples > 4096) return fail(ctx, OSC_E_ARG, "n_samples must be in [1, 4096]");
     if (nbins < 1 || nbins > (1 << 20)) return fail(ctx, OSC_E_ARG, "nbins must be in [1, 2^20]");
     if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo)) return fail(ctx, OSC_E_RANGE, "need finite lo < hi");
@@ -819,7 +823,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     std::vector<int32_t> ids(sample_ids, sample_ids + n_samples);
     for (int32_t id : ids)
         if (!ctx->samples.count(id)) return fail(ctx, OSC_E_ARG, "unknown sample id");
-    const int pr = prec == OSC_FP32_BULK ? kFP32 : kFP64;
+    const int pr = prec_kind(prec);
     const int64_t bins = (int64_t)n_samples * n_points * nbins;
     osc_status st = ensure_acc(ctx, bins);
     if (st) return st;

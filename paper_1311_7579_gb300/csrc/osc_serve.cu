@@ -328,7 +328,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
     if (!ctx || !pt || !ticket) return OSC_E_ARG;
     osc_serve *sv = ctx->serve;
     if (!sv) return OSC_E_STATE;
-    if (prec != OSC_FP64 && prec != OSC_FP32_BULK) return OSC_E_ARG;
+    if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG) return OSC_E_ARG;
     Request r;
     {
         std::lock_guard<std::mutex> api(ctx->api_mu);
@@ -339,7 +339,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
         r.frac_bits = it->second->frac_bits;
     }
     r.pt = *pt;
-    r.prec = prec == OSC_FP32_BULK ? kFP32 : kFP64;
+    r.prec = prec_kind(prec);
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stop) return OSC_E_STATE;

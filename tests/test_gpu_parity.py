@@ -70,8 +70,10 @@ def test_all_channels_random_points(ctx, L, rho):
         po, _ = oracle.reweight(s, oracle.point_from_row(pts[k]))
         p64, _ = _gpu_probs(ctx, sid, k, "fp64", s["n"])
         p32, _ = _gpu_probs(ctx, sid, k, "fp32", s["n"])
+        pmx, _ = _gpu_probs(ctx, sid, k, "fp32_f64eig", s["n"])
         assert np.max(np.abs(p64 - po)) <= TOL_FP64, (k, np.max(np.abs(p64 - po)))
         assert np.max(np.abs(p32 - po)) <= TOL_FP32, (k, np.max(np.abs(p32 - po)))
+        assert np.max(np.abs(pmx - po)) <= TOL_FP32, (k, np.max(np.abs(pmx - po)))
     api.osc_unload_sample(ctx, sid)
 
 
@@ -108,6 +110,7 @@ def test_histograms_multi_point_both_paths(ctx):
     api.osc_set_params(ctx, pts)
     h64 = api.osc_histogram(ctx, [sid], 0, pts.shape[0], "fp64", LO, HI, NB)[0]
     h32 = api.osc_histogram(ctx, [sid], 0, pts.shape[0], "fp32", LO, HI, NB)[0]
+    hmx = api.osc_histogram(ctx, [sid], 0, pts.shape[0], "fp32_f64eig", LO, HI, NB)[0]
     for k in range(pts.shape[0]):
         pt = oracle.point_from_row(pts[k])
         _, wo = oracle.reweight(s, pt)
@@ -120,6 +123,10 @@ def test_histograms_multi_point_both_paths(ctx):
         # and the FP32 histogram against the FP64 oracle: bounded by |dP| <= 1e-5 per event
         wsum = oracle.hist_from_weights(s["e_reco"], s["w_mc"].astype(np.float64), pts[k, 6], LO, HI, NB)
         assert np.all(np.abs(h32[k] - ho) <= TOL_FP32 * wsum + 1e-12)
+        # the FP64-eigen variant the same way
+        _, wmx = _gpu_probs(ctx, sid, k, "fp32_f64eig", s["n"])
+        _check_fp64_hist(hmx[k], oracle.hist_from_weights(s["e_reco"], wmx, pts[k, 6], LO, HI, NB, compensated=True))
+        assert np.all(np.abs(hmx[k] - ho) <= TOL_FP32 * wsum + 1e-12)
     api.osc_unload_sample(ctx, sid)
 
 
@@ -129,7 +136,7 @@ def test_histogram_bitwise_independent_of_tile_shape(ctx):
     pts = synth.scan_points(20, seed=6)
     api.osc_set_params(ctx, pts)
     ref = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64", "fp32_f64eig"):
         for ppb in (1, 4, 16, 64, 256):
             for chunk in (1024, 4096, 0):
                 api.osc_set_tile(ctx, ppb, chunk)
@@ -149,14 +156,14 @@ def test_uneven_samples_one_launch(ctx):
     sids = [api.osc_load_sample(ctx, s) for s in ss]
     pts = synth.uneven_points(9, seed=8)
     api.osc_set_params(ctx, pts)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp32_f64eig"):
         h = api.osc_histogram(ctx, sids, 0, 9, prec, LO, 20.0, 80)
         for j, s in enumerate(ss):
             for k in range(9):
                 if prec == "fp64":
                     _, w = oracle.reweight(s, oracle.point_from_row(pts[k]))
                 else:
-                    _, w = _gpu_probs(ctx, sids[j], k, "fp32", s["n"])
+                    _, w = _gpu_probs(ctx, sids[j], k, prec, s["n"])
                 ho = oracle.hist_from_weights(s["e_reco"], w, pts[k, 6], LO, 20.0, 80, compensated=True)
                 _check_fp64_hist(h[j, k], ho)
     for sid in sids:
