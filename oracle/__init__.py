@@ -73,6 +73,11 @@ def lib():
                 "orc_bin": (ctypes.c_int, [d, ctypes.c_float, d, d, ctypes.c_int]),
                 "orc_bin_many": (None, [i64, fp, d, d, d, ctypes.c_int, i32]),
                 "orc_num_threads": (ctypes.c_int, []),
+                "orc_true_centre": (ctypes.c_float, [d, d, ctypes.c_int, ctypes.c_int]),
+                "orc_reweight_bin_centre": (None, [i64, fp, fp, u8, u8, u8, d, d, d, pt, d, d, ctypes.c_int,
+                                                   dp, dp]),
+                "orc_prob_matrix_layers_many": (None, [pt, ctypes.c_int, dp, dp, dp, i64, dp, ctypes.c_int, dp]),
+                "orc_reweight_layers": (None, [i64, fp, fp, u8, u8, u8, ctypes.c_int, dp, dp, dp, pt, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -192,4 +197,78 @@ def bins(e_reco, escale, lo, hi, nbins) -> np.ndarray:
     out = np.zeros(e_reco.size, dtype=np.int32)
     lib().orc_bin_many(e_reco.size, _ptr(e_reco, ctypes.c_float), escale, lo, hi, nbins,
                        _ptr(out, ctypes.c_int32))
+    return out
+
+
+def true_centre(t_lo, t_hi, t_nbins, t) -> float:
+    """FP32 centre energy of true-energy bin t (see orc_true_centre)."""
+    return lib().orc_true_centre(float(t_lo), float(t_hi), int(t_nbins), int(t))
+
+
+def reweight_bin_centre(sample, pt: OrcPoint, t_lo, t_hi, t_nbins, n=None):
+    """Per-event (prob, weight) of the binned method: P at the centre of the
+    event's true-energy bin, 0 outside [t_lo, t_hi)."""
+    n = sample["n"] if n is None else int(n)
+    prob_out = np.zeros(n)
+    w_out = np.zeros(n)
+    lib().orc_reweight_bin_centre(n, _ptr(sample["e_true"], ctypes.c_float), _ptr(sample["w_mc"], ctypes.c_float),
+                                  _ptr(sample["flav_in"], ctypes.c_uint8), _ptr(sample["flav_out"], ctypes.c_uint8),
+                                  _ptr(sample["is_nubar"], ctypes.c_uint8), sample["baseline_km"],
+                                  sample["density_gcc"], sample["ye"], ctypes.byref(pt), float(t_lo), float(t_hi),
+                                  int(t_nbins), _ptr(prob_out, ctypes.c_double), _ptr(w_out, ctypes.c_double))
+    return prob_out, w_out
+
+
+def histogram_bin_centre(sample, points, t_lo, t_hi, t_nbins, lo, hi, nbins, compensated=False, n=None):
+    """out[p, b]: binned-method histograms (weights of reweight_bin_centre binned
+    by E_reco under each point's energy scale)."""
+    n = sample["n"] if n is None else int(n)
+    out = np.zeros((len(points), nbins))
+    for k, r in enumerate(points):
+        pt = r if isinstance(r, OrcPoint) else point_from_row(r)
+        _, w = reweight_bin_centre(sample, pt, t_lo, t_hi, t_nbins, n)
+        out[k] = hist_from_weights(sample["e_reco"][:n], w, pt.escale, lo, hi, nbins, compensated)
+    return out
+
+
+def _layers(layers):
+    L = np.ascontiguousarray([x[0] for x in layers], dtype=np.float64)
+    rho = np.ascontiguousarray([x[1] for x in layers], dtype=np.float64)
+    ye = np.ascontiguousarray([x[2] for x in layers], dtype=np.float64)
+    return L, rho, ye
+
+
+def prob_matrix_layers_many(pt: OrcPoint, layers, E, nubar) -> np.ndarray:
+    """P[i, beta, alpha] through layers [(L_km, rho, ye), ...] in order of travel."""
+    L, rho, ye = _layers(layers)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    out = np.zeros((E.size, 3, 3))
+    lib().orc_prob_matrix_layers_many(ctypes.byref(pt), L.size, _ptr(L, ctypes.c_double), _ptr(rho, ctypes.c_double),
+                                      _ptr(ye, ctypes.c_double), E.size, _ptr(E, ctypes.c_double), int(nubar),
+                                      _ptr(out, ctypes.c_double))
+    return out
+
+
+def reweight_layers(sample, pt: OrcPoint, layers, n=None):
+    """Per-event (prob, weight) through layers [(L_km, rho, ye), ...]."""
+    n = sample["n"] if n is None else int(n)
+    L, rho, ye = _layers(layers)
+    prob_out = np.zeros(n)
+    w_out = np.zeros(n)
+    lib().orc_reweight_layers(n, _ptr(sample["e_true"], ctypes.c_float), _ptr(sample["w_mc"], ctypes.c_float),
+                              _ptr(sample["flav_in"], ctypes.c_uint8), _ptr(sample["flav_out"], ctypes.c_uint8),
+                              _ptr(sample["is_nubar"], ctypes.c_uint8), L.size, _ptr(L, ctypes.c_double),
+                              _ptr(rho, ctypes.c_double), _ptr(ye, ctypes.c_double), ctypes.byref(pt),
+                              _ptr(prob_out, ctypes.c_double), _ptr(w_out, ctypes.c_double))
+    return prob_out, w_out
+
+
+def histogram_layers(sample, points, layers, lo, hi, nbins, compensated=False, n=None):
+    """out[p, b]: event-by-event histograms through a layered path."""
+    n = sample["n"] if n is None else int(n)
+    out = np.zeros((len(points), nbins))
+    for k, r in enumerate(points):
+        pt = r if isinstance(r, OrcPoint) else point_from_row(r)
+        _, w = reweight_layers(sample, pt, layers, n)
+        out[k] = hist_from_weights(sample["e_reco"][:n], w, pt.escale, lo, hi, nbins, compensated)
     return out
