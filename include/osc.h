@@ -141,6 +141,30 @@ osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samp
                          int32_t point_begin, int32_t n_points, osc_precision prec, double lo,
                          double hi, int32_t nbins, double *out, int out_on_device);
 
+/* Binned ("bin-centre") PDFs: the quicker alternative that Sec. 1.1.1 contrasts
+ * with event-by-event reweighting, in which each event's probability is taken
+ * at the centre of its true-energy bin instead of at its own E_true (the
+ * paper's example: a 25 MeV bin from 0.6 to 0.625 GeV evaluated at its centre).
+ *   true-energy bins: t_nbins equal bins over [t_lo, t_hi); an event's bin
+ *     follows the histogram binning rule above with escale 1 (t = e_true -
+ *     (float)t_lo, u = t * (float)(t_nbins / (t_hi - t_lo)), kept iff t >= 0
+ *     and u < t_nbins, bin (int)u); 1 <= t_nbins <= 65536;
+ *   centre of true bin k: (float)(t_lo + (k + 0.5) * ((t_hi - t_lo) / t_nbins)),
+ *     evaluated in double and rounded to FP32 like an event energy;
+ *   events with E_true outside [t_lo, t_hi) contribute nothing;
+ *   weight P(centre) * w_mc * norm, binned by E_reco exactly as osc_histogram
+ *     does (same out layout and rules, same exact fixed-point accumulation).
+ * The probabilities are computed once per (sample, point, channel occurring in
+ * the sample, true bin) into a table held by the cached launch plan: 4 bytes per
+ * entry for OSC_FP32_BULK and OSC_FP32_F64EIG, 8 for OSC_FP64, counted against
+ * the workspace cap (OSC_E_NOMEM beyond it).  out: host memory if
+ * out_on_device == 0 (the call returns after the copy), else device memory (the
+ * call returns once the work is enqueued on the context stream). */
+osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                                    int32_t point_begin, int32_t n_points, osc_precision prec,
+                                    double t_lo, double t_hi, int32_t t_nbins, double lo, double hi,
+                                    int32_t nbins, double *out, int out_on_device);
+
 /* Launch-shape control.  points_per_block in {1, 4, 16, 64, 256}, or 0 to let
  * the autotuner choose per workload class (default); events_per_item a positive
  * multiple of 64, or 0 for the default.  Results never depend on either. */

@@ -27,7 +27,7 @@ ENTRY_POINTS = [
     "osc_version", "osc_create", "osc_destroy", "osc_last_error", "osc_load_sample", "osc_unload_sample",
     "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
     "osc_last_timing", "osc_timing_totals", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
-    "osc_serve_stop", "osc_histogram_noalloc",
+    "osc_serve_stop", "osc_histogram_noalloc", "osc_histogram_bin_centre",
 ]
 
 
@@ -78,6 +78,8 @@ def load_library(path):
         "osc_reweight": (st, [vp, i32, i32, ctypes.c_int, vp, vp, ctypes.c_int]),
         "osc_histogram": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
                                ctypes.c_int]),
+        "osc_histogram_bin_centre": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, d, d,
+                                          i32, vp, ctypes.c_int]),
         "osc_set_tile": (st, [vp, i32, i32]),
         "osc_enable_timing": (st, [vp, ctypes.c_int]),
         "osc_last_timing": (st, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
@@ -192,6 +194,21 @@ def osc_histogram(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, o
     _check(ctx, lib().osc_histogram(ctx, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size,
                                     int(point_begin), int(n_points), PRECISIONS[prec], float(lo), float(hi),
                                     int(nbins), _ptr(out), 1 if dev else 0))
+    return out
+
+
+def osc_histogram_bin_centre(ctx, sample_ids, point_begin, n_points, prec, t_lo, t_hi, t_nbins, lo, hi, nbins,
+                             out=None):
+    """Binned-method histograms (probability at the centre of each event's
+    true-energy bin); out as for osc_histogram."""
+    ids = np.ascontiguousarray(np.atleast_1d(sample_ids), dtype=np.int32)
+    if out is None:
+        out = np.zeros((ids.size, int(n_points), int(nbins)))
+    dev = _is_device(out)
+    _check(ctx, lib().osc_histogram_bin_centre(ctx, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size,
+                                               int(point_begin), int(n_points), PRECISIONS[prec], float(t_lo),
+                                               float(t_hi), int(t_nbins), float(lo), float(hi), int(nbins),
+                                               _ptr(out), 1 if dev else 0))
     return out
 
 

@@ -1,0 +1,129 @@
+// Binned ("bin-centre") reweighting, the quicker alternative that Sec. 1.1.1
+// contrasts with event-by-event reweighting: every event's probability is taken
+// at the centre of its true-energy bin.  Two kernels:
+//   k_bc_table  one thread per (table row, true bin): P at the bin centre, where
+//               a row is a (sample, point, channel present in the sample);
+//   k_bc_hist   per-warp work items (sample, point, event range): true bin of
+//               each event by the FP32 binning rule, gather of P from the table,
+//               weight P * w_mc binned by E_reco into the same exact fixed-point
+//               accumulators as the event-by-event kernel.
+// The table is tiny next to the event stream, so the histogram kernel is bound
+// by reading the 16-byte event records: four records per lane are in flight.
+#include "osc_kernels.cuh"
+
+namespace osc {
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
+    const int64_t n = (int64_t)b.n_rows * b.t_nbins;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = (int32_t)(idx / b.t_nbins);
+        const int32_t t = (int32_t)(idx - (int64_t)r * b.t_nbins);
+        const BcRow rw = b.rows[r];
+        const SampleDev &sd = b.h.samples[rw.sample];
+        // centre t_lo + (t + 1/2) w in double (no contraction), stored in FP32 like an event energy
+        const float E = __double2float_rn(__dadd_rn(b.t_lo, __dmul_rn((double)t + 0.5, b.t_w)));
+        const int ch = rw.chan;
+        if (PREC == kFP32) {
+            const float *pc = b.h.pc32 + (int64_t)rw.point * C32_STRIDE;
+            Pt32 c;
+            load_pt32(pc, c);
+            Ch32 h;
+            load_ch32(pc, ch, h);
+            float A, th, tl;
+            event_terms32(sd, E, ch, A, th, tl);
+            b.tab32[idx] = prob_fp32(c, h, A, th, tl);
+        } else if (PREC == kMix) {
+            const float *pc = b.h.pc32 + (int64_t)rw.point * C32_STRIDE;
+            Pt32 c;
+            load_pt32(pc, c);
+            Ch32 h;
+            load_ch32(pc, ch, h);
+            Pt64 c64;
+            load_pt64(b.h.pc64 + (int64_t)rw.point * C64_STRIDE, c64);
+            float A, th, tl;
+            event_terms32(sd, E, ch, A, th, tl);
+            const double Ad = sd.kA_rhoye * (double)E;
+            b.tab32[idx] = prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl);
+        } else {
+            const double *pc = b.h.pc64 + (int64_t)rw.point * C64_STRIDE;
+            Pt64 c;
+            load_pt64(pc, c);
+            Ch64 h;
+            load_ch64(pc, ch, h);
+            const double Ad = sd.kA_rhoye * (double)E;
+            b.tab64[idx] = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+        }
+    }
+}
+
+constexpr int kBcUnroll = 4;  // event records in flight per lane
+
+template <bool F64>
+__global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
+    const HistParams &prm = b.h;
+    const int lane = threadIdx.x & 31;
+    int it = 0;
+    if (lane == 0) it = atomicAdd(prm.counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    while (it < prm.n_items) {
+        const WorkItem wi = prm.items[it];
+        const SampleDev &sd = prm.samples[wi.sample];
+        const float4 *ev = sd.ev + wi.ev_begin;
+        const int end = wi.ev_count;
+        const float sf = F64 ? (float)prm.pc64[(int64_t)wi.point_base * C64_STRIDE + C64_ESCALE]
+                             : prm.pc32[(int64_t)wi.point_base * C32_STRIDE + C32_ESCALE];
+        const int sh = sd.frac_bits - 150;
+        const double hs = sd.hscale_d;
+        const int32_t *rmap = b.row_map + wi.acc_base * kChannels;
+        unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
+        RunAcc r{0ull, 0ull, -1};
+        int cur_ch = -1;
+        int64_t row_off = 0;
+        for (int e0 = 0; e0 < end; e0 += 32 * kBcUnroll) {
+            float4 q[kBcUnroll];
+#pragma unroll
+            for (int k = 0; k < kBcUnroll; ++k) {
+                const int e = e0 + lane + 32 * k;
+                q[k] = (e < end) ? ev[e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k < kBcUnroll; ++k) {
+                const int e = e0 + lane + 32 * k;
+                const int ch = __float_as_int(q[k].w);
+                const float tb = __fsub_rn(q[k].x, b.t_lo_f);
+                const float u = __fmul_rn(tb, b.t_inv_f);
+                const bool keep = e < end && tb >= 0.0f && u < b.t_nb_f;
+                if (keep && ch != cur_ch) {
+                    cur_ch = ch;
+                    row_off = (int64_t)rmap[ch] * b.t_nbins;
+                }
+                const int64_t ti = row_off + (keep ? __float2int_rz(u) : 0);
+                if (F64) {
+                    const double P = keep ? b.tab64[ti] : 0.0;
+                    acc_event_f64(r, accp, prm, sf, q[k].y, P * (double)q[k].z, hs, keep);
+                } else {
+                    const float P = keep ? b.tab32[ti] : 0.0f;
+                    acc_event_f32(r, accp, prm, sf, q[k].y, P * q[k].z, sh, keep);
+                }
+            }
+        }
+        acc_finish_warp(r, accp);
+        if (lane == 0) it = atomicAdd(prm.counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+    }
+    if (prm.fuse_final) fused_final_warp(prm);
+}
+
+const void *bc_hist_kernel_fn(int prec) {
+    return prec == kFP64 ? (const void *)k_bc_hist<true> : (const void *)k_bc_hist<false>;
+}
+
+const void *bc_table_kernel_fn(int prec) {
+    return prec == kFP32 ? (const void *)k_bc_table<kFP32>
+           : prec == kMix ? (const void *)k_bc_table<kMix>
+                          : (const void *)k_bc_table<kFP64>;
+}
+
+}  // namespace osc

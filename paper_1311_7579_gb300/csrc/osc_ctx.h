@@ -24,13 +24,16 @@ struct Sample {
     int64_t n = 0, n_pad = 0;
     double L = 0, rho = 0, ye = 0;
     int32_t frac_bits = 96;
+    uint32_t chan_mask = 0;  // bit c set when channel id c occurs in the sample
     float4 *ev = nullptr;
     int32_t *perm = nullptr;
     SampleDev dev{};
 };
 
 // A cached launch plan for one histogram call shape.
+enum PlanKind { kEventByEvent = 0, kBinCentre = 1 };
 struct Plan {
+    int32_t kind = kEventByEvent;
     std::vector<int32_t> sample_ids;
     int32_t point_begin = 0, n_points = 0, nbins = 0, prec = 0, pt = 0, chunk = 0;
     int64_t n_hist = 0;
@@ -45,6 +48,14 @@ struct Plan {
     cudaGraph_t graph_t = nullptr;
     cudaGraphExec_t exec_t = nullptr;
     cudaGraphNode_t t_hist_node = nullptr, t_final_node = nullptr, t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // bin-centre plans: true-energy binning, probability table and its rows
+    double t_lo = 0, t_hi = 0;
+    int32_t t_nbins = 0, n_rows = 0;
+    BcRow *d_rows = nullptr;
+    int32_t *d_rowmap = nullptr;
+    void *d_tab = nullptr;
+    int32_t table_grid = 0;
+    cudaGraphNode_t n_table_node = nullptr;
     uint64_t last_use = 0;
 };
 

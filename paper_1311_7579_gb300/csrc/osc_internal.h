@@ -33,13 +33,16 @@ enum PC32 : int {
     C32_S1, C32_PI1, C32_W1, C32_E1,             // ... sorted root 1
     C32_ESCALE,
     C32_CH = 32,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
-    C32_STRIDE = 32 + 54 + 10                    // = 96 floats, 384 B
+    C32_LU = 96,                                 // U[f][l] (re, im), f flavour, l sorted vacuum root, neutrino
+    C32_STRIDE = 128                             // floats, 512 B
 };
 // FP64 block (doubles).
 enum PC64 : int {
     C64_P0 = 0, C64_P1, C64_Q0, C64_Q1, C64_Q2, C64_T0, C64_C10, C64_SMT, C64_ESCALE, C64_NORM,
     C64_CH = 16,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
-    C64_STRIDE = 16 + 54 + 2                     // = 72 doubles, 576 B
+    C64_LU = 72,                                 // U[f][l] (re, im) as in the FP32 block
+    C64_LD = 90,                                 // sorted vacuum eigenvalues d0 <= d1 <= d2
+    C64_STRIDE = 96                              // doubles, 768 B
 };
 
 // ---- resident sample as seen by a kernel ----------------------------------
@@ -54,7 +57,9 @@ struct SampleDev {
     float hscale_f;           // 2^(F-64): FP32 weight -> fixed-point high word
     double hscale_d;
     int32_t frac_bits;        // F
-    int32_t pad;
+    int32_t n_layers;         // 1: constant density; > 1: the layer tables below
+    const float4 *lay32;      // per layer (k_A rho Y_e, c_L L / (2 pi) hi, lo, 0)
+    const double2 *lay64;     // per layer (k_A rho Y_e, c_L L)
 };
 
 // One unit of histogram work: a point tile of one sample over an event range.
@@ -112,6 +117,25 @@ struct ReweightParams {
     double *out_weight;
 };
 
+// ---- binned (bin-centre) method ---------------------------------------------
+constexpr int kChannels = 18;  // channel ids nubar * 9 + alpha * 3 + beta
+// One row of the bin-centre probability table: P at every true-bin centre for
+// one (sample of the launch, point, channel present in that sample).
+struct BcRow {
+    int32_t sample, point, chan, pad;
+};
+struct BcParams {
+    HistParams h;             // work items, samples, accumulators, E_reco binning, finalize
+    const BcRow *rows;
+    int32_t n_rows;
+    int32_t t_nbins;          // true-energy bins
+    const int32_t *row_map;   // [histogram][channel] -> table row (-1: channel absent)
+    double t_lo, t_w;         // first true-bin edge and bin width (t_hi - t_lo) / t_nbins
+    float t_lo_f, t_inv_f, t_nb_f;
+    float *tab32;             // [n_rows][t_nbins] FP32 / FP32_F64EIG probabilities
+    double *tab64;            // [n_rows][t_nbins] FP64 probabilities
+};
+
 // Launch helpers implemented in the kernel translation units.
 enum Prec { kFP64 = 0, kFP32 = 1, kMix = 2 };  // kMix: FP64 eigen-solve and phases, FP32 amplitude
 cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
@@ -121,6 +145,8 @@ cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
 // Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
 const void *hist_kernel_fn(int prec, int pt);
+const void *bc_table_kernel_fn(int prec);
+const void *bc_hist_kernel_fn(int prec);
 const void *final_kernel_fn();
 int hist_threads();
 

@@ -107,9 +107,35 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
             c32[C32_E0 + o] = (float)(z[l] * aj * ak);
         }
         c32[C32_D0] = (float)d[0]; c32[C32_D1] = (float)d[1]; c32[C32_D2] = (float)d[2];
+        c64[C64_LD] = d[0]; c64[C64_LD + 1] = d[1]; c64[C64_LD + 2] = d[2];
         c32[C32_G01] = (float)(d[0] - d[1]); c32[C32_G02] = (float)(d[0] - d[2]); c32[C32_G12] = (float)(d[1] - d[2]);
         split_ff(d[1] - d[0], &c32[C32_V1H], &c32[C32_V1L]);
         split_ff(d[2] - d[0], &c32[C32_V2H], &c32[C32_V2L]);
+    }
+    if (warp == 2 && lane >= 1 && lane <= 9) {
+        // PMNS entry U[f][m] with its mass column m in the sorted vacuum order
+        // (normal ordering 0, dm21, dm31; inverted dm31, 0, dm21), for the
+        // mass-basis propagation through layered matter
+        const int f = (lane - 1) / 3, l = (lane - 1) % 3;
+        const int m = (dm31 > 0) ? l : (l + 2) % 3;
+        double ur, ui;
+        if (f == 0) {
+            ur = (m == 0) ? c12 * c13 : (m == 1) ? s12 * c13 : s13 * cd;
+            ui = (m == 2) ? -s13 * sd : 0.0;
+        } else if (m == 2) {
+            ur = (f == 1) ? s23 * c13 : c23 * c13;
+            ui = 0.0;
+        } else {
+            // mu, tau rows: a - b s13 e^{+i delta}
+            const double a = (f == 1) ? ((m == 0) ? -s12 * c23 : c12 * c23) : ((m == 0) ? s12 * s23 : -c12 * s23);
+            const double b = (f == 1) ? ((m == 0) ? c12 * s23 : s12 * s23) : ((m == 0) ? c12 * c23 : s12 * c23);
+            ur = a - b * s13 * cd;
+            ui = -b * s13 * sd;
+        }
+        c32[C32_LU + 2 * (lane - 1)] = (float)ur;
+        c32[C32_LU + 2 * (lane - 1) + 1] = (float)ui;
+        c64[C64_LU + 2 * (lane - 1)] = ur;
+        c64[C64_LU + 2 * (lane - 1) + 1] = ui;
     }
     if (warp == 2 && lane == 0) {
         c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10;

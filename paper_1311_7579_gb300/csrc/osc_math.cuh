@@ -153,15 +153,22 @@ __device__ __forceinline__ float amplitude2_32(const Pt32 &c, const Ch32 &h, flo
     return fmaf(Sr, Sr, Si * Si);
 }
 
+// Matter shifts delta_l = lambda_l - d_l of the three sorted eigenvalues (FP32):
+// trigonometric seed, then one Newton step on each lower root's shifted cubic;
+// the top shift follows from the trace (sum of shifts = A).
+__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
+    float m0, m1, t3;
+    seed_roots32(c, A, m0, m1, t3);
+    dl0 = shifted_newton(t3 + m0 - c.d0, A, c.S0, c.PI0, c.W0, c.E0);
+    dl1 = shifted_newton(t3 + m1 - c.d1, A, c.S1, c.PI1, c.W1, c.E1);
+    dl2 = A - dl0 - dl1;
+}
+
 // P(alpha -> beta) for one event and one point, FP32 bulk.  A: signed matter
 // term [eV^2]; (th, tl): c_L L / (2 pi E_true) as float-float.
 __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl) {
-    float m0, m1, t3;
-    seed_roots32(c, A, m0, m1, t3);
-    // matter shifts from the vacuum eigenvalues: Newton on the shifted cubics
-    const float dl0 = shifted_newton(t3 + m0 - c.d0, A, c.S0, c.PI0, c.W0, c.E0);
-    const float dl1 = shifted_newton(t3 + m1 - c.d1, A, c.S1, c.PI1, c.W1, c.E1);
-    const float dl2 = A - dl0 - dl1;  // trace: sum of shifts = A
+    float dl0, dl1, dl2;
+    shifts32(c, A, dl0, dl1, dl2);
     const float L1 = c.d1 + dl1, L2 = c.d2 + dl2;
     const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
     // half phases relative to root 0: pi * revolutions
@@ -179,8 +186,10 @@ struct Ch64 {
     double Xr, Xi, Yr, Yi, Zr, Zi, ee, diag;
 };
 
-// P(alpha -> beta); A signed matter term [eV^2], tau = c_L L / E_true.
-__device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double A, double tau) {
+// Ascending roots m0 <= m1 <= m2 of the depressed characteristic cubic
+// mu^3 + p mu + q (lambda = mu + t3, t3 = (T0 + A) / 3): Viete's trigonometric
+// form, each root polished by one Newton step.
+__device__ __forceinline__ void roots64(const Pt64 &c, double A, double &m0, double &m1, double &m2, double &t3) {
     const double p = fma(fma(A, -1.0 / 3.0, c.p1), A, c.p0);
     const double q = fma(fma(fma(A, -2.0 / 27.0, c.q2), A, c.q1), A, c.q0);
     const double mp3 = fmax(-p / 3.0, 1e-300);
@@ -191,11 +200,19 @@ __device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double
     double sn, cs;
     sincos(th3, &sn, &cs);
     const double rc = r * cs, rsn = r * sn * 1.7320508075688772935;
-    double m0 = -rc - rsn, m1 = -rc + rsn, m2 = 2.0 * rc;  // ascending roots of mu^3 + p mu + q
+    m0 = -rc - rsn;
+    m1 = -rc + rsn;
+    m2 = 2.0 * rc;
     m0 -= fma(fma(m0, m0, p), m0, q) / fma(3.0 * m0, m0, p);
     m1 -= fma(fma(m1, m1, p), m1, q) / fma(3.0 * m1, m1, p);
     m2 -= fma(fma(m2, m2, p), m2, q) / fma(3.0 * m2, m2, p);
-    const double t3 = (c.T0 + A) / 3.0;
+    t3 = (c.T0 + A) / 3.0;
+}
+
+// P(alpha -> beta); A signed matter term [eV^2], tau = c_L L / E_true.
+__device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double A, double tau) {
+    double m0, m1, m2, t3;
+    roots64(c, A, m0, m1, m2, t3);
     const double L0 = m0 + t3, L1 = m1 + t3, L2 = m2 + t3;
     const double g01 = m0 - m1, g02 = m0 - m2, g12 = m1 - m2;
     const double iD0 = 1.0 / (g01 * g02), iD1 = -1.0 / (g01 * g12), iD2 = 1.0 / (g02 * g12);
@@ -223,17 +240,27 @@ __device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double
 // depressed cubic, FP64 phase differences tau (mu_l - mu_0) reduced modulo 2 pi
 // in FP64, then the same FP32 amplitude.  Ad: signed matter term [eV^2];
 // trev = c_L L / (2 pi E) [revolutions per eV^2].
-__device__ __forceinline__ float prob_mix(const Pt32 &c, const Ch32 &h, const Pt64 &c64, double Ad, double trev) {
-    const float A = (float)Ad;
+// Depressed-cubic roots for the FP64-eigenvalue variant: FP32 trigonometric
+// seed, one FP64 Newton step per lower root (the small correction divided in
+// FP32), the top root from the zero sum of the depressed roots.
+__device__ __forceinline__ void roots_mix(const Pt32 &c, const Pt64 &c64, double Ad, double &m0, double &m1,
+                                          double &m2, double &t3) {
     float s0, s1, t3f;
-    seed_roots32(c, A, s0, s1, t3f);
+    seed_roots32(c, (float)Ad, s0, s1, t3f);
     const double p = fma(fma(Ad, -1.0 / 3.0, c64.p1), Ad, c64.p0);
     const double q = fma(fma(fma(Ad, -2.0 / 27.0, c64.q2), Ad, c64.q1), Ad, c64.q0);
-    double m0 = (double)s0, m1 = (double)s1;
+    m0 = (double)s0;
+    m1 = (double)s1;
     m0 -= (double)((float)fma(fma(m0, m0, p), m0, q) / (float)fma(3.0 * m0, m0, p));
     m1 -= (double)((float)fma(fma(m1, m1, p), m1, q) / (float)fma(3.0 * m1, m1, p));
-    const double m2 = -m0 - m1;  // depressed roots sum to zero
-    const double t3 = (c64.T0 + Ad) * (1.0 / 3.0);
+    m2 = -m0 - m1;
+    t3 = (c64.T0 + Ad) * (1.0 / 3.0);
+}
+
+__device__ __forceinline__ float prob_mix(const Pt32 &c, const Ch32 &h, const Pt64 &c64, double Ad, double trev) {
+    const float A = (float)Ad;
+    double m0, m1, m2, t3;
+    roots_mix(c, c64, Ad, m0, m1, m2, t3);
     const float L1 = (float)(m1 + t3), L2 = (float)(m2 + t3);
     const float g01 = (float)(m0 - m1), g02 = (float)(m0 - m2), g12 = (float)(m1 - m2);
     // phase differences in revolutions, reduced in FP64, then half angles [rad]

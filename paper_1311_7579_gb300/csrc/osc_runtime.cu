@@ -262,6 +262,9 @@ static void free_plan(osc_ctx *c, Plan *p) {
     dfree(c, p->d_items);
     dfree(c, p->d_samples);
     dfree(c, p->d_hmeta);
+    dfree(c, p->d_rows);
+    dfree(c, p->d_rowmap);
+    dfree(c, p->d_tab);
     delete p;
 }
 
@@ -363,6 +366,7 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     if (!(d->ye >= 0 && d->ye <= 1)) return fail(ctx, OSC_E_RANGE, "Y_e must be in [0, 1]");
     const int64_t n = d->n;
     double wsum = 0.0, wmax = 0.0;
+    uint32_t mask = 0;
     std::vector<uint8_t> ch((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         const float e = d->e_true[i], r = d->e_reco[i], w = d->w_mc[i];
@@ -382,6 +386,7 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
             return fail(ctx, OSC_E_RANGE, o.str());
         }
         ch[i] = (uint8_t)chan_id(d->flav_in[i], d->flav_out[i], d->is_nubar[i]);
+        mask |= 1u << ch[i];
         wsum += std::fabs((double)w);
         wmax = std::max(wmax, std::fabs((double)w));
     }
@@ -410,6 +415,7 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     s->rho = d->density_gcc;
     s->ye = d->ye;
     s->frac_bits = F;
+    s->chan_mask = mask;
     osc_status st = OSC_OK;
     void *p;
     if ((st = dalloc(ctx, &p, n_pad * sizeof(float4))) == OSC_OK) s->ev = (float4 *)p;
@@ -437,7 +443,9 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     sd.hscale_d = std::ldexp(1.0, F - 64);
     sd.hscale_f = (float)sd.hscale_d;
     sd.frac_bits = F;
-    sd.pad = 0;
+    sd.n_layers = 1;
+    sd.lay32 = nullptr;
+    sd.lay64 = nullptr;
     s->id = ctx->next_id++;
     ctx->samples[s->id] = s;
     *sample_id = s->id;
@@ -644,25 +652,43 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     return (int32_t)c;
 }
 
+// Keep at most 16 cached plans: evict the least recently used one.
+static void evict_plan_if_full(osc_ctx *ctx) {
+    if (ctx->plans.size() < 16) return;
+    auto victim = std::min_element(ctx->plans.begin(), ctx->plans.end(),
+                                   [](Plan *a, Plan *b) { return a->last_use < b->last_use; });
+    cudaStreamSynchronize(ctx->stream);
+    free_plan(ctx, *victim);
+    ctx->plans.erase(victim);
+}
+
+// Per-histogram finalize metadata: (2^(64-F), 2^-F, unused, point index).
+static std::vector<double> hist_meta(const std::vector<const Sample *> &ss, int32_t point_begin, int32_t n_points) {
+    std::vector<double> hmeta(ss.size() * (size_t)n_points * 4);
+    for (size_t s = 0; s < ss.size(); ++s)
+        for (int32_t q = 0; q < n_points; ++q) {
+            const int64_t h = (int64_t)s * n_points + q;
+            const int F = ss[s]->frac_bits;
+            hmeta[4 * h] = std::ldexp(1.0, 64 - F);
+            hmeta[4 * h + 1] = std::ldexp(1.0, -F);
+            hmeta[4 * h + 2] = 0.0;
+            hmeta[4 * h + 3] = (double)(point_begin + q);
+        }
+    return hmeta;
+}
+
 static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t point_begin, int32_t n_points,
                            int prec, int32_t nbins, int32_t pt, int32_t chunk, Plan **out) {
     for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it) {
         Plan *p = *it;
-        if (p->sample_ids == ids && p->point_begin == point_begin && p->n_points == n_points && p->prec == prec &&
-            p->nbins == nbins && p->pt == pt && p->chunk == chunk) {
+        if (p->kind == kEventByEvent && p->sample_ids == ids && p->point_begin == point_begin &&
+            p->n_points == n_points && p->prec == prec && p->nbins == nbins && p->pt == pt && p->chunk == chunk) {
             p->last_use = ++ctx->plan_clock;
             *out = p;
             return OSC_OK;
         }
     }
-    // evict the least recently used plan beyond 16
-    if (ctx->plans.size() >= 16) {
-        auto victim = std::min_element(ctx->plans.begin(), ctx->plans.end(),
-                                       [](Plan *a, Plan *b) { return a->last_use < b->last_use; });
-        cudaStreamSynchronize(ctx->stream);
-        free_plan(ctx, *victim);
-        ctx->plans.erase(victim);
-    }
+    evict_plan_if_full(ctx);
     Plan *p = new Plan();
     p->sample_ids = ids;
     p->point_begin = point_begin;
@@ -682,16 +708,7 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     build_items(ss, point_begin, n_points, pt, chunk, 0, items);
     p->n_items = (int32_t)items.size();
     p->grid = hist_grid(ctx, prec, pt, p->n_items);
-    std::vector<double> hmeta((size_t)p->n_hist * 4);
-    for (size_t s = 0; s < ids.size(); ++s)
-        for (int32_t q = 0; q < n_points; ++q) {
-            const int64_t h = (int64_t)s * n_points + q;
-            const int F = ss[s]->frac_bits;
-            hmeta[4 * h] = std::ldexp(1.0, 64 - F);
-            hmeta[4 * h + 1] = std::ldexp(1.0, -F);
-            hmeta[4 * h + 2] = 0.0;
-            hmeta[4 * h + 3] = (double)(point_begin + q);
-        }
+    const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
     void *a;
     osc_status st = OSC_OK;
     if ((st = dalloc(ctx, &a, items.size() * sizeof(WorkItem))) == OSC_OK) p->d_items = (WorkItem *)a;
@@ -877,5 +894,214 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     if (st) return st;
     if (!out_on_device) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return OSC_OK;
+}
+
+// ------------------------------------------------------ bin-centre method
+// Work items of one point each, event ranges outermost so that the warps
+// running at the same time read the same events for different points (L2 reuse).
+static void build_items_bc(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points,
+                           int32_t chunk, std::vector<WorkItem> &items) {
+    for (size_t s = 0; s < ss.size(); ++s)
+        for (int64_t e = 0; e < ss[s]->n; e += chunk)
+            for (int32_t q = 0; q < n_points; ++q) {
+                WorkItem w;
+                w.sample = (int32_t)s;
+                w.point_base = point_base + q;
+                w.n_pts = 1;
+                w.ev_count = (int32_t)std::min<int64_t>(chunk, ss[s]->n - e);
+                w.ev_begin = e;
+                w.acc_base = (int64_t)s * n_points + q;
+                items.push_back(w);
+            }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const WorkItem &a, const WorkItem &b) { return a.ev_count > b.ev_count; });
+}
+
+static osc_status get_bc_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t point_begin, int32_t n_points,
+                              int prec, int32_t nbins, double t_lo, double t_hi, int32_t t_nbins, Plan **out) {
+    for (Plan *p : ctx->plans)
+        if (p->kind == kBinCentre && p->sample_ids == ids && p->point_begin == point_begin &&
+            p->n_points == n_points && p->prec == prec && p->nbins == nbins && p->t_lo == t_lo && p->t_hi == t_hi &&
+            p->t_nbins == t_nbins) {
+            p->last_use = ++ctx->plan_clock;
+            *out = p;
+            return OSC_OK;
+        }
+    evict_plan_if_full(ctx);
+    std::vector<const Sample *> ss;
+    std::vector<SampleDev> sdev;
+    int64_t ev = 0;
+    for (int32_t id : ids) {
+        ss.push_back(ctx->samples[id]);
+        sdev.push_back(ctx->samples[id]->dev);
+        ev += ctx->samples[id]->n;
+    }
+    // table rows: (sample, point, channel present in the sample)
+    const int64_t n_hist = (int64_t)ids.size() * n_points;
+    std::vector<BcRow> rows;
+    std::vector<int32_t> rowmap((size_t)n_hist * kChannels, -1);
+    for (size_t s = 0; s < ss.size(); ++s)
+        for (int32_t q = 0; q < n_points; ++q)
+            for (int c = 0; c < kChannels; ++c)
+                if (ss[s]->chan_mask >> c & 1u) {
+                    rowmap[((int64_t)s * n_points + q) * kChannels + c] = (int32_t)rows.size();
+                    rows.push_back(BcRow{(int32_t)s, point_begin + q, c, 0});
+                }
+    const size_t tab_bytes = rows.size() * (size_t)t_nbins * (prec == kFP64 ? 8 : 4);
+    // one item per ~4 resident warps' worth of events, a multiple of 128 (32 lanes x 4 records)
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bc_hist_kernel_fn(prec), hist_threads(), 0);
+    per_sm = std::max(per_sm, 1);
+    const int64_t warps = (int64_t)ctx->n_sm * per_sm * (hist_threads() / 32);
+    int64_t chunk = (ev * n_points + 4 * warps - 1) / (4 * warps);
+    chunk = std::max<int64_t>(128, std::min<int64_t>((chunk + 127) / 128 * 128, 1 << 20));
+    std::vector<WorkItem> items;
+    build_items_bc(ss, point_begin, n_points, (int32_t)chunk, items);
+
+    Plan *p = new Plan();
+    p->kind = kBinCentre;
+    p->sample_ids = ids;
+    p->point_begin = point_begin;
+    p->n_points = n_points;
+    p->prec = prec;
+    p->nbins = nbins;
+    p->pt = 1;
+    p->chunk = (int32_t)chunk;
+    p->n_hist = n_hist;
+    p->t_lo = t_lo;
+    p->t_hi = t_hi;
+    p->t_nbins = t_nbins;
+    p->n_rows = (int32_t)rows.size();
+    p->n_items = (int32_t)items.size();
+    p->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->n_sm * per_sm, p->n_items));
+    const int64_t tab_n = (int64_t)rows.size() * t_nbins;
+    p->table_grid = (int)std::max<int64_t>(1, std::min<int64_t>((tab_n + 255) / 256, (int64_t)ctx->n_sm * 8));
+    const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
+    void *a;
+    osc_status st = OSC_OK;
+    if ((st = dalloc(ctx, &a, items.size() * sizeof(WorkItem))) == OSC_OK) p->d_items = (WorkItem *)a;
+    if (!st && (st = dalloc(ctx, &a, sdev.size() * sizeof(SampleDev))) == OSC_OK) p->d_samples = (SampleDev *)a;
+    if (!st && (st = dalloc(ctx, &a, hmeta.size() * sizeof(double))) == OSC_OK) p->d_hmeta = (double *)a;
+    if (!st && (st = dalloc(ctx, &a, rows.size() * sizeof(BcRow))) == OSC_OK) p->d_rows = (BcRow *)a;
+    if (!st && (st = dalloc(ctx, &a, rowmap.size() * sizeof(int32_t))) == OSC_OK) p->d_rowmap = (int32_t *)a;
+    if (!st && (st = dalloc(ctx, &a, tab_bytes)) == OSC_OK) p->d_tab = a;
+    if (st) {
+        free_plan(ctx, p);
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(p->d_samples, sdev.data(), sdev.size() * sizeof(SampleDev), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(p->d_hmeta, hmeta.data(), hmeta.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(p->d_rows, rows.data(), rows.size() * sizeof(BcRow), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(p->d_rowmap, rowmap.data(), rowmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e) {
+        free_plan(ctx, p);
+        return fail_cuda(ctx, e, "cudaMemcpy(bin-centre plan)");
+    }
+    p->last_use = ++ctx->plan_clock;
+    ctx->plans.push_back(p);
+    *out = p;
+    return OSC_OK;
+}
+
+// CUDA graph: table kernel -> histogram kernel (-> finalize kernel for large outputs).
+static osc_status run_bc_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *d_out) {
+    BcParams bp;
+    fill_hist_params(bp.h, p->d_items, p->n_items, p->d_samples, ctx->d_pc32, ctx->d_pc64, ctx->d_acc,
+                     ctx->d_counter, p->nbins, lo, hi);
+    bp.rows = p->d_rows;
+    bp.n_rows = p->n_rows;
+    bp.t_nbins = p->t_nbins;
+    bp.row_map = p->d_rowmap;
+    bp.t_lo = p->t_lo;
+    bp.t_w = (p->t_hi - p->t_lo) / (double)p->t_nbins;
+    bp.t_lo_f = (float)p->t_lo;
+    bp.t_inv_f = (float)((double)p->t_nbins / (p->t_hi - p->t_lo));
+    bp.t_nb_f = (float)p->t_nbins;
+    bp.tab32 = p->prec == kFP64 ? nullptr : (float *)p->d_tab;
+    bp.tab64 = p->prec == kFP64 ? (double *)p->d_tab : nullptr;
+    const bool fused = fuse_finalize(p->n_hist, p->nbins);
+    if (fused) {
+        bp.h.fuse_final = 1;
+        bp.h.fin_n_hist = p->n_hist;
+        bp.h.fin_hmeta = p->d_hmeta;
+        bp.h.fin_out = d_out;
+    }
+    FinalParams fp{ctx->d_acc, p->d_hmeta, ctx->d_pc64, d_out, p->n_hist, p->nbins, ctx->d_counter};
+    void *targs[] = {&bp};
+    void *hargs[] = {&bp};
+    void *fargs[] = {&fp};
+    cudaKernelNodeParams kt{};
+    kt.func = (void *)bc_table_kernel_fn(p->prec);
+    kt.gridDim = dim3(p->table_grid);
+    kt.blockDim = dim3(256);
+    kt.kernelParams = targs;
+    cudaKernelNodeParams kh{};
+    kh.func = (void *)bc_hist_kernel_fn(p->prec);
+    kh.gridDim = dim3(p->grid);
+    kh.blockDim = dim3(hist_threads());
+    kh.kernelParams = hargs;
+    cudaKernelNodeParams kf{};
+    kf.func = (void *)final_kernel_fn();
+    const int64_t nfin = p->n_hist * (int64_t)p->nbins;
+    kf.gridDim = dim3((unsigned)std::min<int64_t>(std::max<int64_t>((nfin + 255) / 256, 1), (int64_t)ctx->n_sm * 8));
+    kf.blockDim = dim3(256);
+    kf.kernelParams = fargs;
+    if (!p->exec) {
+        CK(cudaGraphCreate(&p->graph, 0));
+        CK(cudaGraphAddKernelNode(&p->n_table_node, p->graph, nullptr, 0, &kt));
+        CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, &p->n_table_node, 1, &kh));
+        if (!fused) CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
+        CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
+    } else {
+        CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_table_node, &kt));
+        CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_hist_node, &kh));
+        if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
+    }
+    CK(cudaGraphLaunch(p->exec, ctx->stream));
+    ctx->launches += fused ? 2 : 3;
+    return OSC_OK;
+}
+
+extern "C" osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                                               int32_t point_begin, int32_t n_points, osc_precision prec,
+                                               double t_lo, double t_hi, int32_t t_nbins, double lo, double hi,
+                                               int32_t nbins, double *out, int out_on_device) {
+    CHECK_CTX(ctx);
+    if (!sample_ids || !out) return fail(ctx, OSC_E_ARG, "null argument");
+    if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
+        return fail(ctx, OSC_E_ARG, "bad precision");
+    if (n_samples < 1 || n_samples > 4096) return fail(ctx, OSC_E_ARG, "n_samples must be in [1, 4096]");
+    if (nbins < 1 || nbins > (1 << 20)) return fail(ctx, OSC_E_ARG, "nbins must be in [1, 2^20]");
+    if (t_nbins < 1 || t_nbins > 65536) return fail(ctx, OSC_E_ARG, "t_nbins must be in [1, 65536]");
+    if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo)) return fail(ctx, OSC_E_RANGE, "need finite lo < hi");
+    if (!(std::isfinite(t_lo) && std::isfinite(t_hi) && t_hi > t_lo))
+        return fail(ctx, OSC_E_RANGE, "need finite t_lo < t_hi");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if (n_points < 1 || point_begin < 0 || (int64_t)point_begin + n_points > (int64_t)ctx->pts.size())
+        return fail(ctx, OSC_E_ARG, "point range outside the parameter table");
+    std::vector<int32_t> ids(sample_ids, sample_ids + n_samples);
+    for (int32_t id : ids)
+        if (!ctx->samples.count(id)) return fail(ctx, OSC_E_ARG, "unknown sample id");
+    const int pr = prec_kind(prec);
+    const int64_t bins = (int64_t)n_samples * n_points * nbins;
+    osc_status st = ensure_acc(ctx, bins);
+    if (st) return st;
+    Plan *p;
+    st = get_bc_plan(ctx, ids, point_begin, n_points, pr, nbins, t_lo, t_hi, t_nbins, &p);
+    if (st) return st;
+    double *d_out = out;
+    if (!out_on_device) {
+        st = ensure_buf(ctx, &ctx->d_out, &ctx->out_cap, bins);
+        if (st) return st;
+        d_out = ctx->d_out;
+    }
+    st = run_bc_plan(ctx, p, lo, hi, d_out);
+    if (st) return st;
+    if (!out_on_device) {
+        CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     return OSC_OK;
 }
