@@ -165,6 +165,26 @@ osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *sample_ids, int
                                     double t_lo, double t_hi, int32_t t_nbins, double lo, double hi,
                                     int32_t nbins, double *out, int out_on_device);
 
+/* Piecewise-constant matter along the baseline.  Sec. 1.1 takes the density
+ * as constant; this generalises it (the paper has no layered case).  The
+ * sample's path becomes n_layers layers traversed in the given order from the
+ * source: layer k has length length_km[k] > 0, density density_gcc[k] >= 0
+ * [g/cm^3] and electron fraction ye[k] in [0, 1].  Then
+ *   P(alpha -> beta) = |[S_{n-1} ... S_1 S_0]_{beta alpha}|^2,
+ *   S_k = exp(-i c_L M(A_k) L_k / E_true),  A_k = k_A ye_k rho_k E_true.
+ * This replaces the baseline, density and Y_e given at load.
+ *   - n_layers == 1 sets a constant-density path, served by the single-layer
+ *     kernels.
+ *   - 2 <= n_layers <= 16 routes osc_reweight, osc_histogram and
+ *     osc_histogram_bin_centre for this sample to the layered kernels.  These
+ *     kernels run one point per warp; osc_set_tile does not apply to them.
+ * The serving loop handles single-layer samples only: osc_submit returns
+ * OSC_E_ARG for a layered sample.  This call returns OSC_E_STATE while serving
+ * runs.  Arrays are host memory; the call copies them and drops cached launch
+ * plans. */
+osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, const double *length_km,
+                          const double *density_gcc, const double *ye);
+
 /* Launch-shape control.  points_per_block in {1, 4, 16, 64, 256}, or 0 to let
  * the autotuner choose per workload class (default); events_per_item a positive
  * multiple of 64, or 0 for the default.  Results never depend on either. */
@@ -200,6 +220,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
                       uint64_t *ticket);
 /* osc_submit validates the point and sample on the calling thread and queues
  * the request (OSC_E_BUSY beyond 2^20 queued requests); the ticket is > 0.
+ * A layered sample (osc_set_layers with n_layers > 1) gives OSC_E_ARG.
  * osc_wait waits for a ticket's histogram (host buffer of nbins doubles) and
  * releases it; latency_us (may be NULL) receives the submit-to-completion time.
  * timeout_ms < 0 waits forever; OSC_E_TIMEOUT when the time runs out; OSC_E_ARG

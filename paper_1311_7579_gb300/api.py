@@ -27,7 +27,7 @@ ENTRY_POINTS = [
     "osc_version", "osc_create", "osc_destroy", "osc_last_error", "osc_load_sample", "osc_unload_sample",
     "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
     "osc_last_timing", "osc_timing_totals", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
-    "osc_serve_stop", "osc_histogram_noalloc", "osc_histogram_bin_centre",
+    "osc_serve_stop", "osc_histogram_noalloc", "osc_histogram_bin_centre", "osc_set_layers",
 ]
 
 
@@ -80,6 +80,7 @@ def load_library(path):
                                ctypes.c_int]),
         "osc_histogram_bin_centre": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, d, d,
                                           i32, vp, ctypes.c_int]),
+        "osc_set_layers": (st, [vp, i32, i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
         "osc_set_tile": (st, [vp, i32, i32]),
         "osc_enable_timing": (st, [vp, ctypes.c_int]),
         "osc_last_timing": (st, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
@@ -210,6 +211,14 @@ def osc_histogram_bin_centre(ctx, sample_ids, point_begin, n_points, prec, t_lo,
                                                float(t_hi), int(t_nbins), float(lo), float(hi), int(nbins),
                                                _ptr(out), 1 if dev else 0))
     return out
+
+
+def osc_set_layers(ctx, sample_id, layers):
+    """layers: sequence of (length_km, density_gcc, ye) in the order of travel."""
+    arr = np.ascontiguousarray(np.asarray(layers, dtype=np.float64).reshape(-1, 3))
+    cols = [np.ascontiguousarray(arr[:, k]) for k in range(3)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, lib().osc_set_layers(ctx, int(sample_id), arr.shape[0], *[c.ctypes.data_as(dp) for c in cols]))
 
 
 def osc_set_tile(ctx, points_per_block=0, events_per_item=0):

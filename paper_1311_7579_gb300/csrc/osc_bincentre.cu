@@ -9,7 +9,7 @@
 //               accumulators as the event-by-event kernel.
 // The table is tiny next to the event stream, so the histogram kernel is bound
 // by reading the 16-byte event records: four records per lane are in flight.
-#include "osc_kernels.cuh"
+#include "osc_layers.cuh"
 
 namespace osc {
 
@@ -25,6 +25,25 @@ __global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
         // centre t_lo + (t + 1/2) w in double (no contraction), stored in FP32 like an event energy
         const float E = __double2float_rn(__dadd_rn(b.t_lo, __dmul_rn((double)t + 0.5, b.t_w)));
         const int ch = rw.chan;
+        if (sd.n_layers > 1) {
+            // layered path: the sample's layer sequence, same precision split
+            const double *pc64 = b.h.pc64 + (int64_t)rw.point * C64_STRIDE;
+            Pt64 c64;
+            load_pt64(pc64, c64);
+            if (PREC == kFP64) {
+                LayU<double> u;
+                load_layu(pc64 + C64_LU, ch >= 9, u);
+                b.tab64[idx] = prob_layers64(c64, pc64 + C64_LD, u, sd, ch, E);
+            } else {
+                const float *pc = b.h.pc32 + (int64_t)rw.point * C32_STRIDE;
+                Pt32 c;
+                load_pt32(pc, c);
+                LayU<float> u;
+                load_layu(pc + C32_LU, ch >= 9, u);
+                b.tab32[idx] = prob_layers32<PREC>(c, c64, pc64 + C64_LD, u, sd, ch, E);
+            }
+            continue;
+        }
         if (PREC == kFP32) {
             const float *pc = b.h.pc32 + (int64_t)rw.point * C32_STRIDE;
             Pt32 c;

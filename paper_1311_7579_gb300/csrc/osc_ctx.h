@@ -27,11 +27,12 @@ struct Sample {
     uint32_t chan_mask = 0;  // bit c set when channel id c occurs in the sample
     float4 *ev = nullptr;
     int32_t *perm = nullptr;
+    void *lay = nullptr;     // layered path: float4[n_layers] then double2[n_layers]
     SampleDev dev{};
 };
 
 // A cached launch plan for one histogram call shape.
-enum PlanKind { kEventByEvent = 0, kBinCentre = 1 };
+enum PlanKind { kEventByEvent = 0, kBinCentre = 1, kLayered = 2 };
 struct Plan {
     int32_t kind = kEventByEvent;
     std::vector<int32_t> sample_ids;
@@ -117,7 +118,7 @@ void dfree(osc_ctx *c, void *p);
 osc_status validate_point(osc_ctx *c, const osc_point &p, int index);
 osc_status ensure_acc(osc_ctx *c, int64_t bins);
 // grid of the persistent histogram kernel; finalize fusion rule
-int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items);
+int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items);
 bool fuse_finalize(int64_t n_hist, int32_t nbins);
 int prec_kind(osc_precision p);
 cudaEvent_t pool_event(osc_ctx *c);

@@ -117,6 +117,8 @@ struct ReweightParams {
     double *out_weight;
 };
 
+constexpr int kMaxLayers = 16;  // layers of a piecewise-constant matter path
+
 // ---- binned (bin-centre) method ---------------------------------------------
 constexpr int kChannels = 18;  // channel ids nubar * 9 + alpha * 3 + beta
 // One row of the bin-centre probability table: P at every true-bin centre for
@@ -147,6 +149,8 @@ cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
 const void *hist_kernel_fn(int prec, int pt);
 const void *bc_table_kernel_fn(int prec);
 const void *bc_hist_kernel_fn(int prec);
+const void *layers_hist_kernel_fn(int prec);
+cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream_t st);
 const void *final_kernel_fn();
 int hist_threads();
 

@@ -83,12 +83,22 @@ __device__ __forceinline__ void layer_update(T pr[3], T pi[3], const LayU<T> &u,
     }
 }
 
+// Entry (f, l) of U~ for a flavour f known only at run time, by selects (an
+// indexed register array would go to local memory).
+template <typename T>
+__device__ __forceinline__ void u_entry(const LayU<T> &u, int f, int l, T &re, T &im) {
+    re = (f == 0) ? u.r[l] : (f == 1) ? u.r[3 + l] : u.r[6 + l];
+    im = (f == 0) ? u.i[l] : (f == 1) ? u.i[3 + l] : u.i[6 + l];
+}
+
 template <typename T>
 __device__ __forceinline__ void layer_init(T pr[3], T pi[3], const LayU<T> &u, int alpha) {
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        pr[l] = u.r[3 * alpha + l];
-        pi[l] = -u.i[3 * alpha + l];
+        T ur, ui;
+        u_entry(u, alpha, l, ur, ui);
+        pr[l] = ur;
+        pi[l] = -ui;
     }
 }
 
@@ -97,11 +107,21 @@ __device__ __forceinline__ T layer_prob(const T pr[3], const T pi[3], const LayU
     T ar = 0, ai = 0;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        const T ur = u.r[3 * beta + l], ui = u.i[3 * beta + l];
+        T ur, ui;
+        u_entry(u, beta, l, ur, ui);
         ar += ur * pr[l] - ui * pi[l];
         ai += ur * pi[l] + ui * pr[l];
     }
     return ar * ar + ai * ai;
+}
+
+// Constants of layer k; a single-layer sample in a layered launch has no layer
+// table and uses its own path constants.
+__device__ __forceinline__ float4 layer32(const SampleDev &sd, int k) {
+    return sd.lay32 ? sd.lay32[k] : make_float4(sd.kA_rhoye_f, sd.rev_hi, sd.rev_lo, 0.0f);
+}
+__device__ __forceinline__ double2 layer64(const SampleDev &sd, int k) {
+    return sd.lay64 ? sd.lay64[k] : make_double2(sd.kA_rhoye, sd.cLL);
 }
 
 // P(alpha -> beta) through the sample's layers, FP32 bulk (PREC == kFP32) or with
@@ -118,7 +138,7 @@ __device__ __forceinline__ float prob_layers32(const Pt32 &c, const Pt64 &c64, c
     for (int k = 0; k < sd.n_layers; ++k) {
         float dl1, dl2, h1, h2;
         if (PREC == kFP32) {
-            const float4 ly = sd.lay32[k];
+            const float4 ly = layer32(sd, k);
             const float A = nubar ? -(ly.x * E) : ly.x * E;
             const float th = ly.y * r0;
             const float tl = fmaf(ly.y, r0, -th) + fmaf(ly.y, rl, ly.z * r0);
@@ -127,7 +147,7 @@ __device__ __forceinline__ float prob_layers32(const Pt32 &c, const Pt64 &c64, c
             h1 = 3.14159265358979323846f * phase_rev(th, tl, c.v1h, c.v1l, dl1 - dl0);
             h2 = 3.14159265358979323846f * phase_rev(th, tl, c.v2h, c.v2l, dl2 - dl0);
         } else {
-            const double2 ly = sd.lay64[k];
+            const double2 ly = layer64(sd, k);
             const double Ad = nubar ? -(ly.x * (double)E) : ly.x * (double)E;
             double m0, m1, m2, t3;
             roots_mix(c, c64, Ad, m0, m1, m2, t3);
@@ -155,7 +175,7 @@ __device__ __forceinline__ double prob_layers64(const Pt64 &c, const double *d, 
     layer_init(pr, pi, u, ab / 3);
     const double Ed = (double)E;
     for (int k = 0; k < sd.n_layers; ++k) {
-        const double2 ly = sd.lay64[k];
+        const double2 ly = layer64(sd, k);
         const double A = nubar ? -(ly.x * Ed) : ly.x * Ed;
         double m0, m1, m2, t3;
         roots64(c, A, m0, m1, m2, t3);

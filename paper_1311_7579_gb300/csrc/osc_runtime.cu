@@ -121,9 +121,9 @@ static osc_status ensure_buf(osc_ctx *c, double **buf, int64_t *cap, int64_t n) 
     return OSC_OK;
 }
 
-int hist_grid(osc_ctx *c, int prec, int pt, int32_t n_items) {
+int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_kernel_fn(prec, pt), hist_threads(), 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, hist_threads(), 0);
     if (per_sm < 1) per_sm = 1;
     int g = c->n_sm * per_sm;
     return std::max(1, std::min(g, n_items));
@@ -248,9 +248,20 @@ static void sort_events(int64_t n, const uint8_t *ch, const float *er, std::vect
     order.swap(a);
 }
 
+// Single-layer path constants of a sample: matter term and phase scale.
+static void set_path_consts(SampleDev &sd, double L, double rho, double ye) {
+    sd.kA_rhoye = matter_k_A() * rho * ye;
+    sd.cLL = kCL * L;
+    sd.kA_rhoye_f = (float)sd.kA_rhoye;
+    const double rev = kCL * L / kTwoPi;
+    sd.rev_hi = (float)rev;
+    sd.rev_lo = (float)(rev - (double)sd.rev_hi);
+}
+
 static void free_sample(osc_ctx *c, Sample *s) {
     dfree(c, s->ev);
     dfree(c, s->perm);
+    dfree(c, s->lay);
     delete s;
 }
 
@@ -434,12 +445,7 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     sd.ev = s->ev;
     sd.perm = s->perm;
     sd.n = n;
-    sd.kA_rhoye = matter_k_A() * s->rho * s->ye;
-    sd.cLL = kCL * s->L;
-    sd.kA_rhoye_f = (float)sd.kA_rhoye;
-    const double rev = kCL * s->L / kTwoPi;
-    sd.rev_hi = (float)rev;
-    sd.rev_lo = (float)(rev - (double)sd.rev_hi);
+    set_path_consts(sd, s->L, s->rho, s->ye);
     sd.hscale_d = std::ldexp(1.0, F - 64);
     sd.hscale_f = (float)sd.hscale_d;
     sd.frac_bits = F;
@@ -462,6 +468,66 @@ osc_status osc_unload_sample(osc_ctx *ctx, int32_t sample_id) {
     cudaStreamSynchronize(ctx->stream);
     free_sample(ctx, it->second);
     ctx->samples.erase(it);
+    return OSC_OK;
+}
+
+osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, const double *length_km,
+                          const double *density_gcc, const double *ye) {
+    CHECK_CTX(ctx);
+    if (!length_km || !density_gcc || !ye) return fail(ctx, OSC_E_ARG, "null argument");
+    if (n_layers < 1 || n_layers > kMaxLayers) return fail(ctx, OSC_E_ARG, "n_layers must be in [1, 16]");
+    double total = 0.0;
+    for (int k = 0; k < n_layers; ++k) {
+        if (!(is_fin(length_km[k]) && length_km[k] > 0)) return fail(ctx, OSC_E_RANGE, "layer length must be finite and > 0");
+        if (!(is_fin(density_gcc[k]) && density_gcc[k] >= 0)) return fail(ctx, OSC_E_RANGE, "layer density must be finite and >= 0");
+        if (!(ye[k] >= 0 && ye[k] <= 1)) return fail(ctx, OSC_E_RANGE, "layer Y_e must be in [0, 1]");
+        total += length_km[k];
+    }
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    auto it = ctx->samples.find(sample_id);
+    if (it == ctx->samples.end()) return fail(ctx, OSC_E_ARG, "unknown sample id");
+    if (ctx->serve) return fail(ctx, OSC_E_STATE, "cannot change a sample's path while serving runs");
+    Sample *s = it->second;
+    void *lay = nullptr;
+    if (n_layers > 1) {
+        std::vector<float4> l32(n_layers);
+        std::vector<double2> l64(n_layers);
+        for (int k = 0; k < n_layers; ++k) {
+            const double kA = matter_k_A() * density_gcc[k] * ye[k];
+            const double rev = kCL * length_km[k] / kTwoPi;
+            const float rh = (float)rev;
+            l32[k] = make_float4((float)kA, rh, (float)(rev - (double)rh), 0.0f);
+            l64[k] = make_double2(kA, kCL * length_km[k]);
+        }
+        const size_t b32 = n_layers * sizeof(float4);
+        osc_status st = dalloc(ctx, &lay, b32 + n_layers * sizeof(double2));
+        if (st) return st;
+        cudaError_t e = cudaMemcpy(lay, l32.data(), b32, cudaMemcpyHostToDevice);
+        if (!e) e = cudaMemcpy((char *)lay + b32, l64.data(), n_layers * sizeof(double2), cudaMemcpyHostToDevice);
+        if (e) {
+            dfree(ctx, lay);
+            return fail_cuda(ctx, e, "cudaMemcpy(layers)");
+        }
+    }
+    drop_plans(ctx);  // plans hold copies of the sample's path constants
+    cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, s->lay);
+    s->lay = lay;
+    SampleDev &sd = s->dev;
+    if (n_layers == 1) {
+        s->L = length_km[0];
+        s->rho = density_gcc[0];
+        s->ye = ye[0];
+        set_path_consts(sd, s->L, s->rho, s->ye);
+        sd.n_layers = 1;
+        sd.lay32 = nullptr;
+        sd.lay64 = nullptr;
+    } else {
+        s->L = total;
+        sd.n_layers = n_layers;
+        sd.lay32 = (const float4 *)lay;
+        sd.lay64 = (const double2 *)((char *)lay + n_layers * sizeof(float4));
+    }
     return OSC_OK;
 }
 
@@ -607,7 +673,10 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
     rp.norm = ctx->pts[point].norm;
     rp.out_prob = dp;
     rp.out_weight = dw;
-    CK(launch_reweight(prec_kind(prec), rp, ctx->stream));
+    if (s->dev.n_layers > 1)
+        CK(launch_reweight_layers(prec_kind(prec), rp, ctx->stream));
+    else
+        CK(launch_reweight(prec_kind(prec), rp, ctx->stream));
     ctx->launches += 1;
     if (!out_on_device) {
         if (out_prob) CK(cudaMemcpyAsync(out_prob, dp, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -652,6 +721,11 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     return (int32_t)c;
 }
 
+// Histogram kernel of an event-by-event or layered plan.
+static const void *plan_kernel(const Plan *p) {
+    return p->kind == kLayered ? layers_hist_kernel_fn(p->prec) : hist_kernel_fn(p->prec, p->pt);
+}
+
 // Keep at most 16 cached plans: evict the least recently used one.
 static void evict_plan_if_full(osc_ctx *ctx) {
     if (ctx->plans.size() < 16) return;
@@ -678,10 +752,10 @@ static std::vector<double> hist_meta(const std::vector<const Sample *> &ss, int3
 }
 
 static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t point_begin, int32_t n_points,
-                           int prec, int32_t nbins, int32_t pt, int32_t chunk, Plan **out) {
+                           int prec, int32_t nbins, int32_t pt, int32_t chunk, Plan **out, int kind = kEventByEvent) {
     for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it) {
         Plan *p = *it;
-        if (p->kind == kEventByEvent && p->sample_ids == ids && p->point_begin == point_begin &&
+        if (p->kind == kind && p->sample_ids == ids && p->point_begin == point_begin &&
             p->n_points == n_points && p->prec == prec && p->nbins == nbins && p->pt == pt && p->chunk == chunk) {
             p->last_use = ++ctx->plan_clock;
             *out = p;
@@ -690,6 +764,7 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     }
     evict_plan_if_full(ctx);
     Plan *p = new Plan();
+    p->kind = kind;
     p->sample_ids = ids;
     p->point_begin = point_begin;
     p->n_points = n_points;
@@ -707,7 +782,7 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     std::vector<WorkItem> items;
     build_items(ss, point_begin, n_points, pt, chunk, 0, items);
     p->n_items = (int32_t)items.size();
-    p->grid = hist_grid(ctx, prec, pt, p->n_items);
+    p->grid = hist_grid(ctx, plan_kernel(p), p->n_items);
     const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
     void *a;
     osc_status st = OSC_OK;
@@ -740,7 +815,7 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     void *hargs[] = {&hp};
     void *fargs[] = {&fp};
     cudaKernelNodeParams kh{};
-    kh.func = (void *)hist_kernel_fn(p->prec, p->pt);
+    kh.func = (void *)plan_kernel(p);
     kh.gridDim = dim3(p->grid);
     kh.blockDim = dim3(hist_threads());
     kh.kernelParams = hargs;
@@ -844,8 +919,14 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     const int64_t bins = (int64_t)n_samples * n_points * nbins;
     osc_status st = ensure_acc(ctx, bins);
     if (st) return st;
+    bool layered = false;
+    for (int32_t id : ids) layered = layered || ctx->samples[id]->dev.n_layers > 1;
     int32_t pt = ctx->tile_pt, chunk = ctx->tile_chunk;
-    if (pt == 0) {
+    if (layered) {
+        // one point per warp item; the tile setting applies to the single-layer kernels only
+        pt = 1;
+        chunk = default_chunk(ctx, ids, n_points, 1, pr);
+    } else if (pt == 0) {
         // autotune once per workload class, then reuse
         const std::string key = tune_key(ids, n_points, pr, ctx);
         auto it = ctx->tuned.find(key);
@@ -882,7 +963,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     }
     if (chunk == 0) chunk = default_chunk(ctx, ids, n_points, pt, pr);
     Plan *p;
-    st = get_plan(ctx, ids, point_begin, n_points, pr, nbins, pt, chunk, &p);
+    st = get_plan(ctx, ids, point_begin, n_points, pr, nbins, pt, chunk, &p, layered ? kLayered : kEventByEvent);
     if (st) return st;
     double *d_out = out;
     if (!out_on_device) {

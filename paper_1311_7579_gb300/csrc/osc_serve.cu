@@ -163,7 +163,7 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     hp.fin_n_hist = n;
     hp.fin_hmeta = b.d_hmeta;
     hp.fin_out = b.d_out;
-    e = launch_hist(prec, 1, hp, hist_grid(ctx, prec, 1, (n_items + 7) / 8), st);
+    e = launch_hist(prec, 1, hp, hist_grid(ctx, hist_kernel_fn(prec, 1), (n_items + 7) / 8), st);
     FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
     if (!e && !fused) e = launch_final(fp, st);
     if (!e) e = cudaMemcpyAsync(b.h_out, b.d_out, (size_t)n * sv->nbins * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -335,6 +335,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
         if (validate_point(nullptr, *pt, 0) != OSC_OK) return OSC_E_RANGE;
         auto it = ctx->samples.find(sample_id);
         if (it == ctx->samples.end()) return OSC_E_ARG;
+        if (it->second->dev.n_layers > 1) return OSC_E_ARG;  // the serving kernels are single-layer
         r.sd = it->second->dev;
         r.frac_bits = it->second->frac_bits;
     }
