@@ -256,6 +256,83 @@ def mcmc_leg(api, synth, c, sid, sample, n_steps, prec="fp32"):
             "posterior_sd": [float(x) for x in post.std(axis=0)]}
 
 
+def _event_times(torch, stream, flush, fn, k, w):
+    """Per-call device times [ms] of fn() on the library's stream, L2 flushed before each call."""
+    for _ in range(w):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for i in range(k):
+        flush.zero_()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def bin_centre_leg(torch, api, synth, c, sid, sample, point, stream, flush, hbm_peak, k=200):
+    """Binned (bin-centre) method on the bench workload: P at the centre of each
+    event's 25 MeV true-energy bin (410 bins over [0, 10.25) GeV), same E_reco
+    histogram.  Times the whole call (table kernel + histogram kernel); the
+    event stream (16 B per event) over that time is a lower bound of the
+    histogram kernel's bandwidth.  Also the Sec. 1.1.1 25 MeV-bin study."""
+    tb = (0.0, 10.25, 410)
+    out = torch.zeros((1, 1, NBINS), dtype=torch.float64, device=flush.device)
+    api.osc_set_params(c, point)
+    res = {"true_bins": {"lo": tb[0], "hi": tb[1], "n": tb[2]}}
+    for prec in ("fp32", "fp64"):
+        ms = _event_times(torch, stream, flush, lambda: api.osc_histogram_bin_centre(
+            c, [sid], 0, 1, prec, *tb, LO, HI, NBINS, out=out), k, 5)
+        t = float(np.median(ms))
+        res[prec] = {"value": N_EVENTS / (t * 1e-3), "unit": UNIT, "call_ms_p50": t,
+                     "event_stream_gbs": 16.0 * N_EVENTS / (t * 1e-3) / 1e9}
+        if hbm_peak:
+            res[prec]["event_stream_frac_of_measured_hbm"] = res[prec]["event_stream_gbs"] / hbm_peak
+    # binned vs event-by-event spectra of the whole sample (FP64)
+    hb = api.osc_histogram_bin_centre(c, [sid], 0, 1, "fp64", *tb, LO, HI, NBINS)[0, 0]
+    he = api.osc_histogram(c, [sid], 0, 1, "fp64", LO, HI, NBINS)[0, 0]
+    nz = he > 0
+    res["spectrum_max_rel_diff_vs_event_by_event"] = float(np.max(np.abs(hb[nz] - he[nz]) / he[nz]))
+    # the 25 MeV bin from 0.6 GeV: quadrature nodes of the Gamma(3, 0.25 GeV) spectrum as events
+    from scipy import stats
+    K = 4000
+    h = 0.025 / K
+    nodes = (0.6 + (np.arange(K) + 0.5) * h).astype(np.float32)
+    q = {"n": K, "e_true": nodes, "e_reco": nodes,
+         "w_mc": (stats.gamma(3.0, scale=0.25).pdf(nodes.astype(np.float64)) * h).astype(np.float32),
+         "flav_in": np.ones(K, np.uint8), "flav_out": np.ones(K, np.uint8), "is_nubar": np.zeros(K, np.uint8),
+         "baseline_km": 295.0, "density_gcc": 2.6, "ye": 0.5}
+    qid = api.osc_load_sample(c, q)
+    ee = api.osc_histogram(c, [qid], 0, 1, "fp64", 0.0, 10.0, 400)[0, 0, 24]
+    bb = api.osc_histogram_bin_centre(c, [qid], 0, 1, "fp64", 0.0, 10.0, 400, 0.0, 10.0, 400)[0, 0, 24]
+    api.osc_unload_sample(c, qid)
+    res["study_25MeV_bin_0.6GeV"] = {"event_by_event_over_bin_centre_minus_1": float(ee / bb - 1.0),
+                                     "spectrum": "Gamma(3, 0.25 GeV), nu_mu -> nu_mu, 295 km, 2.6 g/cm^3"}
+    return res
+
+
+def layers_leg(torch, api, synth, c, stream, flush, k=20):
+    """Layered matter: a 2M-event 1300 km beam-shaped sample through three layers
+    (400 km at 2.6, 500 km at 3.3, 400 km at 2.6 g/cm^3), one point, histogram
+    per step, against the same sample at constant density."""
+    s = synth.uneven_samples(sizes=(1, 1, 2_000_000))[2]
+    sid = api.osc_load_sample(c, s)
+    out = torch.zeros((1, 1, NBINS), dtype=torch.float64, device=flush.device)
+    api.osc_set_params(c, synth.table1_point()[None, :])
+    res = {"events": s["n"], "layers": [[400.0, 2.6, 0.5], [500.0, 3.3, 0.5], [400.0, 2.6, 0.5]]}
+    for tag in ("constant_density", "three_layers"):
+        if tag == "three_layers":
+            api.osc_set_layers(c, sid, res["layers"])
+        for prec in ("fp32", "fp64"):
+            ms = _event_times(torch, stream, flush, lambda: api.osc_histogram(
+                c, [sid], 0, 1, prec, 0.0, 20.0, NBINS, out=out), k, 3)
+            t = float(np.median(ms))
+            res.setdefault(tag, {})[prec] = {"value": s["n"] / (t * 1e-3), "unit": UNIT, "call_ms_p50": t}
+    api.osc_unload_sample(c, sid)
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -316,7 +393,11 @@ def run_ours(args):
         api.osc_set_params(c, point)
         api.osc_histogram(c, [sid], 0, 1, prec, LO, HI, NBINS, out=out)
 
-    def timed(prec, k, w, count_launches=False):
+    def timed(prec, k, w, kernel_timing):
+        """k steps after w warm-up steps; per-step device times [ms].  With
+        kernel_timing the library also brackets each of its kernels with CUDA
+        events (its graphs then carry event nodes, which rules out the
+        programmatic launch of the histogram kernel after the constants kernel)."""
         for _ in range(w):
             step(prec)
         torch.cuda.synchronize()
@@ -325,7 +406,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         api.osc_timing_totals(c)  # reset
-        api.osc_enable_timing(c, True)
+        api.osc_enable_timing(c, kernel_timing)
         n0 = api.osc_launch_count(c)
         for i in range(k):
             flush.zero_()
@@ -345,15 +426,17 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         time.sleep(1.0)  # let nvidia-smi start sampling before the timed region
         t_clk0 = time.perf_counter()
-        ms32, counts, sums, launches = timed("fp32", args.steps, args.warmup)
+        ms32, _, _, launches = timed("fp32", args.steps, args.warmup, False)
         t_clk1 = time.perf_counter()
+        # the same K steps again with per-kernel events: kernel durations for the roofline
+        ms32k, counts, sums, _ = timed("fp32", args.steps, 3, True)
     clk.window(t_clk0, t_clk1)
     clocks = clk.summary()
     k64 = max(3, min(args.steps, 40))
-    ms64, c64, s64, _ = timed("fp64", k64, max(3, min(args.warmup, 5)))
+    ms64, c64, s64, _ = timed("fp64", k64, max(3, min(args.warmup, 5)), True)
     # the FP64-eigen-solve variant (FP64 eigenvalues and phases, FP32 amplitude) on the same workload
     kmx = max(3, min(args.steps, 200))
-    msmx, cmx, smx, _ = timed("fp32_f64eig", kmx, max(3, min(args.warmup, 5)))
+    msmx, cmx, smx, _ = timed("fp32_f64eig", kmx, max(3, min(args.warmup, 5)), True)
 
     tot32 = float(ms32.sum())
     tot64 = float(ms64.sum())
@@ -415,6 +498,8 @@ def run_ours(args):
             nz = h64 != 0
             prec_study["fp32_vs_fp64_hist_max_rel"] = float(np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
         mcmc = mcmc_leg(api, synth, c, sid, sample, args.mcmc_steps) if args.mcmc_steps > 0 else None
+        binned = bin_centre_leg(torch, api, synth, c, sid, sample, point, stream, flush, peaks.get("hbm_gbs"))
+        layered = layers_leg(torch, api, synth, c, stream, flush)
         serving = None
         if args.serve_seconds > 0:
             serving = {"fp32": serving_leg(api, synth, c, (2000, 10000, 20000), args.serve_seconds, "fp32"),
@@ -433,6 +518,7 @@ def run_ours(args):
             "latency_us": {"p50": float(np.percentile(lat, 50) * 1e6), "p99": float(np.percentile(lat, 99) * 1e6),
                            "device_p50": float(np.percentile(ms32, 50) * 1e3),
                            "device_p99": float(np.percentile(ms32, 99) * 1e3)},
+            "step_ms_with_kernel_events": float(ms32k.mean()),
             "kernel_ms": {"hist_fp32": k_hist_ms, "final": sums[2] / max(1, counts[2]),
                           "const": sums[0] / max(1, counts[0]), "hist_fp64": s64[1] / max(1, c64[1]),
                           "hist_fp32_f64eig": smx[1] / max(1, cmx[1])},
@@ -450,6 +536,8 @@ def run_ours(args):
             "clocks": clocks,
             "serving": serving,
             "mcmc": mcmc,
+            "bin_centre": binned,
+            "layers": layered,
         }
         print(json.dumps(result), flush=True)
     ctx.close()

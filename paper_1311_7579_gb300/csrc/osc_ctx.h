@@ -124,6 +124,6 @@ int prec_kind(osc_precision p);
 cudaEvent_t pool_event(osc_ctx *c);
 osc_status drain_timing(osc_ctx *c);
 void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,
-                 int32_t chunk, int64_t acc_hist_base, std::vector<WorkItem> &items);
+                 int32_t chunk, int64_t slots, int64_t acc_hist_base, std::vector<WorkItem> &items);
 
 }  // namespace osc

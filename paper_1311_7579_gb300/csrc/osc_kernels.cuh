@@ -21,6 +21,16 @@ namespace osc {
 constexpr int kNT = 256;          // threads per block of the histogram kernel
 constexpr int kET = 4 * kNT;      // events per shared-memory tile
 
+// ------------------------------------------------ programmatic dependent launch
+// A kernel launched with programmatic stream serialization may start before the
+// preceding kernel of its stream has finished; it must wait here before it reads
+// anything that kernel writes.  Without that launch attribute the wait returns
+// at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the dependent kernel of a programmatic launch start (its wait still
+// covers all of this kernel's writes).
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------- constants
 struct cplx64 {
     double re, im;
@@ -463,15 +473,17 @@ __device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const S
 template <int PREC>
 __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
     const int lane = threadIdx.x & 31;
-    // prefetch a second ticket only when items are plentiful (a warp holding two
-    // tickets of a scarce list would leave other warps idle)
-    const bool ahead = prm.n_items >= 3 * (int)(gridDim.x * (blockDim.x >> 5));
-    int it = 0, nxt = 0;
-    if (lane == 0) {
-        it = atomicAdd(prm.counter, 1);
-        if (ahead) nxt = atomicAdd(prm.counter, 1);
-    }
-    it = __shfl_sync(0xffffffffu, it, 0);
+    const int n_warps = (int)(gridDim.x * (blockDim.x >> 5));
+    const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    // The first item of every warp (and, when items are plentiful, the second)
+    // is assigned statically, so the grid does not start with one atomic per
+    // warp on the same counter; later tickets come from the counter, offset
+    // past the static ones.  A second ticket is held ahead only when items are
+    // plentiful (a warp holding two tickets of a scarce list would leave other
+    // warps idle).
+    const bool ahead = prm.n_items >= 3 * n_warps;
+    const int dyn0 = ahead ? 2 * n_warps : n_warps;
+    int it = gw, nxt = ahead ? gw + n_warps : 0;
     int cur_sample = -1, cur_point = -1, cur_ch = -1;
     SampleDev sd;
     Pt32 c32;
@@ -481,12 +493,37 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
     const float *pc32 = nullptr;
     const double *pc64 = nullptr;
     float sf = 1.0f;
-    while (it < prm.n_items) {
-        const WorkItem wi = prm.items[it];
+    // The item in hand: its descriptor and each lane's first two events.
+    WorkItem wi{};
+    const float4 *ev = nullptr;  // 32-bit offsets within the item (items hold fewer than 2^31 events)
+    int end = 0;
+    float Ea = 1.0f, ra = 0.0f, wa = 0.0f, Eb = 1.0f, rb = 0.0f, wb = 0.0f;
+    int ca = 0, cb = 0;
+    auto fetch = [&](int idx) {
+        wi = prm.items[idx];
         if (wi.sample != cur_sample) {
             cur_sample = wi.sample;
             sd = prm.samples[wi.sample];
         }
+        ev = sd.ev + wi.ev_begin;
+        end = wi.ev_count;
+        Ea = 1.0f; ra = 0.0f; wa = 0.0f; ca = 0;
+        Eb = 1.0f; rb = 0.0f; wb = 0.0f; cb = 0;
+        if (lane < end) {
+            const float4 q = ev[lane];
+            Ea = q.x; ra = q.y; wa = q.z; ca = __float_as_int(q.w);
+        }
+        if (lane + 32 < end) {
+            const float4 q = ev[lane + 32];
+            Eb = q.x; rb = q.y; wb = q.z; cb = __float_as_int(q.w);
+        }
+    };
+    // The item list, the sample descriptors and the events are never written by
+    // a kernel, so the first item is fetched before the grid-dependency wait:
+    // under a programmatic dependent launch this overlaps the constants kernel.
+    if (it < prm.n_items) fetch(it);
+    grid_dependency_wait();
+    while (it < prm.n_items) {
         if (wi.point_base != cur_point) {
             cur_point = wi.point_base;
             cur_ch = -1;
@@ -503,20 +540,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
         }
         unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
         RunAcc r{0ull, 0ull, -1};
-        // 32-bit offsets within the item (items hold fewer than 2^31 events)
-        const float4 *ev = sd.ev + wi.ev_begin;
-        const int end = wi.ev_count;
         int e = lane;
-        float Ea = 1.0f, ra = 0.0f, wa = 0.0f, Eb = 1.0f, rb = 0.0f, wb = 0.0f;
-        int ca = 0, cb = 0;
-        if (e < end) {
-            const float4 q = ev[e];
-            Ea = q.x; ra = q.y; wa = q.z; ca = __float_as_int(q.w);
-        }
-        if (e + 32 < end) {
-            const float4 q = ev[e + 32];
-            Eb = q.x; rb = q.y; wb = q.z; cb = __float_as_int(q.w);
-        }
         if (PREC == kFP32) {
             const int sh = sd.frac_bits - 150;
             for (; e < end; e += 64) {
@@ -621,16 +645,18 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
             }
         }
-        acc_finish_warp(r, accp);
-        // move to the ticket fetched an item ago and fetch the one after it, or
-        // (few items) take the next ticket now
+        // move to the ticket held ahead and fetch the one after it, or (few
+        // items) take the next ticket now; the next item's first events are in
+        // flight while this item's runs are closed
         if (ahead) {
             it = __shfl_sync(0xffffffffu, nxt, 0);
-            if (lane == 0 && it < prm.n_items) nxt = atomicAdd(prm.counter, 1);
+            if (lane == 0 && it < prm.n_items) nxt = atomicAdd(prm.counter, 1) + dyn0;
         } else {
-            if (lane == 0) it = atomicAdd(prm.counter, 1);
+            if (lane == 0) it = atomicAdd(prm.counter, 1) + dyn0;
             it = __shfl_sync(0xffffffffu, it, 0);
         }
+        if (it < prm.n_items) fetch(it);
+        acc_finish_warp(r, accp);
     }
 }
 
@@ -650,6 +676,7 @@ __global__ void __launch_bounds__(kNT, (PREC == kFP64) ? 1 : 2) k_hist(const His
         constexpr int S = kNT / PT;
         __shared__ typename StageOf<PREC>::T stg;
         __shared__ int s_item;
+        grid_dependency_wait();
         const int tid = threadIdx.x;
         const int lp = tid % PT;
         const int sl = tid / PT;

@@ -4,6 +4,7 @@
 namespace osc {
 
 __global__ void __launch_bounds__(kConstThreads) k_point_consts(const osc_point *pts, int n, float *pc32, double *pc64) {
+    grid_dependents_launch();
     const int i = blockIdx.x;
     if (i >= n) return;
     point_consts_block(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
@@ -11,6 +12,7 @@ __global__ void __launch_bounds__(kConstThreads) k_point_consts(const osc_point 
 
 template <int N>
 __global__ void __launch_bounds__(kConstThreads) k_point_consts_v(const PointsByValueT<N> pv, float *pc32, double *pc64) {
+    grid_dependents_launch();
     const int i = blockIdx.x;
     if (i >= pv.n) return;
     point_consts_block(pv.p[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);

@@ -129,21 +129,37 @@ int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items) {
     return std::max(1, std::min(g, n_items));
 }
 
+// Size of the next one-point work item by guided self-scheduling: full chunks
+// while the work left is large, then remaining / (2 x slots) events (a multiple
+// of 64, at least 256), so the grid ends on short items while most of the work
+// keeps the lower per-item overhead of full chunks.
+static int32_t guided_size(int64_t remaining, int32_t chunk, int64_t slots) {
+    const int64_t g = remaining / (2 * slots) / 64 * 64;
+    return (int32_t)std::max<int64_t>(std::min<int64_t>(chunk, 256), std::min<int64_t>(chunk, g));
+}
+
 void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,
-                 int32_t chunk, int64_t acc_hist_base, std::vector<WorkItem> &items) {
+                 int32_t chunk, int64_t slots, int64_t acc_hist_base, std::vector<WorkItem> &items) {
     const int32_t n_tiles = (n_points + pt - 1) / pt;
+    int64_t remaining = 0;
+    for (const Sample *s : ss) remaining += s->n * n_tiles;
     for (size_t s = 0; s < ss.size(); ++s)
-        for (int32_t t = 0; t < n_tiles; ++t)
-            for (int64_t e = 0; e < ss[s]->n; e += chunk) {
+        for (int32_t t = 0; t < n_tiles; ++t) {
+            const int64_t n = ss[s]->n;
+            for (int64_t e = 0; e < n;) {
+                const int32_t c = (pt == 1 && slots > 0) ? guided_size(remaining, chunk, slots) : chunk;
                 WorkItem w;
                 w.sample = (int32_t)s;
                 w.point_base = point_base + t * pt;
                 w.n_pts = std::min(pt, n_points - t * pt);
-                w.ev_count = (int32_t)std::min<int64_t>(chunk, ss[s]->n - e);
+                w.ev_count = (int32_t)std::min<int64_t>(c, n - e);
                 w.ev_begin = e;
                 w.acc_base = acc_hist_base + (int64_t)s * n_points + (int64_t)t * pt;
                 items.push_back(w);
+                e += w.ev_count;
+                remaining -= w.ev_count;
             }
+        }
     // largest first for the dynamic scheduler
     std::stable_sort(items.begin(), items.end(), [](const WorkItem &a, const WorkItem &b) {
         return (int64_t)a.ev_count * a.n_pts > (int64_t)b.ev_count * b.n_pts;
@@ -779,8 +795,11 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
         ss.push_back(ctx->samples[id]);
         sdev.push_back(ctx->samples[id]->dev);
     }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel(p), hist_threads(), 0);
+    const int64_t slots = (int64_t)ctx->n_sm * std::max(per_sm, 1) * (pt == 1 ? hist_threads() / 32 : 1);
     std::vector<WorkItem> items;
-    build_items(ss, point_begin, n_points, pt, chunk, 0, items);
+    build_items(ss, point_begin, n_points, pt, chunk, slots, 0, items);
     p->n_items = (int32_t)items.size();
     p->grid = hist_grid(ctx, plan_kernel(p), p->n_items);
     const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
@@ -833,7 +852,22 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
         hp.fin_hmeta = p->d_hmeta;
         hp.fin_out = d_out;
     }
-    if (!ctx->timing) {
+    if (!ctx->timing && fused && p->kind == kEventByEvent) {
+        // one kernel: a direct launch with programmatic stream serialization, so
+        // that it starts (and fetches its first work) while the constants
+        // kernel before it in the stream is still running
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(p->grid);
+        cfg.blockDim = dim3(hist_threads());
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = ctx->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelExC(&cfg, kh.func, hargs));
+    } else if (!ctx->timing) {
         if (!p->exec) {
             CK(cudaGraphCreate(&p->graph, 0));
             CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, nullptr, 0, &kh));
