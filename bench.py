@@ -549,7 +549,9 @@ def run_ours(args):
 def run_profile_case(args):
     """Small fixed case for ncu captures: --events events of the beam-shaped
     sample x --points scan points, --launches histogram launches with the given
-    points-per-block tile (0 = autotuned) and precision."""
+    points-per-block tile (0 = autotuned) and precision.  --method picks the
+    event-by-event histogram (ebe), the bin-centre method (bc, 410 true bins of
+    25 MeV) or event-by-event through three layers (layers)."""
     import torch
 
     from paper_1311_7579_gb300 import api, synth
@@ -563,12 +565,17 @@ def run_profile_case(args):
     pts = synth.table1_point()[None, :] if args.points == 1 else synth.scan_points(args.points)
     api.osc_set_params(c, pts)
     api.osc_set_tile(c, args.tile, 0)
+    if args.method == "layers":
+        api.osc_set_layers(c, sid, [(100.0, 2.2, 0.5), (95.0, 3.0, 0.5), (100.0, 2.2, 0.5)])
     out = torch.zeros((1, args.points, NBINS), dtype=torch.float64, device="cuda")
     for _ in range(args.launches):
-        api.osc_histogram(c, [sid], 0, args.points, args.prec, LO, HI, NBINS, out=out)
+        if args.method == "bc":
+            api.osc_histogram_bin_centre(c, [sid], 0, args.points, args.prec, 0.0, 10.25, 410, LO, HI, NBINS, out=out)
+        else:
+            api.osc_histogram(c, [sid], 0, args.points, args.prec, LO, HI, NBINS, out=out)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": {"events": args.events, "points": args.points, "prec": args.prec,
-                                       "tile": args.tile, "launches": args.launches,
+    print(json.dumps({"profile_case": {"method": args.method, "events": args.events, "points": args.points,
+                                       "prec": args.prec, "tile": args.tile, "launches": args.launches,
                                        "checksum": float(out.sum())}}))
     ctx.close()
     return 0
@@ -591,6 +598,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--method", default="ebe", choices=["ebe", "bc", "layers"])
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)

@@ -187,7 +187,9 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
 
 /* Launch-shape control.  points_per_block in {1, 4, 16, 64, 256}, or 0 to let
  * the autotuner choose per workload class (default); events_per_item a positive
- * multiple of 64, or 0 for the default.  Results never depend on either. */
+ * multiple of 64, or 0 for the default.  events_per_item also sets the work-item
+ * size of osc_histogram_bin_centre; the layered kernels always run one point
+ * per warp.  Results never depend on either. */
 osc_status osc_set_tile(osc_ctx *ctx, int32_t points_per_block, int32_t events_per_item);
 
 /* Enable (1) / disable (0) CUDA-event timing of each kernel.  Events are

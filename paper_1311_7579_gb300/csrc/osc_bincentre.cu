@@ -83,9 +83,9 @@ template <bool F64>
 __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
     const HistParams &prm = b.h;
     const int lane = threadIdx.x & 31;
-    int it = 0;
-    if (lane == 0) it = atomicAdd(prm.counter, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    // first item of every warp assigned statically, later ones from the counter
+    const int n_warps = (int)(gridDim.x * (blockDim.x >> 5));
+    int it = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     while (it < prm.n_items) {
         const WorkItem wi = prm.items[it];
         const SampleDev &sd = prm.samples[wi.sample];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
             }
         }
         acc_finish_warp(r, accp);
-        if (lane == 0) it = atomicAdd(prm.counter, 1);
+        if (lane == 0) it = atomicAdd(prm.counter, 1) + n_warps;
         it = __shfl_sync(0xffffffffu, it, 0);
     }
     if (prm.fuse_final) fused_final_warp(prm);

@@ -52,6 +52,7 @@ struct Plan {
     // bin-centre plans: true-energy binning, probability table and its rows
     double t_lo = 0, t_hi = 0;
     int32_t t_nbins = 0, n_rows = 0;
+    int32_t chunk_req = 0;  // events_per_item requested by osc_set_tile when the plan was made (0: default)
     BcRow *d_rows = nullptr;
     int32_t *d_rowmap = nullptr;
     void *d_tab = nullptr;

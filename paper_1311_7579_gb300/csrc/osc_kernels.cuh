@@ -666,8 +666,16 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
 // sl + 2S, ... (S = kNT / PT), an increasing subsequence of the sorted events, so
 // its bin sequence is monotone within a channel and a register run-length
 // accumulator suffices.  Two events are computed per iteration.
+// Resident blocks per SM: the 256-point tile fits three blocks (80 registers,
+// no spills) and gains from the extra warps; the one-point path needs more
+// registers for its two events in flight, and FP64 more still.
 template <int PREC, int PT>
-__global__ void __launch_bounds__(kNT, (PREC == kFP64) ? 1 : 2) k_hist(const HistParams prm) {
+constexpr int hist_min_blocks() {
+    return PREC == kFP64 ? 1 : (PT == 256 ? 3 : 2);
+}
+
+template <int PREC, int PT>
+__global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(const HistParams prm) {
     if constexpr (PT == 1) {
         hist_items_per_warp<PREC>(prm);
         if (prm.fuse_final) fused_final_warp(prm);

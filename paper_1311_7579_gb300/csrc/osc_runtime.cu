@@ -726,7 +726,9 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     int64_t ev = 0;
     for (int32_t id : ids) ev += ctx->samples[id]->n;
     const int64_t tiles = (n_points + pt - 1) / pt;
-    const int per_sm = (prec == kFP64) ? 1 : 2;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_kernel_fn(prec, pt), hist_threads(), 0);
+    per_sm = std::max(per_sm, 1);
     // one point per item: items are taken per warp; otherwise per block
     const int64_t slots = (int64_t)ctx->n_sm * per_sm * (pt == 1 ? hist_threads() / 32 : 1);
     const int64_t quantum = (pt == 1) ? 64 : 1024;
@@ -1038,7 +1040,7 @@ static osc_status get_bc_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int
     for (Plan *p : ctx->plans)
         if (p->kind == kBinCentre && p->sample_ids == ids && p->point_begin == point_begin &&
             p->n_points == n_points && p->prec == prec && p->nbins == nbins && p->t_lo == t_lo && p->t_hi == t_hi &&
-            p->t_nbins == t_nbins) {
+            p->t_nbins == t_nbins && p->chunk_req == ctx->tile_chunk) {
             p->last_use = ++ctx->plan_clock;
             *out = p;
             return OSC_OK;
@@ -1064,13 +1066,15 @@ static osc_status get_bc_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int
                     rows.push_back(BcRow{(int32_t)s, point_begin + q, c, 0});
                 }
     const size_t tab_bytes = rows.size() * (size_t)t_nbins * (prec == kFP64 ? 8 : 4);
-    // one item per ~4 resident warps' worth of events, a multiple of 128 (32 lanes x 4 records)
+    // about two items per resident warp (the event stream is uniform work), a
+    // multiple of 128 (32 lanes x 4 records); osc_set_tile's events_per_item overrides
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bc_hist_kernel_fn(prec), hist_threads(), 0);
     per_sm = std::max(per_sm, 1);
     const int64_t warps = (int64_t)ctx->n_sm * per_sm * (hist_threads() / 32);
-    int64_t chunk = (ev * n_points + 4 * warps - 1) / (4 * warps);
+    int64_t chunk = (ev * n_points + 2 * warps - 1) / (2 * warps);
     chunk = std::max<int64_t>(128, std::min<int64_t>((chunk + 127) / 128 * 128, 1 << 20));
+    if (ctx->tile_chunk > 0) chunk = ctx->tile_chunk;
     std::vector<WorkItem> items;
     build_items_bc(ss, point_begin, n_points, (int32_t)chunk, items);
 
@@ -1087,6 +1091,7 @@ static osc_status get_bc_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int
     p->t_lo = t_lo;
     p->t_hi = t_hi;
     p->t_nbins = t_nbins;
+    p->chunk_req = ctx->tile_chunk;
     p->n_rows = (int32_t)rows.size();
     p->n_items = (int32_t)items.size();
     p->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->n_sm * per_sm, p->n_items));
