@@ -8,13 +8,16 @@
 //               weight P * w_mc binned by E_reco into the same exact fixed-point
 //               accumulators as the event-by-event kernel.
 // The table is tiny next to the event stream, so the histogram kernel is bound
-// by reading the 16-byte event records: four records per lane are in flight.
+// by reading the 16-byte event records: each lane works on four records while
+// the next four are loaded, and the kernel is launched programmatically after
+// the table kernel so that its first loads overlap the table computation.
 #include "osc_layers.cuh"
 
 namespace osc {
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
+    grid_dependents_launch();
     const int64_t n = (int64_t)b.n_rows * b.t_nbins;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
     }
 }
 
-constexpr int kBcUnroll = 4;  // event records in flight per lane
+constexpr int kBcUnroll = 4;  // event records per lane per step; the next step's are loaded meanwhile
 
 template <bool F64>
 __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
@@ -86,11 +89,29 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
     // first item of every warp assigned statically, later ones from the counter
     const int n_warps = (int)(gridDim.x * (blockDim.x >> 5));
     int it = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    WorkItem wi{};
+    const float4 *ev = nullptr;
+    int end = 0;
+    float4 q[kBcUnroll];
+    auto load_step = [&](float4 *dst, int e0) {
+#pragma unroll
+        for (int k = 0; k < kBcUnroll; ++k) {
+            const int e = e0 + lane + 32 * k;
+            dst[k] = (e < end) ? ev[e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    };
+    auto fetch = [&](int idx) {
+        wi = prm.items[idx];
+        ev = prm.samples[wi.sample].ev + wi.ev_begin;
+        end = wi.ev_count;
+        load_step(q, 0);
+    };
+    // items and events are never written by a kernel: the first item's events are
+    // in flight before the wait for the table kernel (programmatic launch)
+    if (it < prm.n_items) fetch(it);
+    grid_dependency_wait();
     while (it < prm.n_items) {
-        const WorkItem wi = prm.items[it];
         const SampleDev &sd = prm.samples[wi.sample];
-        const float4 *ev = sd.ev + wi.ev_begin;
-        const int end = wi.ev_count;
         const float sf = F64 ? (float)prm.pc64[(int64_t)wi.point_base * C64_STRIDE + C64_ESCALE]
                              : prm.pc32[(int64_t)wi.point_base * C32_STRIDE + C32_ESCALE];
         const int sh = sd.frac_bits - 150;
@@ -101,12 +122,8 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
         int cur_ch = -1;
         int64_t row_off = 0;
         for (int e0 = 0; e0 < end; e0 += 32 * kBcUnroll) {
-            float4 q[kBcUnroll];
-#pragma unroll
-            for (int k = 0; k < kBcUnroll; ++k) {
-                const int e = e0 + lane + 32 * k;
-                q[k] = (e < end) ? ev[e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            }
+            float4 qn[kBcUnroll];
+            load_step(qn, e0 + 32 * kBcUnroll);
 #pragma unroll
             for (int k = 0; k < kBcUnroll; ++k) {
                 const int e = e0 + lane + 32 * k;
@@ -127,10 +144,13 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
                     acc_event_f32(r, accp, prm, sf, q[k].y, P * q[k].z, sh, keep);
                 }
             }
+#pragma unroll
+            for (int k = 0; k < kBcUnroll; ++k) q[k] = qn[k];
         }
-        acc_finish_warp(r, accp);
         if (lane == 0) it = atomicAdd(prm.counter, 1) + n_warps;
         it = __shfl_sync(0xffffffffu, it, 0);
+        if (it < prm.n_items) fetch(it);
+        acc_finish_warp(r, accp);
     }
     if (prm.fuse_final) fused_final_warp(prm);
 }

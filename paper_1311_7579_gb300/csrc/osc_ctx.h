@@ -57,7 +57,6 @@ struct Plan {
     int32_t *d_rowmap = nullptr;
     void *d_tab = nullptr;
     int32_t table_grid = 0;
-    cudaGraphNode_t n_table_node = nullptr;
     uint64_t last_use = 0;
 };
 

@@ -1125,7 +1125,6 @@ static osc_status get_bc_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int
     return OSC_OK;
 }
 
-// CUDA graph: table kernel -> histogram kernel (-> finalize kernel for large outputs).
 static osc_status run_bc_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *d_out) {
     BcParams bp;
     fill_hist_params(bp.h, p->d_items, p->n_items, p->d_samples, ctx->d_pc32, ctx->d_pc64, ctx->d_acc,
@@ -1168,18 +1167,22 @@ static osc_status run_bc_plan(osc_ctx *ctx, Plan *p, double lo, double hi, doubl
     kf.gridDim = dim3((unsigned)std::min<int64_t>(std::max<int64_t>((nfin + 255) / 256, 1), (int64_t)ctx->n_sm * 8));
     kf.blockDim = dim3(256);
     kf.kernelParams = fargs;
-    if (!p->exec) {
-        CK(cudaGraphCreate(&p->graph, 0));
-        CK(cudaGraphAddKernelNode(&p->n_table_node, p->graph, nullptr, 0, &kt));
-        CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, &p->n_table_node, 1, &kh));
-        if (!fused) CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
-        CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
-    } else {
-        CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_table_node, &kt));
-        CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_hist_node, &kh));
-        if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
-    }
-    CK(cudaGraphLaunch(p->exec, ctx->stream));
+    // table kernel, then the histogram kernel by programmatic dependent launch
+    // (it fetches its first items and events while the table is computed), then
+    // the finalize kernel for large outputs
+    CK(cudaLaunchKernel(kt.func, kt.gridDim, kt.blockDim, targs, 0, ctx->stream));
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = kh.gridDim;
+    cfg.blockDim = kh.blockDim;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelExC(&cfg, kh.func, hargs));
+    if (!fused) CK(cudaLaunchKernel(kf.func, kf.gridDim, kf.blockDim, fargs, 0, ctx->stream));
     ctx->launches += fused ? 2 : 3;
     return OSC_OK;
 }
