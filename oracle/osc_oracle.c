@@ -226,6 +226,9 @@ int orc_bin(double escale, float e_reco, double lo, double hi, int nbins) {
     return (int)u;
 }
 
+/* Event weight (Sec. 1.1.1): probability x MC weight x the point's normalisation. */
+static double orc_weight(double p, float w_mc, const orc_point *pt) { return p * (double)w_mc * pt->norm; }
+
 /* Per-event probabilities and weights for one point (Sec. 1.1.1: weight =
  * P(alpha->beta at E_true) * w_mc * norm).  Events are independent; the loop
  * is split over threads, which does not change any result. */
@@ -237,7 +240,7 @@ void orc_reweight(int64_t n, const float *e_true, const float *w_mc, const uint8
         double p = orc_prob(pt, L_km, rho, ye, (double)e_true[i], flav_in[i], flav_out[i],
                             is_nubar[i]);
         if (out_prob) out_prob[i] = p;
-        if (out_weight) out_weight[i] = p * (double)w_mc[i] * pt->norm;
+        if (out_weight) out_weight[i] = orc_weight(p, w_mc[i], pt);
     }
 }
 
@@ -313,7 +316,7 @@ void orc_reweight_bin_centre(int64_t n, const float *e_true, const float *w_mc, 
             p = orc_prob(pt, L_km, rho, ye, (double)orc_true_centre(t_lo, t_hi, t_nbins, t), flav_in[i],
                          flav_out[i], is_nubar[i]);
         if (out_prob) out_prob[i] = p;
-        if (out_weight) out_weight[i] = p * (double)w_mc[i] * pt->norm;
+        if (out_weight) out_weight[i] = orc_weight(p, w_mc[i], pt);
     }
 }
 
@@ -361,7 +364,7 @@ void orc_reweight_layers(int64_t n, const float *e_true, const float *w_mc, cons
         orc_prob_matrix_layers(pt, n_layers, L_km, rho, ye, (double)e_true[i], is_nubar[i], P);
         double p = P[flav_out[i]][flav_in[i]];
         if (out_prob) out_prob[i] = p;
-        if (out_weight) out_weight[i] = p * (double)w_mc[i] * pt->norm;
+        if (out_weight) out_weight[i] = orc_weight(p, w_mc[i], pt);
     }
 }
 

@@ -27,7 +27,7 @@ MUTATIONS = [
     ("binning ignores lo", "float u = t * inv_f;", "float u = x * inv_f;"),
     ("nubar keeps U", "for (int i = 0; i < 3; ++i) U[a][i] = conj(U[a][i]);",
      "for (int i = 0; i < 3; ++i) U[a][i] = U[a][i];"),
-    ("weight drops norm", "out_weight[i] = p * (double)w_mc[i] * pt->norm;", "out_weight[i] = p * (double)w_mc[i];"),
+    ("weight drops norm", "return p * (double)w_mc * pt->norm;", "return p * (double)w_mc;"),
     ("Jacobi rotation missing its phase", "G[q][q] = c * emphi;", "G[q][q] = c;"),
     ("propagator built from conjugated eigenvectors", "s += V[b][k] * ph[k] * conj(V[a][k]);",
      "s += conj(V[b][k]) * ph[k] * V[a][k];"),
