@@ -15,8 +15,44 @@
 
 namespace osc {
 
+// FP64 probabilities enter the table as the integer P * 2^63, rounded (P <= 1 up
+// to rounding, so the value stays below 2^64).
+__device__ __forceinline__ unsigned long long prob_fixed(double P) {
+    return __double2ull_rn(fmin(fmax(P, 0.0), 1.5) * 9223372036854775808.0);
+}
+
+// Adds P * w * 2^F to the lane's 128-bit run accumulator with integer
+// instructions only: Pq = P * 2^63 (integer), w = m * 2^(e - 150) (FP32
+// mantissa m with its implicit bit), so the addend is Pq * m * 2^(e + F - 213),
+// truncated.  |w| * 2^F < 2^63 makes e + F - 213 <= -24, so it is a right
+// shift of the 88-bit product and the addend fits in 63 bits.
+__device__ __forceinline__ void fx_add_pw(unsigned long long &lo, unsigned long long &hi, unsigned long long pq,
+                                          float w, int frac_bits) {
+    const uint32_t u = __float_as_uint(w);
+    const int ef = (int)((u >> 23) & 0xFFu);
+    const unsigned long long m = (unsigned long long)((u & 0x7FFFFFu) | (ef ? 0x800000u : 0u));
+    const int rs = 213 - frac_bits - (ef ? ef : 1);
+    const unsigned long long plo = pq * m, phi = __umul64hi(pq, m);
+    unsigned long long v;
+    if (rs >= 128)
+        v = 0ull;
+    else if (rs >= 64)
+        v = phi >> (rs - 64);
+    else
+        v = (plo >> rs) | (phi << (64 - rs));  // rs >= 24 here
+    if (u >> 31) {
+        asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
+    } else {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
+    }
+}
+
+// Small blocks spread the table over many SMs: its FP64 evaluations are few
+// but long, and the FP64 pipe of one SM would serialise them.
+constexpr int kBcTableThreads = 64;
+
 template <int PREC>
-__global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
+__global__ void __launch_bounds__(kBcTableThreads) k_bc_table(const BcParams b) {
     grid_dependents_launch();
     const int64_t n = (int64_t)b.n_rows * b.t_nbins;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
@@ -36,7 +72,7 @@ __global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
             if (PREC == kFP64) {
                 LayU<double> u;
                 load_layu(pc64 + C64_LU, ch >= 9, u);
-                b.tab64[idx] = prob_layers64(c64, pc64 + C64_LD, u, sd, ch, E);
+                b.tabq[idx] = prob_fixed(prob_layers64(c64, pc64 + C64_LD, u, sd, ch, E));
             } else {
                 const float *pc = b.h.pc32 + (int64_t)rw.point * C32_STRIDE;
                 Pt32 c;
@@ -75,7 +111,7 @@ __global__ void __launch_bounds__(256) k_bc_table(const BcParams b) {
             Ch64 h;
             load_ch64(pc, ch, h);
             const double Ad = sd.kA_rhoye * (double)E;
-            b.tab64[idx] = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+            b.tabq[idx] = prob_fixed(prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E));
         }
     }
 }
@@ -115,7 +151,6 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
         const float sf = F64 ? (float)prm.pc64[(int64_t)wi.point_base * C64_STRIDE + C64_ESCALE]
                              : prm.pc32[(int64_t)wi.point_base * C32_STRIDE + C32_ESCALE];
         const int sh = sd.frac_bits - 150;
-        const double hs = sd.hscale_d;
         const int32_t *rmap = b.row_map + wi.acc_base * kChannels;
         unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
         RunAcc r{0ull, 0ull, -1};
@@ -137,8 +172,19 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
                 }
                 const int64_t ti = row_off + (keep ? __float2int_rz(u) : 0);
                 if (F64) {
-                    const double P = keep ? b.tab64[ti] : 0.0;
-                    acc_event_f64(r, accp, prm, sf, q[k].y, P * (double)q[k].z, hs, keep);
+                    // binning as in acc_event_f64, integer addend
+                    const float x = __fmul_rn(sf, q[k].y);
+                    const float tr = __fsub_rn(x, prm.lo_f);
+                    const float ur = __fmul_rn(tr, prm.inv_f);
+                    if (keep && tr >= 0.0f && ur < prm.nb_f) {
+                        const int bn = __float2int_rz(ur);
+                        if (bn != r.cur_b) {
+                            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+                            r.lo = r.hi = 0;
+                            r.cur_b = bn;
+                        }
+                        fx_add_pw(r.lo, r.hi, b.tabq[ti], q[k].z, sd.frac_bits);
+                    }
                 } else {
                     const float P = keep ? b.tab32[ti] : 0.0f;
                     acc_event_f32(r, accp, prm, sf, q[k].y, P * q[k].z, sh, keep);
@@ -152,12 +198,16 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
         if (it < prm.n_items) fetch(it);
         acc_finish_warp(r, accp);
     }
-    if (prm.fuse_final) fused_final_warp(prm);
+    // block-level completion ticket: one atomic per block rather than per warp,
+    // and the last block converts the bins with all its threads
+    if (prm.fuse_final) fused_final(prm);
 }
 
 const void *bc_hist_kernel_fn(int prec) {
     return prec == kFP64 ? (const void *)k_bc_hist<true> : (const void *)k_bc_hist<false>;
 }
+
+int bc_table_threads() { return kBcTableThreads; }
 
 const void *bc_table_kernel_fn(int prec) {
     return prec == kFP32 ? (const void *)k_bc_table<kFP32>

@@ -135,7 +135,7 @@ struct BcParams {
     double t_lo, t_w;         // first true-bin edge and bin width (t_hi - t_lo) / t_nbins
     float t_lo_f, t_inv_f, t_nb_f;
     float *tab32;             // [n_rows][t_nbins] FP32 / FP32_F64EIG probabilities
-    double *tab64;            // [n_rows][t_nbins] FP64 probabilities
+    unsigned long long *tabq; // [n_rows][t_nbins] FP64 probabilities as P * 2^63, rounded
 };
 
 // Launch helpers implemented in the kernel translation units.
@@ -148,6 +148,7 @@ cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
 // Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
 const void *hist_kernel_fn(int prec, int pt);
 const void *bc_table_kernel_fn(int prec);
+int bc_table_threads();
 const void *bc_hist_kernel_fn(int prec);
 const void *layers_hist_kernel_fn(int prec);
 cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream_t st);

@@ -1096,7 +1096,8 @@ static osc_status get_bc_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int
     p->n_items = (int32_t)items.size();
     p->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->n_sm * per_sm, p->n_items));
     const int64_t tab_n = (int64_t)rows.size() * t_nbins;
-    p->table_grid = (int)std::max<int64_t>(1, std::min<int64_t>((tab_n + 255) / 256, (int64_t)ctx->n_sm * 8));
+    const int64_t tt = bc_table_threads();
+    p->table_grid = (int)std::max<int64_t>(1, std::min<int64_t>((tab_n + tt - 1) / tt, (int64_t)ctx->n_sm * 32));
     const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
     void *a;
     osc_status st = OSC_OK;
@@ -1139,7 +1140,7 @@ static osc_status run_bc_plan(osc_ctx *ctx, Plan *p, double lo, double hi, doubl
     bp.t_inv_f = (float)((double)p->t_nbins / (p->t_hi - p->t_lo));
     bp.t_nb_f = (float)p->t_nbins;
     bp.tab32 = p->prec == kFP64 ? nullptr : (float *)p->d_tab;
-    bp.tab64 = p->prec == kFP64 ? (double *)p->d_tab : nullptr;
+    bp.tabq = p->prec == kFP64 ? (unsigned long long *)p->d_tab : nullptr;
     const bool fused = fuse_finalize(p->n_hist, p->nbins);
     if (fused) {
         bp.h.fuse_final = 1;
@@ -1154,7 +1155,7 @@ static osc_status run_bc_plan(osc_ctx *ctx, Plan *p, double lo, double hi, doubl
     cudaKernelNodeParams kt{};
     kt.func = (void *)bc_table_kernel_fn(p->prec);
     kt.gridDim = dim3(p->table_grid);
-    kt.blockDim = dim3(256);
+    kt.blockDim = dim3(bc_table_threads());
     kt.kernelParams = targs;
     cudaKernelNodeParams kh{};
     kh.func = (void *)bc_hist_kernel_fn(p->prec);
