@@ -73,6 +73,7 @@ def lib():
                 "orc_bin": (ctypes.c_int, [d, ctypes.c_float, d, d, ctypes.c_int]),
                 "orc_bin_many": (None, [i64, fp, d, d, d, ctypes.c_int, i32]),
                 "orc_num_threads": (ctypes.c_int, []),
+                "orc_set_num_threads": (None, [ctypes.c_int]),
                 "orc_true_centre": (ctypes.c_float, [d, d, ctypes.c_int, ctypes.c_int]),
                 "orc_reweight_bin_centre": (None, [i64, fp, fp, u8, u8, u8, d, d, d, pt, d, d, ctypes.c_int,
                                                    dp, dp]),
@@ -110,6 +111,11 @@ def k_A() -> float:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads used by the oracle's parallel loops from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 def pmns(pt: OrcPoint) -> np.ndarray:

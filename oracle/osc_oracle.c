@@ -421,6 +421,16 @@ void orc_bin_many(int64_t n, const float *e_reco, double escale, double lo, doub
     for (int64_t i = 0; i < n; ++i) out[i] = orc_bin(escale, e_reco[i], lo, hi, nbins);
 }
 
+/* Thread count of the OpenMP loops (for timing the oracle on 1 core and on all cores). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     extern int omp_get_max_threads(void);
