@@ -68,9 +68,9 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the bench kernel from its committed ncu summary,
-    or None when the kernel sources changed since that capture."""
+def _profile_field(name):
+    """An integer field of the bench kernel's committed ncu summary, or None when
+    the kernel sources changed since that capture."""
     if not os.path.exists(TRAFFIC_PROFILE):
         return None
     fields = {}
@@ -81,9 +81,14 @@ def _profiled_traffic():
     if fields.get("kernel_source_sha256_16") != _kernel_source_hash():
         return None
     try:
-        return int(fields["dram_bytes_per_launch"])
+        return int(fields[name])
     except (KeyError, ValueError):
         return None
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the bench kernel (ncu), or None."""
+    return _profile_field("dram_bytes_per_launch")
 
 
 def _measured_peaks():
@@ -170,11 +175,19 @@ def cpu_baseline_leg(sample, point_row, gpu_p32, gpu_p64, n_sample):
     oracle.hist_from_weights(sub["e_reco"][:n1], w1, point_row[6], LO, HI, NBINS)
     dt1 = time.perf_counter() - t1
     oracle.set_num_threads(cores)
+    # the batched-scan shape: the first 16 scan points over the 2M-event scan sample
+    from paper_1311_7579_gb300 import synth
+    scan = synth.scan_sample()
+    t2 = time.perf_counter()
+    oracle.histogram(scan, synth.scan_points()[:16], LO, HI, NBINS)
+    dt2 = time.perf_counter() - t2
     cpu = {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": "first %d events of the 10M-event sample, Table 1 point: FP64 Jacobi oracle reweight + "
                      "100-bin histogram, %.2f s wall" % (n_sample, dt),
            "single_core": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
-                           "sample": "first %d events, %.2f s wall" % (n1, dt1)}}
+                           "sample": "first %d events, %.2f s wall" % (n1, dt1)},
+           "scan_16_points": {"value": 16 * scan["n"] / dt2, "unit": UNIT, "cores": cores,
+                              "sample": "2M-event scan sample x first 16 scan points, %.2f s wall" % dt2}}
     prec = {"subsample_events": n_sample, "fp32_max_dP": float(d32.max()), "fp32_rms_dP": float(np.sqrt(np.mean(d32 ** 2))),
             "fp64_max_dP": float(d64.max()), "fp64_rms_dP": float(np.sqrt(np.mean(d64 ** 2)))}
     return cpu, prec, h
@@ -494,6 +507,16 @@ def run_ours(args):
         fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
         achieved = FP32_FLOP_PER_EVPT * N_EVENTS / (k_hist_ms * 1e-3) / 1e12
         traffic = _profiled_traffic()
+        # issue view: the kernel's warp instructions per launch (ncu) over its live duration,
+        # against 4 schedulers x 1 warp instruction per clock per SM
+        winst = _profile_field("warp_instructions_per_launch")
+        issue_peak = n_sm * 4 * sm_mhz * 1e6 / 1e12  # T warp-instructions/s
+        issue = None
+        if winst:
+            ia = winst / (k_hist_ms * 1e-3) / 1e12
+            issue = {"achieved": ia, "peak": issue_peak, "unit": "T warp-instructions/s", "frac": ia / issue_peak,
+                     "warp_instructions_per_launch": winst,
+                     "thread_instructions_per_evpt": 32.0 * winst / N_EVENTS}
         # precision study + CPU baseline (rank 0, N = 1 semantics: its own sample)
         p32 = np.zeros(N_EVENTS)
         p64 = np.zeros(N_EVENTS)
@@ -539,7 +562,8 @@ def run_ours(args):
                                         % (n_sm, sm_mhz, src),
                          "flop_per_evpt": FP32_FLOP_PER_EVPT,
                          "hbm_gbs_event_stream": 16.0 * N_EVENTS / (k_hist_ms * 1e-3) / 1e9,
-                         "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                         "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                         "issue": issue},
             "cpu_baseline": cpu,
             "precision": prec_study,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64, "d2h_bytes_per_step": 8 * NBINS},
