@@ -178,10 +178,10 @@ osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *sample_ids, int
  *   - 2 <= n_layers <= 16 routes osc_reweight, osc_histogram and
  *     osc_histogram_bin_centre for this sample to the layered kernels.  These
  *     kernels run one point per warp; osc_set_tile does not apply to them.
- * The serving loop handles single-layer samples only: osc_submit returns
- * OSC_E_ARG for a layered sample.  This call returns OSC_E_STATE while serving
- * runs.  Arrays are host memory; the call copies them and drops cached launch
- * plans. */
+ * The serving loop runs a batch that holds a layered sample with the layered
+ * kernels.  This call returns OSC_E_STATE while serving runs (in-flight batches
+ * hold the sample's path).  Arrays are host memory; the call copies them and
+ * drops cached launch plans. */
 osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, const double *length_km,
                           const double *density_gcc, const double *ye);
 
@@ -222,7 +222,6 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
                       uint64_t *ticket);
 /* osc_submit validates the point and sample on the calling thread and queues
  * the request (OSC_E_BUSY beyond 2^20 queued requests); the ticket is > 0.
- * A layered sample (osc_set_layers with n_layers > 1) gives OSC_E_ARG.
  * osc_wait waits for a ticket's histogram (host buffer of nbins doubles) and
  * releases it; latency_us (may be NULL) receives the submit-to-completion time.
  * timeout_ms < 0 waits forever; OSC_E_TIMEOUT when the time runs out; OSC_E_ARG

@@ -12,6 +12,7 @@
 // the next four are loaded, and the kernel is launched programmatically after
 // the table kernel so that its first loads overlap the table computation.
 #include "osc_layers.cuh"
+#include "osc_launch.h"
 
 namespace osc {
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "osc_internal.h"
+#include "osc_launch.h"
 
 struct osc_serve;  // serving state (osc_serve.cu)
 

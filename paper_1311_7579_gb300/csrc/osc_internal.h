@@ -138,21 +138,7 @@ struct BcParams {
     unsigned long long *tabq; // [n_rows][t_nbins] FP64 probabilities as P * 2^63, rounded
 };
 
-// Launch helpers implemented in the kernel translation units.
+// Precision of a kernel instantiation.
 enum Prec { kFP64 = 0, kFP32 = 1, kMix = 2 };  // kMix: FP64 eigen-solve and phases, FP32 amplitude
-cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
-cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st);
-cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
-cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
-cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
-// Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
-const void *hist_kernel_fn(int prec, int pt);
-const void *bc_table_kernel_fn(int prec);
-int bc_table_threads();
-const void *bc_hist_kernel_fn(int prec);
-const void *layers_hist_kernel_fn(int prec);
-cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream_t st);
-const void *final_kernel_fn();
-int hist_threads();
 
 }  // namespace osc

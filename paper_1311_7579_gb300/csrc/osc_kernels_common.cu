@@ -1,5 +1,6 @@
 // Constants and finalize kernels, and the precision dispatch of the launch helpers.
 #include "osc_kernels.cuh"
+#include "osc_launch.h"
 
 namespace osc {
 

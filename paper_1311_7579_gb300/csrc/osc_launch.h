@@ -1,0 +1,26 @@
+// osc_launch.h -- host-side entry points of the kernel translation units (launch
+// helpers and kernel function pointers), used by the runtime and the serving loop.
+// Not part of the public ABI.
+#pragma once
+
+#include "osc_internal.h"
+
+namespace osc {
+
+cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
+cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st);
+cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
+cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
+cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
+// Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
+const void *hist_kernel_fn(int prec, int pt);
+const void *bc_table_kernel_fn(int prec);
+int bc_table_threads();
+const void *bc_hist_kernel_fn(int prec);
+const void *layers_hist_kernel_fn(int prec);
+cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream_t st);
+cudaError_t launch_hist_layers(int prec, const HistParams &p, int grid, cudaStream_t st);
+const void *final_kernel_fn();
+int hist_threads();
+
+}  // namespace osc

@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "osc_layers.cuh"
+#include "osc_launch.h"
 
 namespace osc {
 
@@ -123,6 +124,16 @@ const void *layers_hist_kernel_fn(int prec) {
     return prec == kFP32 ? (const void *)k_hist_layers<kFP32>
            : prec == kMix ? (const void *)k_hist_layers<kMix>
                           : (const void *)k_hist_layers<kFP64>;
+}
+
+cudaError_t launch_hist_layers(int prec, const HistParams &p, int grid, cudaStream_t st) {
+    if (prec == kFP32)
+        k_hist_layers<kFP32><<<grid, kNT, 0, st>>>(p);
+    else if (prec == kMix)
+        k_hist_layers<kMix><<<grid, kNT, 0, st>>>(p);
+    else
+        k_hist_layers<kFP64><<<grid, kNT, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream_t st) {

@@ -137,8 +137,15 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
             w.ev_begin = e;
             w.acc_base = r;
         }
-    std::stable_sort(b.h_items, b.h_items + n_items,
-                     [](const WorkItem &x, const WorkItem &y) { return x.ev_count > y.ev_count; });
+    // items of layered samples first (each group largest first): a batch that mixes
+    // layered and single-layer samples runs each group with its own kernel, so a
+    // request's result does not depend on the other requests of its batch
+    std::stable_sort(b.h_items, b.h_items + n_items, [&](const WorkItem &x, const WorkItem &y) {
+        const bool lx = b.h_samples[x.sample].n_layers > 1, ly = b.h_samples[y.sample].n_layers > 1;
+        return lx != ly ? lx : x.ev_count > y.ev_count;
+    });
+    int n_lay = 0;
+    while (n_lay < n_items && b.h_samples[b.h_items[n_lay].sample].n_layers > 1) ++n_lay;
     cudaStream_t st = b.stream;
     cudaError_t e = cudaMemcpyAsync(b.d_pts, b.h_pts, n * sizeof(osc_point), cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(b.d_hmeta, b.h_hmeta, n * 4 * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -163,13 +170,32 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     hp.fin_n_hist = n;
     hp.fin_hmeta = b.d_hmeta;
     hp.fin_out = b.d_out;
-    e = launch_hist(prec, 1, hp, hist_grid(ctx, hist_kernel_fn(prec, 1), (n_items + 7) / 8), st);
+    int kernels = 0;
+    if (n_lay > 0) {
+        // layered items: their own ticket counter, finalized by the last kernel below
+        HistParams hl = hp;
+        hl.n_items = n_lay;
+        if (n_lay < n_items) {
+            hl.counter = b.d_counter + 2;
+            hl.fuse_final = 0;
+            e = cudaMemsetAsync(hl.counter, 0, 2 * sizeof(int32_t), st);
+        }
+        if (!e) e = launch_hist_layers(prec, hl, hist_grid(ctx, layers_hist_kernel_fn(prec), (n_lay + 7) / 8), st);
+        ++kernels;
+    }
+    if (!e && n_lay < n_items) {
+        HistParams hs = hp;
+        hs.items = b.d_items + n_lay;
+        hs.n_items = n_items - n_lay;
+        e = launch_hist(prec, 1, hs, hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + 7) / 8), st);
+        ++kernels;
+    }
     FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
     if (!e && !fused) e = launch_final(fp, st);
     if (!e) e = cudaMemcpyAsync(b.h_out, b.d_out, (size_t)n * sv->nbins * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaLaunchHostFunc(st, on_batch_done, cb_arg);
     if (e) return fail_cuda(ctx, e, "serving batch launch");
-    ctx->launches += fused ? 2 : 3;
+    ctx->launches += 1 + kernels + (fused ? 0 : 1);
     return OSC_OK;
 }
 
@@ -335,7 +361,6 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
         if (validate_point(nullptr, *pt, 0) != OSC_OK) return OSC_E_RANGE;
         auto it = ctx->samples.find(sample_id);
         if (it == ctx->samples.end()) return OSC_E_ARG;
-        if (it->second->dev.n_layers > 1) return OSC_E_ARG;  // the serving kernels are single-layer
         r.sd = it->second->dev;
         r.frac_bits = it->second->frac_bits;
     }

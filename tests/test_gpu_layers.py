@@ -8,7 +8,8 @@ of per-layer constant-density propagators, through the C ABI:
   * one layer set through osc_set_layers equals the load-time constant path,
     and equal-density pieces equal one layer;
   * a layered and a single-layer sample in one launch; the binned method on a
-    layered sample; argument checks; the serving loop refuses layered samples.
+    layered sample; argument checks; served requests on layered samples equal
+    the same histograms from osc_histogram, bit for bit.
 """
 import numpy as np
 import pytest
@@ -145,7 +146,7 @@ def test_full_size_uneven_sample_with_layers():
             assert np.all(np.abs(h[k] - ho) <= TOL32 * wsum + 1e-12)
 
 
-def test_layer_arguments_and_serving_refusal():
+def test_layer_arguments_and_serving_state():
     s = synth.beam_sample(1000, seed=37)
     with api.Context(0) as c:
         sid = api.osc_load_sample(c.ptr, s)
@@ -159,11 +160,40 @@ def test_layer_arguments_and_serving_refusal():
         api.osc_set_params(c.ptr, synth.table1_point()[None, :])
         api.osc_serve_start(c.ptr, 4, 0.0, 5.0, 10)
         try:
-            with pytest.raises(api.OscError):
-                api.osc_submit(c.ptr, sid, synth.table1_point(), "fp32")
+            # the sample's path cannot change while batches may hold it
             with pytest.raises(api.OscError):
                 api.osc_set_layers(c.ptr, sid, [(295.0, 2.6, 0.5)])
         finally:
             api.osc_serve_stop(c.ptr)
         h = api.osc_histogram(c.ptr, [sid], 0, 1, "fp64", 0.0, 5.0, 10)
         assert np.isfinite(h).all()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_serving_layered_and_single_layer_requests(prec):
+    """Requests on a layered and a single-layer sample, queued together, each
+    give the histogram that osc_histogram gives for the same point (same kernels,
+    exact accumulation: bit for bit)."""
+    s1 = synth.all_channel_sample(20_000, seed=38, L_km=1300.0)
+    s2 = synth.beam_sample(15_000, seed=39)
+    pts = synth.scan_points(6, 4747)
+    lo, hi, nb = 0.0, 10.0, 20
+    with api.Context(0) as c:
+        a = api.osc_load_sample(c.ptr, s1)
+        b = api.osc_load_sample(c.ptr, s2)
+        api.osc_set_layers(c.ptr, a, PROFILE)
+        api.osc_set_params(c.ptr, pts)
+        ref_a = api.osc_histogram(c.ptr, [a], 0, 6, prec, lo, hi, nb)[0]
+        ref_b = api.osc_histogram(c.ptr, [b], 0, 6, prec, lo, hi, nb)[0]
+        api.osc_serve_start(c.ptr, 16, lo, hi, nb)
+        try:
+            tickets = []
+            for k in range(6):
+                tickets.append((0, k, api.osc_submit(c.ptr, a, pts[k], prec)))
+                tickets.append((1, k, api.osc_submit(c.ptr, b, pts[k], prec)))
+            for which, k, t in tickets:
+                h, _ = api.osc_wait(c.ptr, t, nb, 20000)
+                ref = ref_a[k] if which == 0 else ref_b[k]
+                assert np.array_equal(h, ref), (which, k)
+        finally:
+            api.osc_serve_stop(c.ptr)
