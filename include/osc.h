@@ -135,8 +135,10 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
 /* Event-by-event binned PDFs (Sec. 1.1.1): out[s][p][b] for s < n_samples,
  * p < n_points (table points point_begin + p), b < nbins, over [lo, hi).
  * All (sample, point, event) work runs in one launch.  out is host memory if
- * out_on_device == 0 (the call then returns after the copy), device memory
- * otherwise (the call returns once the work is enqueued on the context stream). */
+ * out_on_device == 0 (the call then returns when the bins are there; a
+ * page-locked host buffer is written by the kernels directly, a pageable one
+ * through a device staging buffer and a copy), device memory otherwise (the
+ * call returns once the work is enqueued on the context stream). */
 osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
                          int32_t point_begin, int32_t n_points, osc_precision prec, double lo,
                          double hi, int32_t nbins, double *out, int out_on_device);

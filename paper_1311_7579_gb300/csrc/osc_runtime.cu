@@ -186,6 +186,17 @@ static void fill_hist_params(HistParams &hp, const WorkItem *d_items, int32_t n_
     hp.fin_out = nullptr;
 }
 
+// Device address of a page-locked host buffer, which the kernels then write
+// directly (no staging buffer and copy); null for pageable memory.
+static double *pinned_device_ptr(double *host) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? (double *)a.devicePointer : nullptr;
+}
+
 // Outputs this small are converted by the histogram kernel's last block.
 bool fuse_finalize(int64_t n_hist, int32_t nbins) { return n_hist * (int64_t)nbins <= 4096; }
 
@@ -1002,14 +1013,16 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     st = get_plan(ctx, ids, point_begin, n_points, pr, nbins, pt, chunk, &p, layered ? kLayered : kEventByEvent);
     if (st) return st;
     double *d_out = out;
-    if (!out_on_device) {
+    bool staged = false;
+    if (!out_on_device && !(d_out = pinned_device_ptr(out))) {
         st = ensure_buf(ctx, &ctx->d_out, &ctx->out_cap, bins);
         if (st) return st;
         d_out = ctx->d_out;
+        staged = true;
     }
     st = run_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
-    if (!out_on_device) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (staged) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream));
     return OSC_OK;
 }
@@ -1216,16 +1229,16 @@ extern "C" osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *samp
     st = get_bc_plan(ctx, ids, point_begin, n_points, pr, nbins, t_lo, t_hi, t_nbins, &p);
     if (st) return st;
     double *d_out = out;
-    if (!out_on_device) {
+    bool staged = false;
+    if (!out_on_device && !(d_out = pinned_device_ptr(out))) {
         st = ensure_buf(ctx, &ctx->d_out, &ctx->out_cap, bins);
         if (st) return st;
         d_out = ctx->d_out;
+        staged = true;
     }
     st = run_bc_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
-    if (!out_on_device) {
-        CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-    }
+    if (staged) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream));
     return OSC_OK;
 }

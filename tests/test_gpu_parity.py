@@ -257,6 +257,22 @@ def test_device_outputs_match_host_outputs(ctx):
     api.osc_histogram(ctx, [sid], 0, 5, "fp32", LO, HI, NB, out=hd)
     api.osc_sync(ctx)
     assert np.array_equal(hd.cpu().numpy(), hh)
+    # page-locked host buffers are written by the kernels directly: same bins, for
+    # the fused finalize (5 x NB bins) and the separate finalize kernel (60 x 100)
+    hp = torch.zeros((1, 5, NB), dtype=torch.float64).pin_memory().numpy()
+    api.osc_histogram(ctx, [sid], 0, 5, "fp32", LO, HI, NB, out=hp)
+    assert np.array_equal(hp, hh)
+    hb = api.osc_histogram_bin_centre(ctx, [sid], 0, 5, "fp64", 0.0, 10.0, 40, LO, HI, NB)
+    hbp = torch.zeros((1, 5, NB), dtype=torch.float64).pin_memory().numpy()
+    api.osc_histogram_bin_centre(ctx, [sid], 0, 5, "fp64", 0.0, 10.0, 40, LO, HI, NB, out=hbp)
+    assert np.array_equal(hbp, hb)
+    pts60 = synth.scan_points(60, seed=10)
+    api.osc_set_params(ctx, pts60)
+    hl = api.osc_histogram(ctx, [sid], 0, 60, "fp32", LO, HI, 100)
+    hlp = torch.zeros((1, 60, 100), dtype=torch.float64).pin_memory().numpy()
+    api.osc_histogram(ctx, [sid], 0, 60, "fp32", LO, HI, 100, out=hlp)
+    assert np.array_equal(hlp, hl)
+    api.osc_set_params(ctx, pts)
     pd = torch.zeros(s["n"], dtype=torch.float64, device="cuda")
     api.osc_reweight(ctx, sid, 2, "fp64", out_prob=pd)
     ph, _ = _gpu_probs(ctx, sid, 2, "fp64", s["n"])
