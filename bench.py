@@ -4,8 +4,9 @@ Workload (one step = one pass of the whole hot path over one batch): the
 precision-study configuration -- 10M events shaped like the paper's beam MC
 (Gamma(3, 0.25 GeV) true energies, 295 km, 2.6 g/cm^3, Y_e 0.5, nu_mu -> nu_mu
 90 % / nu_mu -> nu_e 10 %, 20 % antineutrinos) at the Table 1 parameter point:
-set the point (H2D of the point + the FP64 constants kernel), then the fused
-probability / weight / bin / histogram kernel and the finalize kernel into a
+set the point (passed by value to the FP64 constants kernel), then the
+histogram kernel -- probability, weight, bin and exact accumulation, finalized
+in place, launched programmatically after the constants kernel -- into a
 100-bin E_reco histogram over [0, 5) GeV.  FP32-bulk path; the all-FP64 path is
 timed on the same workload as the GPU baseline to beat.
 

@@ -1,6 +1,6 @@
 """GPU-vs-oracle parity through the C ABI (needs a GB300).
 
-Tolerances (from the benchmark spec of the method's precision):
+Tolerances:
   * FP64 path probabilities: |dP| <= 1e-12 (Sec. 2.2 validation residual ~1e-12);
   * FP32-bulk path probabilities: |dP| <= 1e-5;
   * histogram bins: relative 1e-9 (FP64 path against the oracle's FP64 histogram;
