@@ -31,7 +31,11 @@
  *   - Errors: every call returns an osc_status.  On error, outputs are left
  *     untouched and osc_last_error() describes the cause.  Invalid input is
  *     rejected on the host before any launch.  A CUDA error poisons the
- *     context: later calls return OSC_E_STATE.  Device code never traps.
+ *     context: later calls return OSC_E_STATE; running out of device memory
+ *     (OSC_E_NOMEM) does not.  Device code never traps.
+ *   - Fault injection (tests): with the environment variable
+ *     OSC_FAULT_ALLOC_FAIL_AT=k set when a context is created, that context's
+ *     k-th device allocation fails as if the device were out of memory.
  *   - Threading: a context is not re-entrant, except osc_submit/osc_wait,
  *     which may be called from any thread while serving runs.
  *   - Determinism: histogram bins are accumulated in exact 128-bit fixed
@@ -210,6 +214,10 @@ osc_status osc_timing_totals(osc_ctx *ctx, int64_t counts[3], double sums_ms[3])
 /* Number of kernels this context has launched so far (graph replays count
  * each kernel node). */
 osc_status osc_launch_count(const osc_ctx *ctx, uint64_t *count);
+
+/* Device memory the context holds (samples, point table, plans, accumulators
+ * and other buffers), in bytes; the workspace cap applies to this total. */
+osc_status osc_workspace_used(const osc_ctx *ctx, size_t *bytes);
 
 /* Block until all work enqueued by the context has finished. */
 osc_status osc_sync(osc_ctx *ctx);

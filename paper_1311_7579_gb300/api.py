@@ -28,6 +28,7 @@ ENTRY_POINTS = [
     "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
     "osc_last_timing", "osc_timing_totals", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
     "osc_serve_stop", "osc_histogram_noalloc", "osc_histogram_bin_centre", "osc_set_layers",
+    "osc_workspace_used",
 ]
 
 
@@ -86,6 +87,7 @@ def load_library(path):
         "osc_last_timing": (st, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
         "osc_timing_totals": (st, [vp, ctypes.POINTER(i64), ctypes.POINTER(d)]),
         "osc_launch_count": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "osc_workspace_used": (st, [vp, ctypes.POINTER(ctypes.c_size_t)]),
         "osc_sync": (st, [vp]),
         "osc_serve_start": (st, [vp, i32, d, d, i32]),
         "osc_submit": (st, [vp, i32, ctypes.POINTER(OscPoint), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
@@ -246,6 +248,12 @@ def osc_timing_totals(ctx):
 def osc_launch_count(ctx) -> int:
     v = ctypes.c_uint64()
     _check(ctx, lib().osc_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def osc_workspace_used(ctx) -> int:
+    v = ctypes.c_size_t()
+    _check(ctx, lib().osc_workspace_used(ctx, ctypes.byref(v)))
     return v.value
 
 

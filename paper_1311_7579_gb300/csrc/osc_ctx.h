@@ -13,6 +13,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "osc_internal.h"
 #include "osc_launch.h"
 
@@ -69,6 +71,9 @@ struct osc_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t cap = 0, used = 0;
+    // fault injection (tests): the fault_alloc_at-th device allocation fails as
+    // if the device were out of memory (0: never)
+    int64_t fault_alloc_at = 0, n_allocs = 0;
     std::unordered_map<void *, size_t> sizes;
     std::string err;
     bool poisoned = false;
@@ -110,6 +115,15 @@ struct osc_ctx {
 };
 
 namespace osc {
+
+// NVTX range over a host-side scope (visible in Nsight timelines; free when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // helpers shared by the runtime and the serving loop
 osc_status fail(osc_ctx *c, osc_status s, const std::string &msg);

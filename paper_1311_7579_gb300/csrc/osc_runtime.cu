@@ -7,6 +7,7 @@
 // on the device in FP64 for a whole table of points; and one persistent launch
 // covers every (sample, point tile, event range) work item of a call.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -50,6 +51,8 @@ osc_status dalloc(osc_ctx *c, void **p, size_t bytes) {
         o << "workspace cap exceeded: " << c->used << " + " << bytes << " > " << c->cap << " bytes";
         return fail(c, OSC_E_NOMEM, o.str());
     }
+    if (++c->n_allocs == c->fault_alloc_at)
+        return fail(c, OSC_E_NOMEM, "injected allocation failure (OSC_FAULT_ALLOC_FAIL_AT)");
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -336,6 +339,7 @@ osc_status osc_create(int device, size_t workspace_cap_bytes, void *cuda_stream,
     osc_ctx *ctx = new osc_ctx();
     ctx->device = device;
     ctx->cap = workspace_cap_bytes;
+    if (const char *f = std::getenv("OSC_FAULT_ALLOC_FAIL_AT")) ctx->fault_alloc_at = std::atoll(f);
     e = cudaSetDevice(device);
     if (e) {
         delete ctx;
@@ -393,6 +397,7 @@ void osc_destroy(osc_ctx *ctx) {
 }
 
 osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *sample_id) {
+    NvtxRange nvtx_range("osc_load_sample");
     CHECK_CTX(ctx);
     if (!d || !sample_id) return fail(ctx, OSC_E_ARG, "null argument");
     std::lock_guard<std::mutex> lk(ctx->api_mu);
@@ -500,6 +505,7 @@ osc_status osc_unload_sample(osc_ctx *ctx, int32_t sample_id) {
 
 osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, const double *length_km,
                           const double *density_gcc, const double *ye) {
+    NvtxRange nvtx_range("osc_set_layers");
     CHECK_CTX(ctx);
     if (!length_km || !density_gcc || !ye) return fail(ctx, OSC_E_ARG, "null argument");
     if (n_layers < 1 || n_layers > kMaxLayers) return fail(ctx, OSC_E_ARG, "n_layers must be in [1, 16]");
@@ -559,6 +565,7 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
 }
 
 osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points) {
+    NvtxRange nvtx_range("osc_set_params");
     CHECK_CTX(ctx);
     if (!pts) return fail(ctx, OSC_E_ARG, "null point table");
     if (n_points < 1 || n_points > (1 << 20)) return fail(ctx, OSC_E_ARG, "n_points must be in [1, 2^20]");
@@ -662,6 +669,12 @@ osc_status osc_timing_totals(osc_ctx *ctx, int64_t counts[3], double sums_ms[3])
     return OSC_OK;
 }
 
+osc_status osc_workspace_used(const osc_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return OSC_E_ARG;
+    *bytes = ctx->used;
+    return OSC_OK;
+}
+
 osc_status osc_launch_count(const osc_ctx *ctx, uint64_t *count) {
     if (!ctx || !count) return OSC_E_ARG;
     *count = ctx->launches.load();
@@ -676,6 +689,7 @@ osc_status osc_sync(osc_ctx *ctx) {
 
 osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_precision prec, double *out_prob,
                         double *out_weight, int out_on_device) {
+    NvtxRange nvtx_range("osc_reweight");
     CHECK_CTX(ctx);
     if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
         return fail(ctx, OSC_E_ARG, "bad precision");
@@ -927,6 +941,7 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
 // Time one candidate tile shape (ms per histogram launch).
 static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t pb, int32_t np, int prec,
                              int32_t nbins, double lo, double hi, int32_t pt, int32_t chunk, double *ms) {
+    NvtxRange nvtx_range("autotune candidate");
     Plan *p;
     osc_status st = get_plan(ctx, ids, pb, np, prec, nbins, pt, chunk, &p);
     if (st) return st;
@@ -949,6 +964,7 @@ static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
 extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
                                     int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
                                     double *out, int out_on_device) {
+    NvtxRange nvtx_range("osc_histogram");
     CHECK_CTX(ctx);
     if (!sample_ids || !out) return fail(ctx, OSC_E_ARG, "null argument");
     if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
@@ -1205,6 +1221,7 @@ extern "C" osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *samp
                                                int32_t point_begin, int32_t n_points, osc_precision prec,
                                                double t_lo, double t_hi, int32_t t_nbins, double lo, double hi,
                                                int32_t nbins, double *out, int out_on_device) {
+    NvtxRange nvtx_range("osc_histogram_bin_centre");
     CHECK_CTX(ctx);
     if (!sample_ids || !out) return fail(ctx, OSC_E_ARG, "null argument");
     if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)

@@ -97,6 +97,7 @@ void CUDART_CB on_batch_done(void *arg) {
 
 // Build and enqueue one batch (called by the scheduler thread without the lock).
 osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *> *cb_arg) {
+    NvtxRange nvtx_range("serving batch");
     osc_ctx *ctx = sv->ctx;
     const int n = (int)b.reqs.size();
     const int prec = b.reqs[0].prec;
