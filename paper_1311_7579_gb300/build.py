@@ -33,23 +33,30 @@ def _deps():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+DEBUG_LIB = os.path.join(LIBDIR, "libosc_gb300_debug.so")
+
+
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    obj_dir = os.path.join(LIBDIR, "obj")
+def build(force: bool = False, verbose: bool = False, debug_checks: bool = False) -> str:
+    """Build the library; with debug_checks, the separate debug library in which
+    every kernel verifies its work-item and index ranges (OSC_DEBUG_CHECKS)."""
+    lib = DEBUG_LIB if debug_checks else LIB
+    if not force and up_to_date(lib):
+        return lib
+    obj_dir = os.path.join(LIBDIR, "obj_debug" if debug_checks else "obj")
     os.makedirs(obj_dir, exist_ok=True)
     srcs = _sources()
+    flags = FLAGS + (["-DOSC_DEBUG_CHECKS"] if debug_checks else [])
 
     def compile_one(src):
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
-        cmd = [NVCC] + FLAGS + ["-c", src, "-o", obj]
+        cmd = [NVCC] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -59,14 +66,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug_checks="--debug-checks" in sys.argv))

@@ -139,8 +139,10 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
     };
     auto fetch = [&](int idx) {
         wi = prm.items[idx];
-        ev = prm.samples[wi.sample].ev + wi.ev_begin;
-        end = wi.ev_count;
+        const SampleDev &s = prm.samples[wi.sample];
+        ev = s.ev + wi.ev_begin;
+        end = debug_ok(wi.ev_begin >= 0 && wi.ev_count >= 0 && wi.ev_begin + wi.ev_count <= s.n, prm.counter,
+                       kDbgItem) ? wi.ev_count : 0;
         load_step(q, 0);
     };
     // items and events are never written by a kernel: the first item's events are
@@ -172,6 +174,8 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
                     row_off = (int64_t)rmap[ch] * b.t_nbins;
                 }
                 const int64_t ti = row_off + (keep ? __float2int_rz(u) : 0);
+                if (keep && !debug_ok(row_off >= 0 && ti < (int64_t)b.n_rows * b.t_nbins, prm.counter, kDbgRow))
+                    continue;
                 if (F64) {
                     // binning as in acc_event_f64, integer addend
                     const float x = __fmul_rn(sf, q[k].y);

@@ -131,6 +131,7 @@ osc_status fail_cuda(osc_ctx *c, cudaError_t e, const char *what);
 osc_status dalloc(osc_ctx *c, void **p, size_t bytes);
 void dfree(osc_ctx *c, void *p);
 osc_status validate_point(osc_ctx *c, const osc_point &p, int index);
+osc_status debug_word_check(osc_ctx *c);
 osc_status ensure_acc(osc_ctx *c, int64_t bins);
 // grid of the persistent histogram kernel; finalize fusion rule
 int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items);

@@ -138,6 +138,12 @@ struct BcParams {
     unsigned long long *tabq; // [n_rows][t_nbins] FP64 probabilities as P * 2^63, rounded
 };
 
+// Debug builds (OSC_DEBUG_CHECKS): bits of the error word, int kDebugWord of a
+// launch's 64-byte counter block, set by a kernel that found an index outside
+// its buffers.
+enum DebugCode : unsigned { kDbgItem = 1u, kDbgBin = 2u, kDbgRow = 4u, kDbgLayers = 8u };
+constexpr int kDebugWord = 15;
+
 // Precision of a kernel instantiation.
 enum Prec { kFP64 = 0, kFP32 = 1, kMix = 2 };  // kMix: FP64 eigen-solve and phases, FP32 amplitude
 

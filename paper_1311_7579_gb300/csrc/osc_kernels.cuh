@@ -21,6 +21,23 @@ namespace osc {
 constexpr int kNT = 256;          // threads per block of the histogram kernel
 constexpr int kET = 4 * kNT;      // events per shared-memory tile
 
+// ------------------------------------------------------------- debug checks
+// Built with OSC_DEBUG_CHECKS, the kernels verify work-item and index ranges
+// against their buffers; a violation skips the access and sets a bit of the
+// error word (int kDebugWord of the launch's counter block), which the host
+// reads after it synchronises.  Release builds compile the checks away.
+__device__ __forceinline__ bool debug_ok(bool ok, int32_t *counter, unsigned code) {
+#ifdef OSC_DEBUG_CHECKS
+    if (!ok) atomicOr(reinterpret_cast<unsigned *>(counter + kDebugWord), code);
+    return ok;
+#else
+    (void)ok;
+    (void)counter;
+    (void)code;
+    return true;
+#endif
+}
+
 // ------------------------------------------------ programmatic dependent launch
 // A kernel launched with programmatic stream serialization may start before the
 // preceding kernel of its stream has finished; it must wait here before it reads
@@ -349,6 +366,7 @@ __device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *acc
     const float u = __fmul_rn(tb, prm.inv_f);
     if (active && tb >= 0.0f && u < prm.nb_f) {
         const int b = __float2int_rz(u);
+        if (!debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) return;
         if (b != r.cur_b) {
             if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
             r.lo = r.hi = 0;
@@ -364,6 +382,7 @@ __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *acc
     const float u = __fmul_rn(tb, prm.inv_f);
     if (active && tb >= 0.0f && u < prm.nb_f) {
         const int b = __float2int_rz(u);
+        if (!debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) return;
         if (b != r.cur_b) {
             if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
             r.lo = r.hi = 0;
@@ -506,7 +525,8 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             sd = prm.samples[wi.sample];
         }
         ev = sd.ev + wi.ev_begin;
-        end = wi.ev_count;
+        end = debug_ok(wi.ev_begin >= 0 && wi.ev_count >= 0 && wi.ev_begin + wi.ev_count <= sd.n, prm.counter,
+                       kDbgItem) ? wi.ev_count : 0;
         Ea = 1.0f; ra = 0.0f; wa = 0.0f; ca = 0;
         Eb = 1.0f; rb = 0.0f; wb = 0.0f; cb = 0;
         if (lane < end) {
@@ -696,6 +716,9 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
             if (it >= prm.n_items) break;
             const WorkItem wi = prm.items[it];
             const SampleDev sd = prm.samples[wi.sample];
+            if (!debug_ok(wi.ev_begin >= 0 && wi.ev_count >= 0 && wi.ev_begin + wi.ev_count <= sd.n, prm.counter,
+                          kDbgItem))
+                continue;
             const bool active = lp < wi.n_pts;
             const int pidx = wi.point_base + (active ? lp : wi.n_pts - 1);
             unsigned long long *accp = prm.acc + 3 * (wi.acc_base + lp) * (int64_t)prm.nbins;

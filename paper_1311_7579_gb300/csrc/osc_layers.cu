@@ -59,7 +59,10 @@ __global__ void __launch_bounds__(kNT) k_hist_layers(const HistParams prm) {
         const double hs = sd.hscale_d;
         RunAcc r{0ull, 0ull, -1};
         const float4 *ev = sd.ev + wi.ev_begin;
-        for (int e = lane; e < wi.ev_count; e += 32) {
+        const bool valid = debug_ok(wi.ev_begin >= 0 && wi.ev_count >= 0 && wi.ev_begin + wi.ev_count <= sd.n,
+                                    prm.counter, kDbgItem) &&
+                           debug_ok(sd.n_layers >= 1 && sd.n_layers <= kMaxLayers, prm.counter, kDbgLayers);
+        for (int e = lane; valid && e < wi.ev_count; e += 32) {
             const float4 q = ev[e];
             const int ch = __float_as_int(q.w);
             const int nb = ch >= 9;

@@ -75,6 +75,25 @@ void dfree(osc_ctx *c, void *p) {
 
 static bool is_fin(double x) { return std::isfinite(x); }
 
+// Debug builds: report (and poison the context on) a kernel's index check that
+// failed, once the work has finished.  Release builds do nothing here.
+osc_status debug_word_check(osc_ctx *c) {
+#ifdef OSC_DEBUG_CHECKS
+    unsigned w = 0;
+    const cudaError_t e = cudaMemcpy(&w, c->d_counter + kDebugWord, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(debug word)");
+    if (w) {
+        c->poisoned = true;
+        std::ostringstream o;
+        o << "device index check failed (debug build), code " << w;
+        return fail(c, OSC_E_CUDA, o.str());
+    }
+#else
+    (void)c;
+#endif
+    return OSC_OK;
+}
+
 int prec_kind(osc_precision p) { return p == OSC_FP32_BULK ? kFP32 : p == OSC_FP32_F64EIG ? kMix : kFP64; }
 
 osc_status validate_point(osc_ctx *c, const osc_point &p, int i) {
@@ -684,7 +703,7 @@ osc_status osc_launch_count(const osc_ctx *ctx, uint64_t *count) {
 osc_status osc_sync(osc_ctx *ctx) {
     CHECK_CTX(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
-    return OSC_OK;
+    return debug_word_check(ctx);
 }
 
 osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_precision prec, double *out_prob,
@@ -1039,7 +1058,10 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     st = run_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
     if (staged) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream));
+    if (!out_on_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return debug_word_check(ctx);
+    }
     return OSC_OK;
 }
 
@@ -1256,6 +1278,9 @@ extern "C" osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *samp
     st = run_bc_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
     if (staged) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream));
+    if (!out_on_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return debug_word_check(ctx);
+    }
     return OSC_OK;
 }

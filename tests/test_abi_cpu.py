@@ -40,6 +40,14 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert hasattr(L, n)
 
 
+def test_debug_build_exports_the_same_symbols():
+    """The debug-check build (OSC_DEBUG_CHECKS) compiles and exports the same ABI."""
+    dbg = build.build(debug_checks=True)
+    syms = subprocess.run(["nm", "-D", "--defined-only", dbg], capture_output=True, text=True, check=True).stdout
+    for name in api.ENTRY_POINTS:
+        assert re.search(r"\b%s\b" % name, syms), name
+
+
 def test_build_targets_sm_103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
