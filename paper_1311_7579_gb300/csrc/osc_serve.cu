@@ -4,9 +4,10 @@
 // A scheduler thread inside the library admits queued (sample, point) requests
 // into batches while at most max_slots requests are in flight and a batch slot
 // (preallocated device memory, charged to the workspace cap at serve start) is
-// free.  Each batch runs on its own stream -- constants kernel, histogram
-// kernel over (request, event range) work items, finalize kernel, copy-out --
-// so batches admitted while earlier ones run overlap on the device.  A host
+// free.  Each batch runs on its own stream -- one input copy, constants kernel,
+// histogram kernel over (request, event range) work items whose finalize writes
+// the bins straight into pinned host memory -- so batches admitted while earlier
+// ones run overlap on the device.  A host
 // callback marks the batch complete; osc_wait hands each request's histogram
 // back.  Bins are exact integer sums, so a request's result is bitwise the same
 // alone and in any mix.
@@ -40,28 +41,46 @@ struct Result {
     double latency_us;
 };
 
+// A batch's inputs travel in one copy: the pinned staging block and the device
+// block share one layout (points, histogram metadata, sample table, work items),
+// and only the used prefix of the item list is copied.
+struct StageLayout {
+    size_t pts = 0, hmeta = 0, samples = 0, items = 0, bytes = 0;
+    explicit StageLayout(size_t slots) {
+        auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+        hmeta = up(pts + slots * sizeof(osc_point));
+        samples = up(hmeta + slots * 4 * sizeof(double));
+        items = up(samples + slots * sizeof(SampleDev));
+        bytes = items + (size_t)kMaxItems * sizeof(WorkItem);
+    }
+    StageLayout() = default;
+};
+
 struct Batch {
     cudaStream_t stream = nullptr;
+    StageLayout lay;
     // device
+    char *d_stage = nullptr;
     osc_point *d_pts = nullptr;
+    double *d_hmeta = nullptr;
+    SampleDev *d_samples = nullptr;
+    WorkItem *d_items = nullptr;
     float *d_pc32 = nullptr;
     double *d_pc64 = nullptr;
     unsigned long long *d_acc = nullptr;
-    double *d_out = nullptr;
-    double *d_hmeta = nullptr;
-    WorkItem *d_items = nullptr;
-    SampleDev *d_samples = nullptr;
     int32_t *d_counter = nullptr;
-    // pinned host staging
+    // pinned host memory: staging block (same layout) and the results, which the
+    // finalize writes directly (d_out is h_out's device address)
+    char *h_stage = nullptr;
     osc_point *h_pts = nullptr;
-    double *h_out = nullptr;
     double *h_hmeta = nullptr;
-    WorkItem *h_items = nullptr;
     SampleDev *h_samples = nullptr;
+    WorkItem *h_items = nullptr;
+    double *h_out = nullptr;
+    double *d_out = nullptr;
     // state
     std::vector<Request> reqs;
-    bool busy = false;
-    bool done = false;
+    bool busy = false;  // queued work not yet finished (cleared by the completion callback)
 };
 
 }  // namespace
@@ -85,13 +104,27 @@ struct osc_serve {
 
 namespace {
 
+// Runs (on the CUDA callback thread) when a batch's work has finished: publishes
+// its requests' histograms, which the finalize wrote into pinned host memory, and
+// frees the batch slot -- the waiters and the scheduler are woken directly.
 void CUDART_CB on_batch_done(void *arg) {
     auto *pr = static_cast<std::pair<osc_serve *, Batch *> *>(arg);
     osc_serve *sv = pr->first;
+    Batch &b = *pr->second;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        pr->second->done = true;
+        const auto now = Clock::now();
+        for (size_t r = 0; r < b.reqs.size(); ++r) {
+            Result res;
+            res.hist.assign(b.h_out + r * sv->nbins, b.h_out + (r + 1) * sv->nbins);
+            res.latency_us = std::chrono::duration<double, std::micro>(now - b.reqs[r].t_submit).count();
+            sv->results[b.reqs[r].ticket] = std::move(res);
+        }
+        sv->inflight -= (int32_t)b.reqs.size();
+        b.reqs.clear();
+        b.busy = false;
     }
+    sv->cv_done.notify_all();
     sv->cv.notify_all();
 }
 
@@ -127,31 +160,34 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     int64_t chunk = std::max<int64_t>((total + 4 * warps - 1) / (4 * warps), 1024);
     chunk = std::max<int64_t>(chunk, (total + kMaxItems - n - 1) / (kMaxItems - n));
     chunk = (chunk + 63) / 64 * 64;
+    // Items of layered samples first: a batch that mixes layered and single-layer
+    // samples runs each group with its own kernel, so a request's result does not
+    // depend on the other requests of its batch.  Within a group, all full chunks
+    // come before the shorter tails (largest first, built in one pass, no sort).
     int n_items = 0;
-    for (int r = 0; r < n; ++r)
-        for (int64_t e = 0; e < b.reqs[r].sd.n; e += chunk) {
-            WorkItem &w = b.h_items[n_items++];
-            w.sample = samp_of[r];
-            w.point_base = r;
-            w.n_pts = 1;
-            w.ev_count = (int32_t)std::min<int64_t>(chunk, b.reqs[r].sd.n - e);
-            w.ev_begin = e;
-            w.acc_base = r;
+    auto emit = [&](bool layered, bool tails) {
+        for (int r = 0; r < n; ++r) {
+            if ((b.h_samples[samp_of[r]].n_layers > 1) != layered) continue;
+            const int64_t nr = b.reqs[r].sd.n, full_end = nr / chunk * chunk;
+            for (int64_t e = tails ? full_end : 0; e < (tails ? nr : full_end); e += chunk) {
+                WorkItem &w = b.h_items[n_items++];
+                w.sample = samp_of[r];
+                w.point_base = r;
+                w.n_pts = 1;
+                w.ev_count = (int32_t)std::min<int64_t>(chunk, nr - e);
+                w.ev_begin = e;
+                w.acc_base = r;
+            }
         }
-    // items of layered samples first (each group largest first): a batch that mixes
-    // layered and single-layer samples runs each group with its own kernel, so a
-    // request's result does not depend on the other requests of its batch
-    std::stable_sort(b.h_items, b.h_items + n_items, [&](const WorkItem &x, const WorkItem &y) {
-        const bool lx = b.h_samples[x.sample].n_layers > 1, ly = b.h_samples[y.sample].n_layers > 1;
-        return lx != ly ? lx : x.ev_count > y.ev_count;
-    });
-    int n_lay = 0;
-    while (n_lay < n_items && b.h_samples[b.h_items[n_lay].sample].n_layers > 1) ++n_lay;
+    };
+    emit(true, false);
+    emit(true, true);
+    const int n_lay = n_items;
+    emit(false, false);
+    emit(false, true);
     cudaStream_t st = b.stream;
-    cudaError_t e = cudaMemcpyAsync(b.d_pts, b.h_pts, n * sizeof(osc_point), cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b.d_hmeta, b.h_hmeta, n * 4 * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b.d_items, b.h_items, n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(b.d_samples, b.h_samples, n_samp * sizeof(SampleDev), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(b.d_stage, b.h_stage, b.lay.items + (size_t)n_items * sizeof(WorkItem),
+                                    cudaMemcpyHostToDevice, st);
     if (!e) e = launch_point_consts(b.d_pts, n, b.d_pc32, b.d_pc64, st);
     if (e) return fail_cuda(ctx, e, "serving batch set-up");
     HistParams hp;
@@ -193,7 +229,6 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     }
     FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
     if (!e && !fused) e = launch_final(fp, st);
-    if (!e) e = cudaMemcpyAsync(b.h_out, b.d_out, (size_t)n * sv->nbins * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaLaunchHostFunc(st, on_batch_done, cb_arg);
     if (e) return fail_cuda(ctx, e, "serving batch launch");
     ctx->launches += 1 + kernels + (fused ? 0 : 1);
@@ -208,37 +243,12 @@ void scheduler(osc_serve *sv) {
     for (;;) {
         sv->cv.wait(lk, [&] {
             bool any_busy = false;
-            for (auto &b : sv->batch) {
-                if (b.busy && b.done) return true;
-                any_busy |= b.busy;
-            }
-            if (sv->stop) return !any_busy;
+            for (auto &b : sv->batch) any_busy |= b.busy;
+            if (sv->stop) return !any_busy;  // let in-flight batches finish
             if (sv->pending.empty() || sv->inflight >= sv->max_slots) return false;
             return !(sv->batch[0].busy && sv->batch[1].busy && sv->batch[2].busy);
         });
-        // publish finished batches
-        bool published = false;
-        for (auto &b : sv->batch) {
-            if (!(b.busy && b.done)) continue;
-            const auto now = Clock::now();
-            for (size_t r = 0; r < b.reqs.size(); ++r) {
-                Result res;
-                res.hist.assign(b.h_out + r * sv->nbins, b.h_out + (r + 1) * sv->nbins);
-                res.latency_us = std::chrono::duration<double, std::micro>(now - b.reqs[r].t_submit).count();
-                sv->results[b.reqs[r].ticket] = std::move(res);
-            }
-            sv->inflight -= (int32_t)b.reqs.size();
-            b.reqs.clear();
-            b.busy = b.done = false;
-            published = true;
-        }
-        if (published) sv->cv_done.notify_all();
-        if (sv->stop) {
-            bool any = false;
-            for (auto &b : sv->batch) any |= b.busy;
-            if (!any) break;
-            continue;  // let in-flight batches finish
-        }
+        if (sv->stop) break;
         // admit: one free batch slot, up to the free request slots, one precision per batch
         Batch *free_b = nullptr;
         int free_k = 0;
@@ -257,7 +267,6 @@ void scheduler(osc_serve *sv) {
         }
         sv->inflight += (int32_t)free_b->reqs.size();
         free_b->busy = true;
-        free_b->done = false;
         lk.unlock();
         osc_status st = launch_batch(sv, *free_b, &cb[free_k]);
         lk.lock();
@@ -278,20 +287,13 @@ void free_serve(osc_ctx *ctx, osc_serve *sv) {
             cudaStreamSynchronize(b.stream);
             cudaStreamDestroy(b.stream);
         }
-        dfree(ctx, b.d_pts);
+        dfree(ctx, b.d_stage);
         dfree(ctx, b.d_pc32);
         dfree(ctx, b.d_pc64);
         dfree(ctx, b.d_acc);
-        dfree(ctx, b.d_out);
-        dfree(ctx, b.d_hmeta);
-        dfree(ctx, b.d_items);
-        dfree(ctx, b.d_samples);
         dfree(ctx, b.d_counter);
-        cudaFreeHost(b.h_pts);
+        cudaFreeHost(b.h_stage);
         cudaFreeHost(b.h_out);
-        cudaFreeHost(b.h_hmeta);
-        cudaFreeHost(b.h_items);
-        cudaFreeHost(b.h_samples);
     }
     delete sv;
 }
@@ -318,27 +320,32 @@ osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi
     osc_status st = OSC_OK;
     for (auto &b : sv->batch) {
         void *p;
+        b.lay = StageLayout(S);
         cudaError_t e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
         if (e) st = fail_cuda(ctx, e, "cudaStreamCreate");
-        if (!st && !(st = dalloc(ctx, &p, S * sizeof(osc_point)))) b.d_pts = (osc_point *)p;
+        if (!st && !(st = dalloc(ctx, &p, b.lay.bytes))) b.d_stage = (char *)p;
         if (!st && !(st = dalloc(ctx, &p, S * C32_STRIDE * 4))) b.d_pc32 = (float *)p;
         if (!st && !(st = dalloc(ctx, &p, S * C64_STRIDE * 8))) b.d_pc64 = (double *)p;
         if (!st && !(st = dalloc(ctx, &p, S * B * 24))) b.d_acc = (unsigned long long *)p;
-        if (!st && !(st = dalloc(ctx, &p, S * B * 8))) b.d_out = (double *)p;
-        if (!st && !(st = dalloc(ctx, &p, S * 4 * 8))) b.d_hmeta = (double *)p;
-        if (!st && !(st = dalloc(ctx, &p, (size_t)kMaxItems * sizeof(WorkItem)))) b.d_items = (WorkItem *)p;
-        if (!st && !(st = dalloc(ctx, &p, S * sizeof(SampleDev)))) b.d_samples = (SampleDev *)p;
         if (!st && !(st = dalloc(ctx, &p, 64))) b.d_counter = (int32_t *)p;
         if (!st) {
+            b.d_pts = (osc_point *)(b.d_stage + b.lay.pts);
+            b.d_hmeta = (double *)(b.d_stage + b.lay.hmeta);
+            b.d_samples = (SampleDev *)(b.d_stage + b.lay.samples);
+            b.d_items = (WorkItem *)(b.d_stage + b.lay.items);
             e = cudaMemsetAsync(b.d_acc, 0, S * B * 24, b.stream);
             if (!e) e = cudaMemsetAsync(b.d_counter, 0, 64, b.stream);
-            if (!e) e = cudaHostAlloc((void **)&b.h_pts, S * sizeof(osc_point), 0);
-            if (!e) e = cudaHostAlloc((void **)&b.h_out, S * B * 8, 0);
-            if (!e) e = cudaHostAlloc((void **)&b.h_hmeta, S * 4 * 8, 0);
-            if (!e) e = cudaHostAlloc((void **)&b.h_items, (size_t)kMaxItems * sizeof(WorkItem), 0);
-            if (!e) e = cudaHostAlloc((void **)&b.h_samples, S * sizeof(SampleDev), 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_stage, b.lay.bytes, 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_out, S * B * 8, cudaHostAllocMapped);
+            if (!e) e = cudaHostGetDevicePointer((void **)&b.d_out, b.h_out, 0);
             if (!e) e = cudaStreamSynchronize(b.stream);
             if (e) st = fail_cuda(ctx, e, "serving buffers");
+        }
+        if (!st) {
+            b.h_pts = (osc_point *)(b.h_stage + b.lay.pts);
+            b.h_hmeta = (double *)(b.h_stage + b.lay.hmeta);
+            b.h_samples = (SampleDev *)(b.h_stage + b.lay.samples);
+            b.h_items = (WorkItem *)(b.h_stage + b.lay.items);
         }
         if (st) break;
     }
