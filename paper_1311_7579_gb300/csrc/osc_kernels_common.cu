@@ -75,6 +75,25 @@ cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStr
                           : launch_hist_fp64(pt, p, grid, st);
 }
 
+// The same launch with programmatic stream serialization: the kernel may start
+// while the preceding kernel of the stream still runs (its work that reads no
+// kernel output overlaps it; everything else waits in griddepcontrol.wait).
+cudaError_t launch_hist_programmatic(int prec, int pt, const HistParams &p, int grid, cudaStream_t st) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kNT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HistParams q = p;
+    void *args[] = {&q};
+    return cudaLaunchKernelExC(&cfg, hist_kernel_fn(prec, pt), args);
+}
+
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st) {
     int64_t n = p.n_hist * (int64_t)p.nbins;
     int64_t blocks = (n + 255) / 256;

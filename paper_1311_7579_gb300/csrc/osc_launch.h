@@ -10,6 +10,7 @@ namespace osc {
 cudaError_t launch_point_consts(const osc_point *d_pts, int n, float *pc32, double *pc64, cudaStream_t st);
 cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st);
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
+cudaError_t launch_hist_programmatic(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
 // Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).

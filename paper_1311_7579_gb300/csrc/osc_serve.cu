@@ -224,7 +224,8 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
         HistParams hs = hp;
         hs.items = b.d_items + n_lay;
         hs.n_items = n_items - n_lay;
-        e = launch_hist(prec, 1, hs, hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + 7) / 8), st);
+        // programmatic launch after the kernel before it (constants or layered histogram)
+        e = launch_hist_programmatic(prec, 1, hs, hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + 7) / 8), st);
         ++kernels;
     }
     FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
