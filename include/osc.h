@@ -33,6 +33,10 @@
  *     rejected on the host before any launch.  A CUDA error poisons the
  *     context: later calls return OSC_E_STATE; running out of device memory
  *     (OSC_E_NOMEM) does not.  Device code never traps.
+ *   - Autotuner cache: with OSC_AUTOTUNE_CACHE=<file> set when a context is
+ *     created, the launch shapes the autotuner picks are appended to <file> (one
+ *     line per GPU model and workload class) and read back by later contexts on
+ *     the same GPU model, which then skip tuning.
  *   - Fault injection (tests): with the environment variable
  *     OSC_FAULT_ALLOC_FAIL_AT=k set when a context is created, that context's
  *     k-th device allocation fails as if the device were out of memory.

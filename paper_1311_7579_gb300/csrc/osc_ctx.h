@@ -110,6 +110,8 @@ struct osc_ctx {
 
     int32_t tile_pt = 0, tile_chunk = 0;
     std::map<std::string, std::pair<int32_t, int32_t>> tuned;
+    std::string tune_file;    // autotuner results persisted here (OSC_AUTOTUNE_CACHE), or empty
+    std::string device_name;  // part of every persisted key
 
     osc_serve *serve = nullptr;
 };

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <numeric>
 #include <sstream>
 
@@ -335,6 +336,26 @@ static void drop_plans(osc_ctx *c) {
     c->plans.clear();
 }
 
+// Persisted autotuner results: one line per workload class,
+// "<device>/<SMs> <class> <points_per_block> <events_per_item>".  Lines of other
+// devices are ignored; unreadable files are treated as empty.
+static void load_tuned(osc_ctx *c) {
+    if (c->tune_file.empty()) return;
+    std::ifstream in(c->tune_file);
+    std::string dev, key;
+    int32_t pt, chunk;
+    while (in >> dev >> key >> pt >> chunk)
+        if (dev == c->device_name && (pt == 1 || pt == 4 || pt == 16 || pt == 64 || pt == 256) && chunk > 0 &&
+            chunk % 64 == 0)
+            c->tuned[key] = {pt, chunk};
+}
+
+static void save_tuned(osc_ctx *c, const std::string &key, int32_t pt, int32_t chunk) {
+    if (c->tune_file.empty()) return;
+    std::ofstream out(c->tune_file, std::ios::app);
+    if (out) out << c->device_name << " " << key << " " << pt << " " << chunk << "\n";
+}
+
 // ------------------------------------------------------------------ the ABI
 extern "C" {
 
@@ -359,12 +380,23 @@ osc_status osc_create(int device, size_t workspace_cap_bytes, void *cuda_stream,
     ctx->device = device;
     ctx->cap = workspace_cap_bytes;
     if (const char *f = std::getenv("OSC_FAULT_ALLOC_FAIL_AT")) ctx->fault_alloc_at = std::atoll(f);
+    if (const char *f = std::getenv("OSC_AUTOTUNE_CACHE")) ctx->tune_file = f;
     e = cudaSetDevice(device);
     if (e) {
         delete ctx;
         return OSC_E_CUDA;
     }
     cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+    {
+        cudaDeviceProp prop{};
+        if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) ctx->device_name = prop.name;
+        for (char &ch : ctx->device_name)
+            if (ch == ' ') ch = '_';
+        std::ostringstream o;
+        o << ctx->device_name << "/" << ctx->n_sm;
+        ctx->device_name = o.str();
+    }
+    load_tuned(ctx);
     if (cuda_stream) {
         ctx->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -1041,6 +1073,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
             pt = best_pt;
             chunk = best_chunk;
             ctx->tuned[key] = {pt, chunk};
+            save_tuned(ctx, key, pt, chunk);
         }
     }
     if (chunk == 0) chunk = default_chunk(ctx, ids, n_points, pt, pr);
