@@ -194,6 +194,48 @@ def cpu_baseline_leg(sample, point_row, gpu_p32, gpu_p64, n_sample):
     return cpu, prec, h
 
 
+def precision_per_config(api, synth, c):
+    """FP32-bulk and FP32_F64EIG |dP| against the FP64 oracle on each workload
+    shape (bounded subsets so the oracle finishes in seconds): the Table 1
+    sample (100k events), the scan sample at 4 scan points, the first 500k
+    events of each uneven sample at one point, and the 10M U(0.05, 30) GeV
+    validation energies subsampled to 1M (nu_mu -> nu_mu at Table 1)."""
+    import oracle
+    cases = []
+    cases.append(("table1_100k", synth.table1_sample(), synth.table1_point()[None, :]))
+    scan = synth.scan_sample()
+    cases.append(("scan_2M_x_4pts", scan, synth.scan_points()[[0, 1, 2047, 4095]]))
+    for j, u in enumerate(synth.uneven_samples()):
+        sub = {k: (v[:500_000] if isinstance(v, np.ndarray) else v) for k, v in u.items()}
+        sub["n"] = min(u["n"], 500_000)
+        cases.append(("uneven_%d_first500k" % j, sub, synth.uneven_points()[[3]]))
+    e = synth.validation_energies(1_000_000)
+    n = e.size
+    val = {"n": n, "e_true": e.astype(np.float32), "e_reco": e.astype(np.float32),
+           "w_mc": np.ones(n, np.float32), "flav_in": np.ones(n, np.uint8), "flav_out": np.ones(n, np.uint8),
+           "is_nubar": np.zeros(n, np.uint8), "baseline_km": 295.0, "density_gcc": 2.6, "ye": 0.5}
+    cases.append(("validation_1M_U(0.05,30)", val, synth.table1_point()[None, :]))
+    out = {}
+    for name, smp, pts in cases:
+        sid = api.osc_load_sample(c, smp)
+        api.osc_set_params(c, pts)
+        res = {"events": int(smp["n"]), "points": int(pts.shape[0])}
+        worst = {"fp32": [0.0, 0.0], "fp32_f64eig": [0.0, 0.0], "fp64": [0.0, 0.0]}
+        for k in range(pts.shape[0]):
+            po, _ = oracle.reweight(smp, oracle.point_from_row(pts[k]))
+            for prec in worst:
+                p = np.zeros(smp["n"])
+                api.osc_reweight(c, sid, k, prec, out_prob=p)
+                d = np.abs(p - po)
+                worst[prec][0] = max(worst[prec][0], float(d.max()))
+                worst[prec][1] = max(worst[prec][1], float(np.sqrt(np.mean(d ** 2))))
+        for prec, (mx, rms) in worst.items():
+            res[prec] = {"max_dP": mx, "rms_dP": rms}
+        out[name] = res
+        api.osc_unload_sample(c, sid)
+    return out
+
+
 def serving_leg(api, synth, c, rates, seconds, prec="fp32"):
     """Serving workload: requests (sample id uniform over the 8 uneven samples,
     point from the scan distribution) arrive as a Poisson process at each rate for
@@ -554,6 +596,7 @@ def run_ours(args):
             # bin-wise relative error of the full-sample histograms, FP32 vs FP64 GPU path
             nz = h64 != 0
             prec_study["fp32_vs_fp64_hist_max_rel"] = float(np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
+            prec_study["per_config"] = precision_per_config(api, synth, c)
         mcmc = mcmc_leg(api, synth, c, sid, sample, args.mcmc_steps) if args.mcmc_steps > 0 else None
         binned = bin_centre_leg(torch, api, synth, c, sid, sample, point, stream, flush, peaks.get("hbm_gbs"))
         layered = layers_leg(torch, api, synth, c, stream, flush)
