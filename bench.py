@@ -194,6 +194,16 @@ def cpu_baseline_leg(sample, point_row, gpu_p32, gpu_p64, n_sample):
     return cpu, prec, h
 
 
+_UNEVEN = []
+
+
+def _uneven_samples(synth):
+    """The 8 uneven samples (47.6M events), generated once per run."""
+    if not _UNEVEN:
+        _UNEVEN.extend(synth.uneven_samples())
+    return _UNEVEN
+
+
 def precision_per_config(api, synth, c):
     """FP32-bulk and FP32_F64EIG |dP| against the FP64 oracle on each workload
     shape (bounded subsets so the oracle finishes in seconds): the Table 1
@@ -205,7 +215,7 @@ def precision_per_config(api, synth, c):
     cases.append(("table1_100k", synth.table1_sample(), synth.table1_point()[None, :]))
     scan = synth.scan_sample()
     cases.append(("scan_2M_x_4pts", scan, synth.scan_points()[[0, 1, 2047, 4095]]))
-    for j, u in enumerate(synth.uneven_samples()):
+    for j, u in enumerate(_uneven_samples(synth)):
         sub = {k: (v[:500_000] if isinstance(v, np.ndarray) else v) for k, v in u.items()}
         sub["n"] = min(u["n"], 500_000)
         cases.append(("uneven_%d_first500k" % j, sub, synth.uneven_points()[[3]]))
@@ -243,7 +253,7 @@ def serving_leg(api, synth, c, rates, seconds, prec="fp32"):
     waits on the tickets.  Reports achieved request and event-weight throughput and
     the p50/p99 submit-to-completion latency measured inside the library."""
     import threading
-    samples = synth.uneven_samples()
+    samples = _uneven_samples(synth)
     sids = [api.osc_load_sample(c, s) for s in samples]
     sizes = np.array([s["n"] for s in samples], dtype=np.float64)
     api.osc_serve_start(c, 256, LO, 20.0, NBINS)
@@ -376,6 +386,37 @@ def bin_centre_leg(torch, api, synth, c, sid, sample, point, stream, flush, hbm_
     api.osc_unload_sample(c, qid)
     res["study_25MeV_bin_0.6GeV"] = {"event_by_event_over_bin_centre_minus_1": float(ee / bb - 1.0),
                                      "spectrum": "Gamma(3, 0.25 GeV), nu_mu -> nu_mu, 295 km, 2.6 g/cm^3"}
+    return res
+
+
+def configs_leg(torch, api, synth, c, stream, flush):
+    """The other workload configurations, one histogram call each (autotuned):
+    the 100k-event Table 1 sample x 1 point in FP64 and FP32, and the 8 uneven
+    samples (47.6M events) x 512 points in one FP32 launch."""
+    res = {}
+    s0 = synth.table1_sample()
+    sid = api.osc_load_sample(c, s0)
+    api.osc_set_params(c, synth.table1_point()[None, :])
+    out = torch.zeros((1, 1, NBINS), dtype=torch.float64, device=flush.device)
+    for prec in ("fp64", "fp32"):
+        ms = _event_times(torch, stream, flush, lambda: api.osc_histogram(
+            c, [sid], 0, 1, prec, LO, HI, NBINS, out=out), 50, 5)
+        t = float(np.median(ms))
+        res["table1_100k_x_1_%s" % prec] = {"value": s0["n"] / (t * 1e-3), "unit": UNIT, "call_ms_p50": t}
+    api.osc_unload_sample(c, sid)
+    ss = _uneven_samples(synth)
+    sids = [api.osc_load_sample(c, u) for u in ss]
+    pts = synth.uneven_points()
+    api.osc_set_params(c, pts)
+    out = torch.zeros((len(ss), pts.shape[0], NBINS), dtype=torch.float64, device=flush.device)
+    ms = _event_times(torch, stream, flush, lambda: api.osc_histogram(
+        c, sids, 0, pts.shape[0], "fp32", 0.0, 20.0, NBINS, out=out), 3, 2)
+    t = float(np.median(ms))
+    ev_pt = sum(u["n"] for u in ss) * pts.shape[0]
+    res["uneven_8_samples_x_512_fp32"] = {"value": ev_pt / (t * 1e-3), "unit": UNIT, "call_ms_p50": t,
+                                          "event_points": ev_pt}
+    for x in sids:
+        api.osc_unload_sample(c, x)
     return res
 
 
@@ -600,10 +641,12 @@ def run_ours(args):
         mcmc = mcmc_leg(api, synth, c, sid, sample, args.mcmc_steps) if args.mcmc_steps > 0 else None
         binned = bin_centre_leg(torch, api, synth, c, sid, sample, point, stream, flush, peaks.get("hbm_gbs"))
         layered = layers_leg(torch, api, synth, c, stream, flush)
-        scan = scan_leg(torch, api, synth, c, stream, flush)
+        configs = {"scan_2M_x_4096": scan_leg(torch, api, synth, c, stream, flush)}
+        configs.update(configs_leg(torch, api, synth, c, stream, flush))
         serving = None
         if args.serve_seconds > 0:
-            serving = {"fp32": serving_leg(api, synth, c, (2000, 10000, 20000), args.serve_seconds, "fp32"),
+            serving = {"fp32": serving_leg(api, synth, c, (1000, 2000, 10000, 20000, 50000), args.serve_seconds,
+                                           "fp32"),
                        "fp64": serving_leg(api, synth, c, (100,), args.serve_seconds, "fp64")}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -640,7 +683,7 @@ def run_ours(args):
             "mcmc": mcmc,
             "bin_centre": binned,
             "layers": layered,
-            "batched_scan": scan,
+            "configs": configs,
         }
         print(json.dumps(result), flush=True)
     ctx.close()
