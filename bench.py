@@ -442,6 +442,44 @@ def scan_leg(torch, api, synth, c, stream, flush, k=5):
     return res
 
 
+def scaling_leg(api, synth, c, sample, point):
+    """The paper's timing experiment (Sec. 2.2) redone on this GPU: probabilities
+    for N events with the results copied back to the host (osc_reweight into a
+    host array: wall time of the call, FP64 as in the paper and FP32-bulk), against
+    the oracle on one host core and on all of them, for N = 1e2 ... 1e7."""
+    import oracle
+    api.osc_set_params(c, point)
+    cores = oracle.num_threads()
+    rows = []
+    for n in (100, 1_000, 10_000, 100_000, 1_000_000, 10_000_000):
+        sub = {k: (v[:n] if isinstance(v, np.ndarray) else v) for k, v in sample.items()}
+        sub["n"] = n
+        sid = api.osc_load_sample(c, sub)
+        prob = np.zeros(n)
+        row = {"n": n}
+        for prec in ("fp64", "fp32"):
+            api.osc_reweight(c, sid, 0, prec, out_prob=prob)  # warm
+            reps = max(3, min(200, 2_000_000 // n))
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                api.osc_reweight(c, sid, 0, prec, out_prob=prob)
+            row["gpu_%s_per_s" % prec] = n * reps / (time.perf_counter() - t0)
+        api.osc_unload_sample(c, sid)
+        pt = oracle.point_from_row(point[0])
+        m = min(n, 100_000)  # the oracle's rate from at most 1e5 events
+        part = dict(sub, n=m)
+        for threads, key in ((1, "cpu_1_core_per_s"), (cores, "cpu_all_cores_per_s")):
+            oracle.set_num_threads(threads)
+            t0 = time.perf_counter()
+            oracle.reweight(part, pt)
+            row[key] = m / (time.perf_counter() - t0)
+        oracle.set_num_threads(cores)
+        row["gpu_fp64_over_cpu_1_core"] = row["gpu_fp64_per_s"] / row["cpu_1_core_per_s"]
+        rows.append(row)
+    return {"what": "per-event probabilities copied back to the host (osc_reweight), wall time per call",
+            "cores": cores, "rows": rows}
+
+
 def layers_leg(torch, api, synth, c, stream, flush, k=20):
     """Layered matter: a 2M-event 1300 km beam-shaped sample through three layers
     (400 km at 2.6, 500 km at 3.3, 400 km at 2.6 g/cm^3), one point, histogram
@@ -641,6 +679,7 @@ def run_ours(args):
         mcmc = mcmc_leg(api, synth, c, sid, sample, args.mcmc_steps) if args.mcmc_steps > 0 else None
         binned = bin_centre_leg(torch, api, synth, c, sid, sample, point, stream, flush, peaks.get("hbm_gbs"))
         layered = layers_leg(torch, api, synth, c, stream, flush)
+        scaling = scaling_leg(api, synth, c, sample, point) if not args.no_cpu_baseline else None
         configs = {"scan_2M_x_4096": scan_leg(torch, api, synth, c, stream, flush)}
         configs.update(configs_leg(torch, api, synth, c, stream, flush))
         serving = None
@@ -684,6 +723,7 @@ def run_ours(args):
             "bin_centre": binned,
             "layers": layered,
             "configs": configs,
+            "scaling_vs_n": scaling,
         }
         print(json.dumps(result), flush=True)
     ctx.close()
