@@ -10,7 +10,8 @@
 // The table is tiny next to the event stream, so the histogram kernel is bound
 // by reading the 16-byte event records: each lane works on four records while
 // the next four are loaded, and the kernel is launched programmatically after
-// the table kernel so that its first loads overlap the table computation.
+// the table kernel so that its first loads overlap the table computation (and
+// the finalize kernel programmatically after it).
 #include "osc_layers.cuh"
 #include "osc_launch.h"
 
@@ -121,6 +122,7 @@ constexpr int kBcUnroll = 4;  // event records per lane per step; the next step'
 
 template <bool F64>
 __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
+    grid_dependents_launch();  // the finalize kernel after this one may become resident early
     const HistParams &prm = b.h;
     const int lane = threadIdx.x & 31;
     // first item of every warp assigned statically, later ones from the counter
@@ -203,9 +205,6 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
         if (it < prm.n_items) fetch(it);
         acc_finish_warp(r, accp);
     }
-    // block-level completion ticket: one atomic per block rather than per warp,
-    // and the last block converts the bins with all its threads
-    if (prm.fuse_final) fused_final(prm);
 }
 
 const void *bc_hist_kernel_fn(int prec) {

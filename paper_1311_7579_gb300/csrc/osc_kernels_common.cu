@@ -1,4 +1,6 @@
 // Constants and finalize kernels, and the precision dispatch of the launch helpers.
+#include <algorithm>
+
 #include "osc_kernels.cuh"
 #include "osc_launch.h"
 
@@ -19,14 +21,38 @@ __global__ void __launch_bounds__(kConstThreads) k_point_consts_v(const PointsBy
     point_consts_block(pv.p[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
 }
 
-__global__ void k_final(const FinalParams f) {
+// Converts the exact bins to doubles and clears them for the next launch.  It
+// is launched programmatically after the histogram kernel: its blocks may be
+// resident before that grid ends, and griddepcontrol.wait returns once the grid
+// has completed and its reductions are visible.  Each thread loads the digit
+// columns of up to kFinPerThread bins before converting any (one memory round
+// trip rather than one per bin).
+constexpr int kFinPerThread = 4;
+__global__ void __launch_bounds__(256) k_final(const FinalParams f) {
+    grid_dependency_wait();
     const int64_t n = f.n_hist * (int64_t)f.nbins;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long d0 = f.acc[3 * i], d1 = f.acc[3 * i + 1], d2 = f.acc[3 * i + 2];
-        f.acc[3 * i] = 0ull;
-        f.acc[3 * i + 1] = 0ull;
-        f.acc[3 * i + 2] = 0ull;
-        f.out[i] = final_bin(d0, d1, d2, f.hmeta + 4 * (i / f.nbins), f.pc64);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += stride * kFinPerThread) {
+        unsigned long long d[kFinPerThread][3];
+#pragma unroll
+        for (int k = 0; k < kFinPerThread; ++k) {
+            const int64_t i = i0 + k * stride;
+            if (i < n) {
+                d[k][0] = __ldcg(f.acc + 3 * i);
+                d[k][1] = __ldcg(f.acc + 3 * i + 1);
+                d[k][2] = __ldcg(f.acc + 3 * i + 2);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kFinPerThread; ++k) {
+            const int64_t i = i0 + k * stride;
+            if (i < n) {
+                f.acc[3 * i] = 0ull;
+                f.acc[3 * i + 1] = 0ull;
+                f.acc[3 * i + 2] = 0ull;
+                f.out[i] = final_bin(d[k][0], d[k][1], d[k][2], f.hmeta + 4 * (i / f.nbins), f.pc64);
+            }
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
 }
@@ -94,13 +120,29 @@ cudaError_t launch_hist_programmatic(int prec, int pt, const HistParams &p, int 
     return cudaLaunchKernelExC(&cfg, hist_kernel_fn(prec, pt), args);
 }
 
+int final_blocks(int64_t n_bins) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n_bins + 255) / 256, 152 * 8));
+}
+
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st) {
-    int64_t n = p.n_hist * (int64_t)p.nbins;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_final<<<(int)blocks, 256, 0, st>>>(p);
+    k_final<<<final_blocks(p.n_hist * (int64_t)p.nbins), 256, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_final_programmatic(const FinalParams &p, cudaStream_t st) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(final_blocks(p.n_hist * (int64_t)p.nbins));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FinalParams q = p;
+    void *args[] = {&q};
+    return cudaLaunchKernelExC(&cfg, (const void *)k_final, args);
 }
 
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st) {

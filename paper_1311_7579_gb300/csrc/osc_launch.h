@@ -12,6 +12,9 @@ cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32,
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
 cudaError_t launch_hist_programmatic(int prec, int pt, const HistParams &p, int grid, cudaStream_t st);
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
+// The finalize kernel with programmatic stream serialization (after a histogram kernel).
+cudaError_t launch_final_programmatic(const FinalParams &p, cudaStream_t st);
+int final_blocks(int64_t n_bins);
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
 // Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
 const void *hist_kernel_fn(int prec, int pt);

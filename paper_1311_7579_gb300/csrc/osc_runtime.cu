@@ -1225,50 +1225,29 @@ static osc_status run_bc_plan(osc_ctx *ctx, Plan *p, double lo, double hi, doubl
     bp.t_nb_f = (float)p->t_nbins;
     bp.tab32 = p->prec == kFP64 ? nullptr : (float *)p->d_tab;
     bp.tabq = p->prec == kFP64 ? (unsigned long long *)p->d_tab : nullptr;
-    const bool fused = fuse_finalize(p->n_hist, p->nbins);
-    if (fused) {
-        bp.h.fuse_final = 1;
-        bp.h.fin_n_hist = p->n_hist;
-        bp.h.fin_hmeta = p->d_hmeta;
-        bp.h.fin_out = d_out;
-    }
     FinalParams fp{ctx->d_acc, p->d_hmeta, ctx->d_pc64, d_out, p->n_hist, p->nbins, ctx->d_counter};
     void *targs[] = {&bp};
     void *hargs[] = {&bp};
-    void *fargs[] = {&fp};
-    cudaKernelNodeParams kt{};
-    kt.func = (void *)bc_table_kernel_fn(p->prec);
-    kt.gridDim = dim3(p->table_grid);
-    kt.blockDim = dim3(bc_table_threads());
-    kt.kernelParams = targs;
-    cudaKernelNodeParams kh{};
-    kh.func = (void *)bc_hist_kernel_fn(p->prec);
-    kh.gridDim = dim3(p->grid);
-    kh.blockDim = dim3(hist_threads());
-    kh.kernelParams = hargs;
-    cudaKernelNodeParams kf{};
-    kf.func = (void *)final_kernel_fn();
-    const int64_t nfin = p->n_hist * (int64_t)p->nbins;
-    kf.gridDim = dim3((unsigned)std::min<int64_t>(std::max<int64_t>((nfin + 255) / 256, 1), (int64_t)ctx->n_sm * 8));
-    kf.blockDim = dim3(256);
-    kf.kernelParams = fargs;
     // table kernel, then the histogram kernel by programmatic dependent launch
     // (it fetches its first items and events while the table is computed), then
-    // the finalize kernel for large outputs
-    CK(cudaLaunchKernel(kt.func, kt.gridDim, kt.blockDim, targs, 0, ctx->stream));
+    // the finalize kernel the same way: its blocks are resident when the
+    // histogram grid completes, and no block of the histogram kernel waits at a
+    // barrier for the block's slowest warp to convert the bins
+    CK(cudaLaunchKernel(bc_table_kernel_fn(p->prec), dim3(p->table_grid), dim3(bc_table_threads()), targs, 0,
+                        ctx->stream));
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = kh.gridDim;
-    cfg.blockDim = kh.blockDim;
+    cfg.gridDim = dim3(p->grid);
+    cfg.blockDim = dim3(hist_threads());
     cfg.dynamicSmemBytes = 0;
     cfg.stream = ctx->stream;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelExC(&cfg, kh.func, hargs));
-    if (!fused) CK(cudaLaunchKernel(kf.func, kf.gridDim, kf.blockDim, fargs, 0, ctx->stream));
-    ctx->launches += fused ? 2 : 3;
+    CK(cudaLaunchKernelExC(&cfg, bc_hist_kernel_fn(p->prec), hargs));
+    CK(launch_final_programmatic(fp, ctx->stream));
+    ctx->launches += 3;
     return OSC_OK;
 }
 
