@@ -100,7 +100,7 @@ typedef struct {
     double s2_12, s2_13, s2_23; /* sin^2 theta_ij in [0, 1] */
     double dm21;                /* eV^2, > 0 */
     double dm32;                /* eV^2, |dm32| > dm21 (non-degenerate vacuum spectrum) */
-    double dcp;                 /* rad, finite */
+    double dcp;                 /* rad, |dcp| <= 1e6 */
     double escale;              /* energy scale applied to E_reco before binning, > 0 */
     double norm;                /* weight normalisation, finite */
 } osc_point;

@@ -63,108 +63,123 @@ __device__ __forceinline__ void split_ff(double v, float *hi, float *lo) {
     *lo = (float)(v - (double)h);
 }
 
-// One block of three warps per point.  Independent FP64 chains run on different
-// warps so that they overlap (divergent lanes of one warp would serialise):
-//   1. warp 0 lanes 0-5: the six square roots | warp 1: sine/cosine of delta
-//   2. warp 0 lanes 0-8: one entry each of H0 = U diag(m) U^dagger and H0^2
-//      | warp 1: sorted vacuum spectrum, |U_e|^2 and shifted-cubic constants
-//      | warp 2: trace, c1(0) and the systematics
-//   3. warp 0 lanes 0-8: one channel each | warp 2: depressed-cubic coefficients
-constexpr int kConstThreads = 96;
+// sin and cos of delta in FP64, evaluated by two lanes in the same instruction
+// stream (lane 0 the sine, lane 1 the cosine), so that the chain is one
+// polynomial long.  Cody and Waite's reduction by pi/2 with a two-part constant
+// (the high part has 33 significant bits, so k * hi is exact for |k| < 2^20)
+// leaves r in [-pi/4, pi/4]; the Taylor series of sin r / r and cos r in u = r^2
+// through u^8 truncate below 3e-18.  Returns (sin, cos) of delta on lane 0.
+__device__ __forceinline__ void sincos_lanes(double x, int lane, double *sn, double *cs) {
+    constexpr double kTwoOverPi = 0.63661977236758134308;
+    constexpr double kPio2Hi = 1.5707963267341256;        // pi/2 to 33 bits
+    constexpr double kPio2Lo = 6.077100506506192e-11;     // pi/2 - kPio2Hi
+    const double k = rint(x * kTwoOverPi);
+    const double r = fma(-k, kPio2Lo, fma(-k, kPio2Hi, x));
+    const double u = r * r;
+    const bool c = lane == 1;
+    // coefficients (-1)^j / (2j + 1)! (sine) and (-1)^j / (2j)! (cosine), j = 8 .. 1
+    double p = c ? 1.0 / 20922789888000.0 : 1.0 / 355687428096000.0;
+    p = fma(p, u, c ? -1.0 / 87178291200.0 : -1.0 / 1307674368000.0);
+    p = fma(p, u, c ? 1.0 / 479001600.0 : 1.0 / 6227020800.0);
+    p = fma(p, u, c ? -1.0 / 3628800.0 : -1.0 / 39916800.0);
+    p = fma(p, u, c ? 1.0 / 40320.0 : 1.0 / 362880.0);
+    p = fma(p, u, c ? -1.0 / 720.0 : -1.0 / 5040.0);
+    p = fma(p, u, c ? 1.0 / 24.0 : 1.0 / 120.0);
+    p = fma(p, u, c ? -1.0 / 2.0 : -1.0 / 6.0);
+    p = fma(p, u, 1.0);
+    const double v = c ? p : p * r;
+    const double w = __shfl_xor_sync(0x3u, v, 1);
+    const int q = (int)k & 3;  // quadrant, two's complement for negative k
+    *sn = q == 0 ? v : q == 1 ? w : q == 2 ? -v : -w;
+    *cs = q == 0 ? w : q == 1 ? -v : q == 2 ? -w : v;
+}
+
+// PMNS entry U[f][m] (PDG: U_e3 = s13 e^{-i delta}, e^{+i delta} in the mu and
+// tau rows of the first two mass columns), written for every (f, m) as
+// a + b s13 (cos delta + i g sin delta), with a and b products of two of the
+// sines and cosines; each lane of one instruction stream picks its operands.
+// t = (s12, c12, s13, c13, s23, c23, sin delta, cos delta).
+__device__ __forceinline__ cplx64 pmns_entry(const double *t, int f, int m) {
+    const double s12 = t[0], c12 = t[1], s13 = t[2], c13 = t[3], s23 = t[4], c23 = t[5], sd = t[6], cd = t[7];
+    double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0, g = 1.0;
+    if (f == 0) {
+        if (m == 0) { ax = c12; ay = c13; }
+        else if (m == 1) { ax = s12; ay = c13; }
+        else { bx = 1.0; by = 1.0; g = -1.0; }
+    } else if (m == 2) {
+        ax = (f == 1) ? s23 : c23; ay = c13;
+    } else if (f == 1) {
+        ax = (m == 0) ? -s12 : c12; ay = c23;
+        bx = (m == 0) ? -c12 : -s12; by = s23;
+    } else {
+        ax = (m == 0) ? s12 : -c12; ay = s23;
+        bx = (m == 0) ? -c12 : -s12; by = c23;
+    }
+    const double bs = bx * by * s13;
+    return {fma(bs, cd, ax * ay), bs * (g * sd)};
+}
+
+// One block of four warps (one per scheduler) per point.  FP64 runs at a small
+// fraction of the FP32 rate on this GPU: a warp instruction occupies its
+// scheduler's FP64 unit for many cycles whatever the number of active lanes, so
+// the kernel's latency is the number of FP64 instructions on its longest path.
+// Independent work therefore runs on different warps, and parallel work as one
+// instruction stream over lanes with per-lane operands (never as divergent
+// branches, which would issue each path in turn):
+//   1. warp 0 lanes 0-5: the six square roots | warp 1 lanes 0-1: sin, cos delta
+//      | warp 2 lanes 0-1: shifted-cubic constants of sorted root lane (from the
+//      sorted vacuum spectrum and |U_e|^2 = products of the s^2 inputs)
+//      | warp 3: sorted spectrum, gaps, float-float differences, T0, c1(0), systematics
+//   2. warp 0 lanes 0-8: one PMNS entry each
+//   3. warp 0 lanes 0-8: one entry each of H0 = U diag(m) U^dagger and H0^2
+//      | warp 2 lanes 1-9: U with its columns in the sorted vacuum order
+//   4. warp 0 lanes 0-8: one channel each | warp 2 lanes 0-4: one
+//      depressed-cubic coefficient each
+constexpr int kConstThreads = 128;
 __device__ inline void point_consts_block(const osc_point &P, float *c32, double *c64) {
     __shared__ double t[8];
+    __shared__ cplx64 Us[9];     // U[f][m] at 3 f + m
     __shared__ double Hs[4][9];  // H re, H im, H2 re, H2 im, entry (b, a) at 3 b + a
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double dm21 = P.dm21, dm31 = P.dm32 + P.dm21;
+    const double T0 = dm21 + dm31;
+    const double c10 = dm21 * dm31;
+    // sorted vacuum spectrum d0 <= d1 <= d2 (normal ordering 0, dm21, dm31;
+    // inverted dm31, 0, dm21) and the matching |U_e|^2
+    const bool no = dm31 > 0;
+    const double d0 = no ? 0.0 : dm31, d1 = no ? dm21 : 0.0, d2 = no ? dm31 : dm21;
     if (warp == 0 && lane < 6) {
         const double x = (lane == 0) ? P.s2_12 : (lane == 1) ? 1.0 - P.s2_12 : (lane == 2) ? P.s2_13
                        : (lane == 3) ? 1.0 - P.s2_13 : (lane == 4) ? P.s2_23 : 1.0 - P.s2_23;
         t[lane] = sqrt(x);
     }
-    if (warp == 1 && lane == 0) sincos(P.dcp, &t[6], &t[7]);
-    __syncthreads();
-    const double s12 = t[0], c12 = t[1], s13 = t[2], c13 = t[3], s23 = t[4], c23 = t[5], sd = t[6], cd = t[7];
-    const double dm21 = P.dm21, dm31 = P.dm32 + P.dm21;
-    const double T0 = dm21 + dm31;
-    const double c10 = dm21 * dm31;
-    if (warp == 0 && lane < 9) {
-        // columns 1, 2 of the PDG PMNS rows needed (U_e3 = s13 e^{-i delta},
-        // e^{+i delta} in the mu and tau rows; column 0 carries m = 0)
-        const int b = lane / 3, a = lane % 3;
-        cplx64 Ub[3], Ua[3];
-        for (int side = 0; side < 2; ++side) {
-            const int f = side ? a : b;
-            cplx64 *u = side ? Ua : Ub;
-            if (f == 0) {
-                u[1] = {s12 * c13, 0.0};
-                u[2] = {s13 * cd, -s13 * sd};
-            } else if (f == 1) {
-                u[1] = {c12 * c23 - s12 * s23 * s13 * cd, -s12 * s23 * s13 * sd};
-                u[2] = {s23 * c13, 0.0};
-            } else {
-                u[1] = {-c12 * s23 - s12 * c23 * s13 * cd, -s12 * c23 * s13 * sd};
-                u[2] = {c23 * c13, 0.0};
-            }
+    if (warp == 1 && lane < 2) {
+        double sn, cs;
+        sincos_lanes(P.dcp, lane, &sn, &cs);
+        if (lane == 0) {
+            t[6] = sn;
+            t[7] = cs;
         }
-        const double m[3] = {0.0, dm21, dm31};
-        cplx64 h = {0, 0}, h2 = {0, 0};
-        for (int k = 1; k < 3; ++k) {
-            const cplx64 q = cmul_conj(Ub[k], m[k], Ua[k]);
-            h.re += q.re; h.im += q.im;
-            h2.re += q.re * m[k]; h2.im += q.im * m[k];
-        }
-        Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
     }
-    if (warp == 1 && lane == 0) {
-        const double ze[3] = {c12 * c12 * c13 * c13, s12 * s12 * c13 * c13, s13 * s13};
-        double d[3], z[3];
-        if (dm31 > 0) {
-            d[0] = 0.0; d[1] = dm21; d[2] = dm31;
-            z[0] = ze[0]; z[1] = ze[1]; z[2] = ze[2];
-        } else {
-            d[0] = dm31; d[1] = 0.0; d[2] = dm21;
-            z[0] = ze[2]; z[1] = ze[0]; z[2] = ze[1];
-        }
-        for (int l = 0; l < 2; ++l) {
-            const int j = (l + 1) % 3, k = (l + 2) % 3;
-            const double aj = d[l] - d[j], ak = d[l] - d[k];
-            const int o = l ? (C32_S1 - C32_S0) : 0;
-            c32[C32_S0 + o] = (float)(aj + ak);
-            c32[C32_PI0 + o] = (float)(aj * ak);
-            c32[C32_W0 + o] = (float)(z[l] * (aj + ak) + z[j] * ak + z[k] * aj);
-            c32[C32_E0 + o] = (float)(z[l] * aj * ak);
-        }
-        c32[C32_D0] = (float)d[0]; c32[C32_D1] = (float)d[1]; c32[C32_D2] = (float)d[2];
-        c64[C64_LD] = d[0]; c64[C64_LD + 1] = d[1]; c64[C64_LD + 2] = d[2];
-        c32[C32_G01] = (float)(d[0] - d[1]); c32[C32_G02] = (float)(d[0] - d[2]); c32[C32_G12] = (float)(d[1] - d[2]);
-        split_ff(d[1] - d[0], &c32[C32_V1H], &c32[C32_V1L]);
-        split_ff(d[2] - d[0], &c32[C32_V2H], &c32[C32_V2L]);
+    if (warp == 2 && lane < 2) {
+        // sorted root l = lane and the other two j, k: a_j = d_l - d_j, a_k = d_l - d_k
+        const double ze0 = (1.0 - P.s2_12) * (1.0 - P.s2_13), ze1 = P.s2_12 * (1.0 - P.s2_13), ze2 = P.s2_13;
+        const double z0 = no ? ze0 : ze2, z1 = no ? ze1 : ze0, z2 = no ? ze2 : ze1;
+        const double dl = lane ? d1 : d0, dj = lane ? d2 : d1, dk = lane ? d0 : d2;
+        const double zl = lane ? z1 : z0, zj = lane ? z2 : z1, zk = lane ? z0 : z2;
+        const double aj = dl - dj, ak = dl - dk;
+        const int o = lane ? (C32_S1 - C32_S0) : 0;
+        c32[C32_S0 + o] = (float)(aj + ak);
+        c32[C32_PI0 + o] = (float)(aj * ak);
+        c32[C32_W0 + o] = (float)(zl * (aj + ak) + zj * ak + zk * aj);
+        c32[C32_E0 + o] = (float)(zl * aj * ak);
     }
-    if (warp == 2 && lane >= 1 && lane <= 9) {
-        // PMNS entry U[f][m] with its mass column m in the sorted vacuum order
-        // (normal ordering 0, dm21, dm31; inverted dm31, 0, dm21), for the
-        // mass-basis propagation through layered matter
-        const int f = (lane - 1) / 3, l = (lane - 1) % 3;
-        const int m = (dm31 > 0) ? l : (l + 2) % 3;
-        double ur, ui;
-        if (f == 0) {
-            ur = (m == 0) ? c12 * c13 : (m == 1) ? s12 * c13 : s13 * cd;
-            ui = (m == 2) ? -s13 * sd : 0.0;
-        } else if (m == 2) {
-            ur = (f == 1) ? s23 * c13 : c23 * c13;
-            ui = 0.0;
-        } else {
-            // mu, tau rows: a - b s13 e^{+i delta}
-            const double a = (f == 1) ? ((m == 0) ? -s12 * c23 : c12 * c23) : ((m == 0) ? s12 * s23 : -c12 * s23);
-            const double b = (f == 1) ? ((m == 0) ? c12 * s23 : s12 * s23) : ((m == 0) ? c12 * c23 : s12 * c23);
-            ur = a - b * s13 * cd;
-            ui = -b * s13 * sd;
-        }
-        c32[C32_LU + 2 * (lane - 1)] = (float)ur;
-        c32[C32_LU + 2 * (lane - 1) + 1] = (float)ui;
-        c64[C64_LU + 2 * (lane - 1)] = ur;
-        c64[C64_LU + 2 * (lane - 1) + 1] = ui;
-    }
-    if (warp == 2 && lane == 0) {
+    if (warp == 3 && lane == 0) {
+        c32[C32_D0] = (float)d0; c32[C32_D1] = (float)d1; c32[C32_D2] = (float)d2;
+        c64[C64_LD] = d0; c64[C64_LD + 1] = d1; c64[C64_LD + 2] = d2;
+        c32[C32_G01] = (float)(d0 - d1); c32[C32_G02] = (float)(d0 - d2); c32[C32_G12] = (float)(d1 - d2);
+        split_ff(d1 - d0, &c32[C32_V1H], &c32[C32_V1L]);
+        split_ff(d2 - d0, &c32[C32_V2H], &c32[C32_V2L]);
         c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10;
         c64[C64_T0] = T0; c64[C64_C10] = c10;
         c32[C32_ESCALE] = (float)P.escale;
@@ -172,14 +187,39 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
         c64[C64_NORM] = P.norm;
     }
     __syncthreads();
+    if (warp == 0 && lane < 9) Us[lane] = pmns_entry(t, lane / 3, lane % 3);
+    __syncthreads();
+    if (warp == 0 && lane < 9) {
+        // entry (b, a) of H0 and H0^2: sum over the mass columns 1, 2 (column 0 carries m = 0)
+        const int b = lane / 3, a = lane % 3;
+        const double m[3] = {0.0, dm21, dm31};
+        cplx64 h = {0, 0}, h2 = {0, 0};
+        for (int k = 1; k < 3; ++k) {
+            const cplx64 q = cmul_conj(Us[3 * b + k], m[k], Us[3 * a + k]);
+            h.re += q.re; h.im += q.im;
+            h2.re += q.re * m[k]; h2.im += q.im * m[k];
+        }
+        Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
+    }
+    if (warp == 2 && lane >= 1 && lane <= 9) {
+        // PMNS entry U[f][m] with its mass column m in the sorted vacuum order,
+        // for the mass-basis propagation through layered matter
+        const int f = (lane - 1) / 3, l = (lane - 1) % 3;
+        const int m = no ? l : (l + 2) % 3;
+        const cplx64 u = Us[3 * f + m];
+        c32[C32_LU + 2 * (lane - 1)] = (float)u.re;
+        c32[C32_LU + 2 * (lane - 1) + 1] = (float)u.im;
+        c64[C64_LU + 2 * (lane - 1)] = u.re;
+        c64[C64_LU + 2 * (lane - 1) + 1] = u.im;
+    }
+    __syncthreads();
     if (warp == 0 && lane < 9) {
         // channel (alpha -> beta) = lane (alpha * 3 + beta):
         // X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
         const int a = lane / 3, b = lane % 3;
         const int o = 6 * lane;
-        double Zr = 0, Zi = 0;
-        if (a == 0) { Zr += Hs[0][3 * b]; Zi += Hs[1][3 * b]; }
-        if (b == 0) { Zr += Hs[0][a]; Zi += Hs[1][a]; }
+        const double Zr = (a == 0 ? Hs[0][3 * b] : 0.0) + (b == 0 ? Hs[0][a] : 0.0);
+        const double Zi = (a == 0 ? Hs[1][3 * b] : 0.0) + (b == 0 ? Hs[1][a] : 0.0);
         const int ba = 3 * b + a;
         const double v[6] = {Hs[0][ba], Hs[1][ba], Hs[2][ba], Hs[3][ba], Zr, Zi};
         for (int k = 0; k < 6; ++k) {
@@ -187,21 +227,39 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
             c64[C64_CH + o + k] = v[k];
         }
     }
-    if (warp == 2 && lane == 0) {
+    if (warp == 2 && lane < 5) {
         // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
-        //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee
+        //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee;
+        // lane j forms coefficient j of (p0, p1, q0, q1, q2) as one weighted sum
+        //   w3 T0^3 + w2 T0^2 + w1 T0 + wc c10 + wct c10 T0 + ws smt + wst smt T0 - [j = 3] mee
         constexpr double k3 = 1.0 / 3.0, k9 = 1.0 / 9.0, k27 = 1.0 / 27.0;
         const double smt = Hs[0][4] + Hs[0][8];
-        const double mee = Hs[0][4] * Hs[0][8] - (Hs[0][5] * Hs[0][5] + Hs[1][5] * Hs[1][5]);
-        const double p0 = c10 - T0 * T0 * k3, p1 = smt - 2.0 * T0 * k3;
-        const double q0 = -2.0 * T0 * T0 * T0 * k27 + c10 * T0 * k3;
-        const double q1 = -2.0 * T0 * T0 * k9 + c10 * k3 + smt * T0 * k3 - mee;
-        const double q2 = -2.0 * T0 * k9 + smt * k3;
-        c32[C32_P0] = (float)p0; c32[C32_P1] = (float)p1;
-        c32[C32_Q0] = (float)q0; c32[C32_Q1] = (float)q1; c32[C32_Q2] = (float)q2;
-        c32[C32_SMT] = (float)smt;
-        c64[C64_P0] = p0; c64[C64_P1] = p1; c64[C64_Q0] = q0; c64[C64_Q1] = q1; c64[C64_Q2] = q2;
-        c64[C64_SMT] = smt;
+        const double mee = fma(Hs[0][4], Hs[0][8], -fma(Hs[0][5], Hs[0][5], Hs[1][5] * Hs[1][5]));
+        const double w3 = lane == 2 ? -2.0 * k27 : 0.0;
+        const double w2 = lane == 0 ? -k3 : lane == 3 ? -2.0 * k9 : 0.0;
+        const double w1 = lane == 1 ? -2.0 * k3 : lane == 4 ? -2.0 * k9 : 0.0;
+        const double wc = lane == 0 ? 1.0 : lane == 3 ? k3 : 0.0;
+        const double wct = lane == 2 ? k3 : 0.0;
+        const double ws = lane == 1 ? 1.0 : lane == 4 ? k3 : 0.0;
+        const double wst = lane == 3 ? k3 : 0.0;
+        const double wm = lane == 3 ? -1.0 : 0.0;
+        const double T2 = T0 * T0;
+        double v = wm * mee;
+        v = fma(wst, smt * T0, v);
+        v = fma(ws, smt, v);
+        v = fma(wct, c10 * T0, v);
+        v = fma(wc, c10, v);
+        v = fma(w1, T0, v);
+        v = fma(w2, T2, v);
+        v = fma(w3, T2 * T0, v);
+        const int o32 = lane == 0 ? C32_P0 : lane == 1 ? C32_P1 : lane == 2 ? C32_Q0 : lane == 3 ? C32_Q1 : C32_Q2;
+        const int o64 = lane == 0 ? C64_P0 : lane == 1 ? C64_P1 : lane == 2 ? C64_Q0 : lane == 3 ? C64_Q1 : C64_Q2;
+        c32[o32] = (float)v;
+        c64[o64] = v;
+        if (lane == 0) {
+            c32[C32_SMT] = (float)smt;
+            c64[C64_SMT] = smt;
+        }
     }
 }
 

@@ -162,7 +162,7 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
     if (!(fin(P.s2_12) && fin(P.s2_13) && fin(P.s2_23) && fin(P.dm21) && fin(P.dm32) && fin(P.dcp) &&
           fin(P.escale) && fin(P.norm)) ||
         !(P.s2_12 > 0 && P.s2_12 < 1) || !(P.s2_13 > 0 && P.s2_13 < 1) || !(P.s2_23 >= 0 && P.s2_23 <= 1) ||
-        !(P.dm21 > 0) || !(std::fabs(P.dm32) > P.dm21) || !(P.escale > 0)) {
+        !(P.dm21 > 0) || !(std::fabs(P.dm32) > P.dm21) || !(P.escale > 0) || !(std::fabs(P.dcp) <= 1e6)) {
         put_err(err, err_len, "invalid parameter point (same rules as osc_set_params)");
         return OSC_E_RANGE;
     }

@@ -109,6 +109,8 @@ osc_status validate_point(osc_ctx *c, const osc_point &p, int i) {
     if (!(p.s2_23 >= 0.0 && p.s2_23 <= 1.0)) return fail(c, OSC_E_RANGE, o.str() + "sin^2 theta23 must be in [0, 1]");
     if (!(p.dm21 > 0.0)) return fail(c, OSC_E_RANGE, o.str() + "dm21 must be > 0");
     if (!(std::fabs(p.dm32) > p.dm21)) return fail(c, OSC_E_RANGE, o.str() + "|dm32| must exceed dm21");
+    // the device reduces delta by pi/2 exactly only for |delta| below about 1.6e6
+    if (!(std::fabs(p.dcp) <= 1e6)) return fail(c, OSC_E_RANGE, o.str() + "|delta_CP| must be <= 1e6 rad");
     if (!(p.escale > 0.0)) return fail(c, OSC_E_RANGE, o.str() + "escale must be > 0");
     return OSC_OK;
 }

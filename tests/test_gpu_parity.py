@@ -77,6 +77,26 @@ def test_all_channels_random_points(ctx, L, rho):
     api.osc_unload_sample(ctx, sid)
 
 
+def test_delta_in_every_quadrant(ctx):
+    """The constants kernel reduces delta_CP by pi/2 and sums Taylor series for
+    its sine and cosine; phases on the quadrant edges, past 2 pi and far from the
+    origin (up to the ABI limit of 1e6 rad) must match the oracle's libm values."""
+    s = synth.all_channel_sample(20000, seed=1300, L_km=1300.0, rho=2.85, e_hi=40.0)
+    sid = api.osc_load_sample(ctx, s)
+    deltas = [0.0, np.pi / 2, np.pi, -np.pi, -np.pi / 2, 1.5 * np.pi, 2 * np.pi, 0.1 - 2 * np.pi, 7.0, -20.3,
+              1e5 + 0.3, -9.99e5]
+    pts = np.tile(synth.table1_point(), (len(deltas), 1))
+    pts[:, 5] = deltas
+    api.osc_set_params(ctx, pts)
+    for k, d in enumerate(deltas):
+        po, _ = oracle.reweight(s, oracle.point_from_row(pts[k]))
+        p64, _ = _gpu_probs(ctx, sid, k, "fp64", s["n"])
+        p32, _ = _gpu_probs(ctx, sid, k, "fp32", s["n"])
+        assert np.max(np.abs(p64 - po)) <= TOL_FP64, (d, np.max(np.abs(p64 - po)))
+        assert np.max(np.abs(p32 - po)) <= TOL_FP32, (d, np.max(np.abs(p32 - po)))
+    api.osc_unload_sample(ctx, sid)
+
+
 def test_validation_residual_10M(ctx, golden_dir):
     """Sec. 2.2: 10 million energies uniform in (0.05, 30] GeV, Table 1 point:
     FP64 GPU vs CPU residual within 1e-12."""
@@ -211,7 +231,7 @@ def test_invalid_input_rejected_before_launch(ctx):
     bad["flav_out"][3] = 3
     with pytest.raises(api.OscError):
         api.osc_load_sample(ctx, bad)
-    for field, val in ((1, 0.0), (3, 0.0), (4, 5e-5), (6, 0.0), (0, float("nan"))):
+    for field, val in ((1, 0.0), (3, 0.0), (4, 5e-5), (6, 0.0), (0, float("nan")), (5, 2e6)):
         row = synth.table1_point().copy()
         row[field] = val
         with pytest.raises(api.OscError) as e:
