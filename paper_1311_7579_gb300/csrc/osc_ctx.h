@@ -45,10 +45,7 @@ struct Plan {
     WorkItem *d_items = nullptr;
     SampleDev *d_samples = nullptr;
     double *d_hmeta = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t n_hist_node = nullptr, n_final_node = nullptr;
-    // the same step with event-record nodes around each kernel (timing mode)
+    // timing mode: the step as a CUDA graph with event-record nodes around each kernel
     cudaGraph_t graph_t = nullptr;
     cudaGraphExec_t exec_t = nullptr;
     cudaGraphNode_t t_hist_node = nullptr, t_final_node = nullptr, t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -137,7 +134,7 @@ osc_status debug_word_check(osc_ctx *c);
 osc_status ensure_acc(osc_ctx *c, int64_t bins);
 // grid of the persistent histogram kernel; finalize fusion rule
 int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items);
-bool fuse_finalize(int64_t n_hist, int32_t nbins);
+bool fuse_finalize(int64_t n_hist, int32_t nbins, int32_t pt);
 int prec_kind(osc_precision p);
 cudaEvent_t pool_event(osc_ctx *c);
 osc_status drain_timing(osc_ctx *c);

@@ -345,22 +345,32 @@ __device__ __forceinline__ void fx_flush(unsigned long long *p, unsigned long lo
     if (d2) atomicAdd(p + 2, (unsigned long long)d2);
 }
 
-// Value of bin i: the three digit columns depend on how runs were split into
+// Value of a bin: the three digit columns depend on how runs were split into
 // flushes; their combination, the exact 128-bit sum, does not, and only that
-// is converted (times 2^-F and the point's norm).
-__device__ __forceinline__ double final_bin(unsigned long long d0, unsigned long long d1, unsigned long long d2,
-                                            const double *m, const double *pc64) {
+// is converted: (hi 2^64 + lo) 2^-F times the point's norm, with m0 = 2^(64-F)
+// and m1 = 2^-F (both products exact, so the result does not depend on how the
+// sum is contracted).
+__device__ __forceinline__ double bin_value(unsigned long long d0, unsigned long long d1, unsigned long long d2,
+                                            double m0, double m1, double norm) {
     const unsigned __int128 v = (unsigned __int128)d0 + ((unsigned __int128)d1 << 40) +
                                 ((unsigned __int128)(__int128)(long long)d2 << 80);
     const long long hi = (long long)(unsigned long long)(v >> 64);
     const unsigned long long lo = (unsigned long long)v;
-    const double x = (double)hi * m[0] + (double)lo * m[1];
-    return x * pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM];
+    return ((double)hi * m0 + (double)lo * m1) * norm;
+}
+// m: the histogram's (2^(64-F), 2^-F, unused, point index)
+__device__ __forceinline__ double final_bin(unsigned long long d0, unsigned long long d1, unsigned long long d2,
+                                            const double *m, const double *pc64) {
+    return bin_value(d0, d1, d2, m[0], m[1], pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM]);
 }
 
-// Small outputs: the last block of the histogram kernel to finish converts the
-// bins (instead of a separate finalize launch).  Every thread fences its own
-// flushes before the block takes its completion ticket.
+// Small outputs (one conversion round: up to 256 bins for a block, 128 for a
+// warp; larger outputs go to the finalize kernel, launched programmatically):
+// the last block or warp of the histogram kernel to finish converts the bins
+// instead of a separate launch.  Every thread fences its own flushes before its
+// block or warp takes its completion ticket.  The last one runs alone at the
+// end of the grid, so it issues the loads of all its bins (digit columns and
+// histogram scales, then the points' norms) before it converts any of them.
 __device__ __forceinline__ void fused_final(const HistParams &prm) {
     __shared__ int s_last;
     __threadfence();
@@ -373,10 +383,13 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long d0 = __ldcg(prm.acc + 3 * i), d1 = __ldcg(prm.acc + 3 * i + 1),
                                  d2 = __ldcg(prm.acc + 3 * i + 2);
+        const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
+        const double m0 = m[0], m1 = m[1];
+        const double nm = prm.pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM];
         prm.acc[3 * i] = 0ull;
         prm.acc[3 * i + 1] = 0ull;
         prm.acc[3 * i + 2] = 0ull;
-        prm.fin_out[i] = final_bin(d0, d1, d2, prm.fin_hmeta + 4 * (i / prm.nbins), prm.pc64);
+        prm.fin_out[i] = bin_value(d0, d1, d2, m0, m1, nm);
     }
     if (threadIdx.x == 0) {
         prm.counter[0] = 0;
@@ -384,9 +397,8 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
     }
 }
 
-// Per-warp variant for one-point items: every warp fences its lanes' flushes and
-// takes a completion ticket; the last warp of the grid converts the bins, so
-// warps that finish early exit without waiting at a block barrier.
+// Per-warp variant for one-point items: warps that finish early exit without
+// waiting at a block barrier; the last warp converts four bins per lane per round.
 __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     const int lane = threadIdx.x & 31;
     __threadfence();
@@ -396,14 +408,39 @@ __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
+    constexpr int kU = 4;
     const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
-    for (int64_t i = lane; i < n; i += 32) {
-        const unsigned long long d0 = __ldcg(prm.acc + 3 * i), d1 = __ldcg(prm.acc + 3 * i + 1),
-                                 d2 = __ldcg(prm.acc + 3 * i + 2);
-        prm.acc[3 * i] = 0ull;
-        prm.acc[3 * i + 1] = 0ull;
-        prm.acc[3 * i + 2] = 0ull;
-        prm.fin_out[i] = final_bin(d0, d1, d2, prm.fin_hmeta + 4 * (i / prm.nbins), prm.pc64);
+    for (int64_t i0 = 0; i0 < n; i0 += 32 * kU) {
+        unsigned long long d[kU][3];
+        double m0[kU], m1[kU], nm[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t i = i0 + lane + 32 * k;
+            d[k][0] = d[k][1] = d[k][2] = 0ull;
+            m0[k] = m1[k] = nm[k] = 0.0;
+            if (i < n) {
+                d[k][0] = __ldcg(prm.acc + 3 * i);
+                d[k][1] = __ldcg(prm.acc + 3 * i + 1);
+                d[k][2] = __ldcg(prm.acc + 3 * i + 2);
+                const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
+                m0[k] = m[0];
+                m1[k] = m[1];
+                nm[k] = m[3];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (i0 + lane + 32 * k < n) nm[k] = prm.pc64[(int64_t)nm[k] * C64_STRIDE + C64_NORM];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t i = i0 + lane + 32 * k;
+            if (i < n) {
+                prm.acc[3 * i] = 0ull;
+                prm.acc[3 * i + 1] = 0ull;
+                prm.acc[3 * i + 2] = 0ull;
+                prm.fin_out[i] = bin_value(d[k][0], d[k][1], d[k][2], m0[k], m1[k], nm[k]);
+            }
+        }
     }
     if (lane == 0) {
         prm.counter[0] = 0;
@@ -754,6 +791,9 @@ constexpr int hist_min_blocks() {
 
 template <int PREC, int PT>
 __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(const HistParams prm) {
+    // a finalize kernel after this one (programmatic launch) may become resident
+    // as blocks of this grid retire; it waits for the whole grid
+    grid_dependents_launch();
     if constexpr (PT == 1) {
         hist_items_per_warp<PREC>(prm);
         if (prm.fuse_final) fused_final_warp(prm);

@@ -37,6 +37,7 @@ __device__ __forceinline__ void load_lay_point(LayPoint<PREC> &lp, const float *
 
 template <int PREC>
 __global__ void __launch_bounds__(kNT) k_hist_layers(const HistParams prm) {
+    grid_dependents_launch();  // lets a finalize kernel after it (programmatic launch) become resident early
     const int lane = threadIdx.x & 31;
     int it = 0;
     if (lane == 0) it = atomicAdd(prm.counter, 1);

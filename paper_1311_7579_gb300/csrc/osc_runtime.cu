@@ -222,8 +222,12 @@ static double *pinned_device_ptr(double *host) {
     return (a.type == cudaMemoryTypeHost && a.devicePointer) ? (double *)a.devicePointer : nullptr;
 }
 
-// Outputs this small are converted by the histogram kernel's last block.
-bool fuse_finalize(int64_t n_hist, int32_t nbins) { return n_hist * (int64_t)nbins <= 4096; }
+// Outputs of one conversion round are converted by the histogram kernel's last
+// warp (one-point items: 128 bins) or block (point tiles: 256 bins); larger ones
+// by the finalize kernel, whose blocks convert in parallel.
+bool fuse_finalize(int64_t n_hist, int32_t nbins, int32_t pt) {
+    return n_hist * (int64_t)nbins <= (pt == 1 ? 128 : 256);
+}
 
 cudaEvent_t pool_event(osc_ctx *c) {
     if (!c->ev_pool.empty()) {
@@ -318,8 +322,6 @@ static void free_sample(osc_ctx *c, Sample *s) {
 }
 
 static void free_plan(osc_ctx *c, Plan *p) {
-    if (p->exec) cudaGraphExecDestroy(p->exec);
-    if (p->graph) cudaGraphDestroy(p->graph);
     if (p->exec_t) cudaGraphExecDestroy(p->exec_t);
     if (p->graph_t) cudaGraphDestroy(p->graph_t);
     dfree(c, p->d_items);
@@ -905,7 +907,9 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     return OSC_OK;
 }
 
-// Two-node CUDA graph (histogram kernel -> finalize kernel), parameters refreshed per call.
+// Histogram kernel, then (outputs of more than one conversion round) the
+// finalize kernel.  Timing mode runs them as a CUDA graph with event-record
+// nodes around each kernel, parameters refreshed per call.
 static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *d_out) {
     HistParams hp;
     fill_hist_params(hp, p->d_items, p->n_items, p->d_samples, ctx->d_pc32, ctx->d_pc64, ctx->d_acc, ctx->d_counter,
@@ -925,17 +929,20 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     kf.gridDim = dim3((unsigned)fb);
     kf.blockDim = dim3(256);
     kf.kernelParams = fargs;
-    const bool fused = fuse_finalize(p->n_hist, p->nbins);
+    const bool fused = fuse_finalize(p->n_hist, p->nbins, p->pt);
     if (fused) {
         hp.fuse_final = 1;
         hp.fin_n_hist = p->n_hist;
         hp.fin_hmeta = p->d_hmeta;
         hp.fin_out = d_out;
     }
-    if (!ctx->timing && fused && p->kind == kEventByEvent) {
-        // one kernel: a direct launch with programmatic stream serialization, so
-        // that it starts (and fetches its first work) while the constants
-        // kernel before it in the stream is still running
+    if (!ctx->timing) {
+        // Direct launches.  The event-by-event histogram kernel goes with
+        // programmatic stream serialization: it starts (and fetches its first
+        // work) while the constants kernel before it is still running, and waits
+        // in griddepcontrol.wait before it reads the constants.  The finalize
+        // kernel goes the same way after it: its blocks become resident as the
+        // histogram blocks retire and convert as soon as that grid completes.
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[0].val.programmaticStreamSerializationAllowed = 1;
@@ -945,19 +952,9 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
         cfg.dynamicSmemBytes = 0;
         cfg.stream = ctx->stream;
         cfg.attrs = at;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = p->kind == kEventByEvent ? 1 : 0;
         CK(cudaLaunchKernelExC(&cfg, kh.func, hargs));
-    } else if (!ctx->timing) {
-        if (!p->exec) {
-            CK(cudaGraphCreate(&p->graph, 0));
-            CK(cudaGraphAddKernelNode(&p->n_hist_node, p->graph, nullptr, 0, &kh));
-            if (!fused) CK(cudaGraphAddKernelNode(&p->n_final_node, p->graph, &p->n_hist_node, 1, &kf));
-            CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
-        } else {
-            CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_hist_node, &kh));
-            if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec, p->n_final_node, &kf));
-        }
-        CK(cudaGraphLaunch(p->exec, ctx->stream));
+        if (!fused) CK(launch_final_programmatic(fp, ctx->stream));
     } else {
         // timing mode: the same graph with event-record nodes around each kernel,
         // fresh events swapped in per launch (read later without blocking the stream)

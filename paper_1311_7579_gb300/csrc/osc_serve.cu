@@ -202,7 +202,7 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     hp.lo_f = (float)sv->lo;
     hp.inv_f = (float)((double)sv->nbins / (sv->hi - sv->lo));
     hp.nb_f = (float)sv->nbins;
-    const bool fused = fuse_finalize(n, sv->nbins);
+    const bool fused = fuse_finalize(n, sv->nbins, 1);
     hp.fuse_final = fused ? 1 : 0;
     hp.fin_n_hist = n;
     hp.fin_hmeta = b.d_hmeta;
@@ -229,7 +229,7 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
         ++kernels;
     }
     FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
-    if (!e && !fused) e = launch_final(fp, st);
+    if (!e && !fused) e = launch_final_programmatic(fp, st);
     if (!e) e = cudaLaunchHostFunc(st, on_batch_done, cb_arg);
     if (e) return fail_cuda(ctx, e, "serving batch launch");
     ctx->launches += 1 + kernels + (fused ? 0 : 1);
