@@ -58,6 +58,8 @@ _lib = None
 def lib():
     """Build (if stale) and load the CUDA library; raises if that is impossible."""
     global _lib
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is None:
             _lib = load_library(_build.build())
@@ -109,13 +111,30 @@ def _check(ctx, status):
         raise OscError(status, msg.decode() if msg else "")
 
 
+def _addr(a):
+    """Data address of a numpy array.  A ctypes view of a writable contiguous
+    buffer is cheaper to make than ``a.ctypes``; other arrays use the latter."""
+    try:
+        return ctypes.addressof(ctypes.c_char.from_buffer(a))
+    except (TypeError, ValueError, BufferError):
+        return a.ctypes.data
+
+
 def _ptr(a):
     """Address of a numpy array or torch tensor (None -> NULL)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        return a.ctypes.data
+        return _addr(a)
     return a.data_ptr()
+
+
+def _ids(sample_ids):
+    """Sample ids as a C int32 array and its length."""
+    if type(sample_ids) in (list, tuple):
+        return (ctypes.c_int32 * len(sample_ids))(*[int(i) for i in sample_ids]), len(sample_ids)
+    a = np.ascontiguousarray(np.atleast_1d(sample_ids), dtype=np.int32)
+    return (ctypes.c_int32 * a.size).from_buffer_copy(a), a.size
 
 
 def _is_device(a):
@@ -123,6 +142,11 @@ def _is_device(a):
 
 
 def _points(points):
+    if (type(points) is np.ndarray and points.dtype == np.float64 and points.ndim in (1, 2) and points.shape[-1] == 8
+            and points.size > 0 and points.flags.c_contiguous and points.flags.writeable):
+        # a view of the caller's rows (read during the call)
+        n = points.size // 8
+        return (OscPoint * n).from_buffer(points), n
     rows = np.ascontiguousarray(np.atleast_2d(np.asarray(points, dtype=np.float64)))
     if rows.shape[1] != 8:
         raise ValueError("points must have 8 columns: s2_12 s2_13 s2_23 dm21 dm32 dcp escale norm")
@@ -190,13 +214,12 @@ def osc_reweight(ctx, sample_id, point, prec, out_prob=None, out_weight=None):
 
 def osc_histogram(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, out=None):
     """out: numpy (n_samples, n_points, nbins) float64 (allocated if None) or a torch CUDA tensor."""
-    ids = np.ascontiguousarray(np.atleast_1d(sample_ids), dtype=np.int32)
+    ids, n_ids = _ids(sample_ids)
     if out is None:
-        out = np.zeros((ids.size, int(n_points), int(nbins)))
+        out = np.zeros((n_ids, int(n_points), int(nbins)))
     dev = _is_device(out)
-    _check(ctx, lib().osc_histogram(ctx, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size,
-                                    int(point_begin), int(n_points), PRECISIONS[prec], float(lo), float(hi),
-                                    int(nbins), _ptr(out), 1 if dev else 0))
+    _check(ctx, lib().osc_histogram(ctx, ids, n_ids, int(point_begin), int(n_points), PRECISIONS[prec], float(lo),
+                                    float(hi), int(nbins), _ptr(out), 1 if dev else 0))
     return out
 
 
@@ -204,11 +227,11 @@ def osc_histogram_bin_centre(ctx, sample_ids, point_begin, n_points, prec, t_lo,
                              out=None):
     """Binned-method histograms (probability at the centre of each event's
     true-energy bin); out as for osc_histogram."""
-    ids = np.ascontiguousarray(np.atleast_1d(sample_ids), dtype=np.int32)
+    ids, n_ids = _ids(sample_ids)
     if out is None:
-        out = np.zeros((ids.size, int(n_points), int(nbins)))
+        out = np.zeros((n_ids, int(n_points), int(nbins)))
     dev = _is_device(out)
-    _check(ctx, lib().osc_histogram_bin_centre(ctx, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ids.size,
+    _check(ctx, lib().osc_histogram_bin_centre(ctx, ids, n_ids,
                                                int(point_begin), int(n_points), PRECISIONS[prec], float(t_lo),
                                                float(t_hi), int(t_nbins), float(lo), float(hi), int(nbins),
                                                _ptr(out), 1 if dev else 0))
@@ -277,7 +300,7 @@ def osc_wait(ctx, ticket, nbins, timeout_ms=-1, out=None):
     if out is None:
         out = np.zeros(int(nbins))
     lat = ctypes.c_double()
-    _check(ctx, lib().osc_wait(ctx, int(ticket), out.ctypes.data, int(timeout_ms), ctypes.byref(lat)))
+    _check(ctx, lib().osc_wait(ctx, int(ticket), _addr(out), int(timeout_ms), ctypes.byref(lat)))
     return out, lat.value
 
 

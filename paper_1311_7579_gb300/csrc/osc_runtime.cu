@@ -788,10 +788,11 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
 static std::string tune_key(const std::vector<int32_t> &ids, int32_t n_points, int prec, osc_ctx *ctx) {
     int64_t ev = 0;
     for (int32_t id : ids) ev += ctx->samples[id]->n;
-    std::ostringstream o;
     // workload class: precision, point count (log2 bucket), event count (log2 bucket)
-    o << prec << ":" << (int)std::ceil(std::log2((double)n_points + 0.5)) << ":" << (int)std::ceil(std::log2((double)ev + 1));
-    return o.str();
+    char k[64];
+    std::snprintf(k, sizeof k, "%d:%d:%d", prec, (int)std::ceil(std::log2((double)n_points + 0.5)),
+                  (int)std::ceil(std::log2((double)ev + 1)));
+    return k;
 }
 
 static int32_t default_pt(int32_t n_points) {
