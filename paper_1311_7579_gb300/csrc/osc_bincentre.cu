@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBcTableThreads) k_bc_table(const BcParams b) 
             Ch64 h;
             load_ch64(pc, ch, h);
             const double Ad = sd.kA_rhoye * (double)E;
-            b.tabq[idx] = prob_fixed(prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E));
+            b.tabq[idx] = prob_fixed(prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, tau64(sd.cLL, E)));
         }
     }
 }

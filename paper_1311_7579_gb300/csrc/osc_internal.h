@@ -42,7 +42,9 @@ enum PC64 : int {
     C64_CH = 16,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
     C64_LU = 72,                                 // U[f][l] (re, im) as in the FP32 block
     C64_LD = 90,                                 // sorted vacuum eigenvalues d0 <= d1 <= d2
-    C64_STRIDE = 96                              // doubles, 768 B
+    C64_SH = 96,                                 // shifted-cubic constants S, PI, W, E of sorted roots 0, 1
+    C64_VG = 104,                                // vacuum gaps d1 - d0, d2 - d0, d1 - d2
+    C64_STRIDE = 112                             // doubles, 896 B
 };
 
 // ---- resident sample as seen by a kernel ----------------------------------

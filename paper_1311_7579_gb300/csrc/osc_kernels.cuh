@@ -169,14 +169,20 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
         const double zl = lane ? z1 : z0, zj = lane ? z2 : z1, zk = lane ? z0 : z2;
         const double aj = dl - dj, ak = dl - dk;
         const int o = lane ? (C32_S1 - C32_S0) : 0;
-        c32[C32_S0 + o] = (float)(aj + ak);
-        c32[C32_PI0 + o] = (float)(aj * ak);
-        c32[C32_W0 + o] = (float)(zl * (aj + ak) + zj * ak + zk * aj);
-        c32[C32_E0 + o] = (float)(zl * aj * ak);
+        const double S = aj + ak, PI = aj * ak, W = zl * (aj + ak) + zj * ak + zk * aj, E = zl * aj * ak;
+        c32[C32_S0 + o] = (float)S;
+        c32[C32_PI0 + o] = (float)PI;
+        c32[C32_W0 + o] = (float)W;
+        c32[C32_E0 + o] = (float)E;
+        c64[C64_SH + 4 * lane] = S;
+        c64[C64_SH + 4 * lane + 1] = PI;
+        c64[C64_SH + 4 * lane + 2] = W;
+        c64[C64_SH + 4 * lane + 3] = E;
     }
     if (warp == 3 && lane == 0) {
         c32[C32_D0] = (float)d0; c32[C32_D1] = (float)d1; c32[C32_D2] = (float)d2;
         c64[C64_LD] = d0; c64[C64_LD + 1] = d1; c64[C64_LD + 2] = d2;
+        c64[C64_VG] = d1 - d0; c64[C64_VG + 1] = d2 - d0; c64[C64_VG + 2] = d1 - d2;
         c32[C32_G01] = (float)(d0 - d1); c32[C32_G02] = (float)(d0 - d2); c32[C32_G12] = (float)(d1 - d2);
         split_ff(d1 - d0, &c32[C32_V1H], &c32[C32_V1L]);
         split_ff(d2 - d0, &c32[C32_V2H], &c32[C32_V2L]);
@@ -285,6 +291,10 @@ __device__ __forceinline__ void load_ch32(const float *__restrict__ c, int ch, C
 __device__ __forceinline__ void load_pt64(const double *__restrict__ c, Pt64 &o) {
     o.p0 = c[C64_P0]; o.p1 = c[C64_P1]; o.q0 = c[C64_Q0]; o.q1 = c[C64_Q1]; o.q2 = c[C64_Q2];
     o.T0 = c[C64_T0]; o.c10 = c[C64_C10]; o.smt = c[C64_SMT];
+    o.S0 = c[C64_SH]; o.PI0 = c[C64_SH + 1]; o.W0 = c[C64_SH + 2]; o.E0 = c[C64_SH + 3];
+    o.S1 = c[C64_SH + 4]; o.PI1 = c[C64_SH + 5]; o.W1 = c[C64_SH + 6]; o.E1 = c[C64_SH + 7];
+    o.d0 = c[C64_LD]; o.d1 = c[C64_LD + 1]; o.d2 = c[C64_LD + 2];
+    o.V1 = c[C64_VG]; o.V2 = c[C64_VG + 1]; o.G12 = c[C64_VG + 2];
 }
 __device__ __forceinline__ void load_ch64(const double *__restrict__ c, int ch, Ch64 &o) {
     const int nubar = ch >= 9;
@@ -533,7 +543,8 @@ struct Stage32 {
 };
 struct Stage64 {
     double a[kET];
-    double tau[kET];
+    double tau[kET];     // c_L L / E as hi + lo (the FP32-amplitude variant uses hi only)
+    double tau_lo[kET];
     float2 ew[kET];  // (e_reco, w_mc)
     int ch[kET];
 };
@@ -548,7 +559,9 @@ __device__ __forceinline__ void stage_one32(Stage32 &s, int j, const SampleDev &
 __device__ __forceinline__ void stage_one64(Stage64 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
     const double Ad = sd.kA_rhoye * (double)E;
     s.a[j] = (ch >= 9) ? -Ad : Ad;
-    s.tau[j] = sd.cLL / (double)E;
+    const Tau64 t = tau64(sd.cLL, E);
+    s.tau[j] = t.hi;
+    s.tau_lo[j] = t.lo;
     s.ew[j] = make_float2(er, w);
     s.ch[j] = ch;
 }
@@ -753,7 +766,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                         load_ch64(pc64, ch, h64);
                     }
                     const double Ad = sd.kA_rhoye * (double)E;
-                    const double P = prob_fp64(c64, h64, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+                    const double P = prob_fp64(c64, h64, (ch >= 9) ? -Ad : Ad, tau64(sd.cLL, E));
                     acc_event_f64(r, accp, prm, sf, er, P * (double)w, hs, true);
                 }
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
@@ -907,7 +920,7 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                             cur_ch = ch;
                             load_ch64(pc, ch, h);
                         }
-                        const double P = prob_fp64(c, h, s.a[j], s.tau[j]);
+                        const double P = prob_fp64(c, h, s.a[j], Tau64{s.tau[j], s.tau_lo[j]});
                         const float2 ew = s.ew[j];
                         acc_event_f64(r, accp, prm, sf, ew.x, P * (double)ew.y, hs, active);
                     }
@@ -986,7 +999,7 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
                 load_ch64(pc, ch, h);
             }
             const double Ad = sd.kA_rhoye * (double)E;
-            const double P = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, sd.cLL / (double)E);
+            const double P = prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, tau64(sd.cLL, E));
             const double w = P * (double)q.z;
             const int32_t o = sd.perm[i];
             if (r.out_prob) r.out_prob[o] = P;

@@ -43,7 +43,7 @@ __device__ __forceinline__ float rcp_t<float>(float x) {
 }
 template <>
 __device__ __forceinline__ double rcp_t<double>(double x) {
-    return 1.0 / x;
+    return rcp64(x);
 }
 
 // One layer: psi <- psi + sum_{l=1,2} (e^{-i phi_l} - 1) P_l psi (phases relative
@@ -174,16 +174,19 @@ __device__ __forceinline__ double prob_layers64(const Pt64 &c, const double *d, 
     double pr[3], pi[3];
     layer_init(pr, pi, u, ab / 3);
     const double Ed = (double)E;
+    const double iE = rcp64(Ed);
     for (int k = 0; k < sd.n_layers; ++k) {
         const double2 ly = layer64(sd, k);
         const double A = nubar ? -(ly.x * Ed) : ly.x * Ed;
-        double m0, m1, m2, t3;
-        roots64(c, A, m0, m1, m2, t3);
-        const double dl1 = (m1 + t3) - d[1], dl2 = (m2 + t3) - d[2];
-        const double htau = 0.5 * ly.y / Ed;
+        double dl0, dl1, dl2;
+        shifts64(c, A, dl0, dl1, dl2);
+        // half phases c_L L (lambda_l - lambda_0) / (2 E)
+        Tau64 ht = tau64(ly.y, Ed, iE);
+        ht.hi *= 0.5;
+        ht.lo *= 0.5;
         double s1, k1, s2, k2;
-        sincos(htau * (m1 - m0), &s1, &k1);
-        sincos(htau * (m2 - m0), &s2, &k2);
+        sincos_gap64(ht, c.V1, dl1 - dl0, &s1, &k1);
+        sincos_gap64(ht, c.V2, dl2 - dl0, &s2, &k2);
         layer_update<double>(pr, pi, u, d[0] - d[1], d[0] - d[2], d[1] - d[2], dl1, dl2, s1, k1, s2, k2);
     }
     return layer_prob(pr, pi, u, ab % 3);

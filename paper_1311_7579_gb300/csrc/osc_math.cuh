@@ -13,8 +13,8 @@
 // (M^2)_{beta alpha}:  N_l = (M^2)_ba - sigma_l M_ba + pi_l delta_ba with
 // sigma_l = lambda_j + lambda_k and pi_l = lambda_j lambda_k.
 //
-// FP64 path: the depressed cubic is solved by Viete's trigonometric form,
-// polished by one Newton step, and everything else is FP64.
+// FP64 path: the matter shifts are refined by FP64 Newton steps on the shifted
+// cubics from the FP32 trigonometric seed, and everything else is FP64.
 //
 // FP32 path (GB300 has ~1/64 of its FP32 rate in FP64): each eigenvalue is
 // written as its vacuum value plus a matter shift, lambda_l = d_l + delta_l.
@@ -104,11 +104,9 @@ __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float v
     return fr + fmaf(th, dd, e1 + e2);
 }
 
-// Trigonometric FP32 seed of the two lower sorted roots of the characteristic
-// cubic, as roots mu of the depressed cubic (lambda = mu + (T0 + A) / 3).
-__device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3) {
-    const float p = fmaf(fmaf(A, -1.0f / 3.0f, c.p1), A, c.p0);
-    const float q = fmaf(fmaf(fmaf(A, -2.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
+// Trigonometric FP32 seed of the two lower roots m0 <= m1 of the depressed
+// cubic mu^3 + p mu + q (Viete's form with the arccos and cube-angle above).
+__device__ __forceinline__ void seed_depressed32(float p, float q, float &m0, float &m1) {
     const float mp3 = fmaxf(p * (-1.0f / 3.0f), 1e-30f);
     const float ir = rsqrt_approx(mp3);
     const float r = mp3 * ir;
@@ -118,9 +116,17 @@ __device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, 
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;
-    t3 = (c.T0 + A) * (1.0f / 3.0f);
     m0 = -rc - rsn;  // smallest root
     m1 = -rc + rsn;  // middle root
+}
+
+// The same seed for the characteristic cubic of one event, as roots mu of the
+// depressed cubic (lambda = mu + (T0 + A) / 3).
+__device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3) {
+    const float p = fmaf(fmaf(A, -1.0f / 3.0f, c.p1), A, c.p0);
+    const float q = fmaf(fmaf(fmaf(A, -2.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
+    seed_depressed32(p, q, m0, m1);
+    t3 = (c.T0 + A) * (1.0f / 3.0f);
 }
 
 // |S_ba|^2 from the eigenvalues L1, L2 (FP32), the gaps g_ij = L_i - L_j and the
@@ -179,59 +185,161 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
 }
 
 // ------------------------------------------------------------------ FP64 path
+// This GPU's FP64 pipe issues one warp instruction per several tens of cycles
+// per scheduler, so the FP64 path is bound by its count of FP64 instructions
+// and is written to keep that count low: the eigenvalues' matter shifts by FP64
+// Newton steps from the FP32 trigonometric seed, reciprocals by Newton-Raphson from the
+// approximate PTX reciprocal, sine and cosine of exactly formed phases by
+// Cody-Waite reduction and Taylor series, and no Sylvester coefficient for root 0.
 struct Pt64 {
     double p0, p1, q0, q1, q2, T0, c10, smt;
+    double S0, PI0, W0, E0, S1, PI1, W1, E1;  // shifted cubics of sorted roots 0, 1
+    double d0, d1, d2;                        // sorted vacuum eigenvalues
+    double V1, V2, G12;                       // d1 - d0, d2 - d0, d1 - d2
 };
 struct Ch64 {
     double Xr, Xi, Yr, Yi, Zr, Zi, ee, diag;
 };
 
-// Ascending roots m0 <= m1 <= m2 of the depressed characteristic cubic
-// mu^3 + p mu + q (lambda = mu + t3, t3 = (T0 + A) / 3): Viete's trigonometric
-// form, each root polished by one Newton step.
-__device__ __forceinline__ void roots64(const Pt64 &c, double A, double &m0, double &m1, double &m2, double &t3) {
-    const double p = fma(fma(A, -1.0 / 3.0, c.p1), A, c.p0);
-    const double q = fma(fma(fma(A, -2.0 / 27.0, c.q2), A, c.q1), A, c.q0);
-    const double mp3 = fmax(-p / 3.0, 1e-300);
-    const double r = sqrt(mp3);
-    double cth = (-0.5 * q) / (mp3 * r);
-    cth = fmin(fmax(cth, -1.0), 1.0);
-    const double th3 = acos(cth) / 3.0;
-    double sn, cs;
-    sincos(th3, &sn, &cs);
-    const double rc = r * cs, rsn = r * sn * 1.7320508075688772935;
-    m0 = -rc - rsn;
-    m1 = -rc + rsn;
-    m2 = 2.0 * rc;
-    m0 -= fma(fma(m0, m0, p), m0, q) / fma(3.0 * m0, m0, p);
-    m1 -= fma(fma(m1, m1, p), m1, q) / fma(3.0 * m1, m1, p);
-    m2 -= fma(fma(m2, m2, p), m2, q) / fma(3.0 * m2, m2, p);
-    t3 = (c.T0 + A) / 3.0;
+// 1/x for normal x: rcp.approx.ftz.f64 (relative error about 1e-6), then two
+// Newton-Raphson steps r <- r + r (1 - x r), each squaring the relative error.
+__device__ __forceinline__ double rcp64(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
 }
 
-// P(alpha -> beta); A signed matter term [eV^2], tau = c_L L / E_true.
-__device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double A, double tau) {
-    double m0, m1, m2, t3;
-    roots64(c, A, m0, m1, m2, t3);
-    const double L0 = m0 + t3, L1 = m1 + t3, L2 = m2 + t3;
-    const double g01 = m0 - m1, g02 = m0 - m2, g12 = m1 - m2;
-    const double iD0 = 1.0 / (g01 * g02), iD1 = -1.0 / (g01 * g12), iD2 = 1.0 / (g02 * g12);
+// c_L L / E as an unevaluated sum hi + lo (relative error about 1e-32): hi from
+// the reciprocal 1/E, lo from the exact remainder c_L L - hi E.
+struct Tau64 {
+    double hi, lo;
+};
+__device__ __forceinline__ Tau64 tau64(double cLL, double E, double iE) {
+    const double hi = cLL * iE;
+    return {hi, fma(-hi, E, cLL) * iE};
+}
+__device__ __forceinline__ Tau64 tau64(double cLL, float E) {
+    const double Ed = (double)E;
+    return tau64(cLL, Ed, rcp64(Ed));
+}
+
+// sin and cos of the phase ph + pl [rad] (pl a small correction to ph).  ph is
+// reduced by pi/2 in three parts (Cody and Waite; the first two parts have 33
+// significant bits, so k times them is exact for |k| < 2^20, i.e. phases below
+// 1.6e6 rad), and the Taylor series of sin x / x and cos x through x^16
+// (truncation below 4e-18) are evaluated on the remainder x in [-pi/4, pi/4].
+__device__ __forceinline__ void sincos_reduce64(double ph, double pl, double *sn, double *cs) {
+    const double k = rint(ph * 0.63661977236758134308);  // 2 / pi
+    double r = fma(-k, 1.5707963267341256, ph);           // pi/2, first 33 bits: exact
+    r = fma(-k, 6.077100506303966e-11, r);                 // next 33 bits
+    r = fma(-k, 2.0222662487959506e-21, r);                // remainder of pi/2
+    const double x = r + pl;
+    const double u = x * x;
+    double ps = 1.0 / 355687428096000.0;       // (-1)^j / (2j + 1)!, j = 8 .. 0
+    ps = fma(ps, u, -1.0 / 1307674368000.0);
+    ps = fma(ps, u, 1.0 / 6227020800.0);
+    ps = fma(ps, u, -1.0 / 39916800.0);
+    ps = fma(ps, u, 1.0 / 362880.0);
+    ps = fma(ps, u, -1.0 / 5040.0);
+    ps = fma(ps, u, 1.0 / 120.0);
+    ps = fma(ps, u, -1.0 / 6.0);
+    ps = fma(ps, u, 1.0);
+    double pc = 1.0 / 20922789888000.0;        // (-1)^j / (2j)!, j = 8 .. 0
+    pc = fma(pc, u, -1.0 / 87178291200.0);
+    pc = fma(pc, u, 1.0 / 479001600.0);
+    pc = fma(pc, u, -1.0 / 3628800.0);
+    pc = fma(pc, u, 1.0 / 40320.0);
+    pc = fma(pc, u, -1.0 / 720.0);
+    pc = fma(pc, u, 1.0 / 24.0);
+    pc = fma(pc, u, -0.5);
+    pc = fma(pc, u, 1.0);
+    const double s = ps * x;
+    const int iq = (int)k & 3;  // quadrant, two's complement for negative k
+    *sn = iq == 0 ? s : iq == 1 ? pc : iq == 2 ? -s : -pc;
+    *cs = iq == 0 ? pc : iq == 1 ? -s : iq == 2 ? -pc : s;
+}
+
+// sin and cos of the phase tau (V + dd), V a vacuum gap and dd a difference of
+// matter shifts: V + dd is formed as an exact sum s + se (Knuth's TwoSum) and the
+// product with tau = hi + lo as ph + pl (the rounding error of hi s by an FMA),
+// so the phase carries neither the rounding of the gap nor that of the product.
+__device__ __forceinline__ void sincos_gap64(const Tau64 &t, double V, double dd, double *sn, double *cs) {
+    const double s = V + dd;
+    const double bv = s - V;
+    const double se = (V - (s - bv)) + (dd - bv);
+    const double ph = t.hi * s;
+    const double pl = fma(t.hi, s, -ph) + fma(t.hi, se, t.lo * s);
+    sincos_reduce64(ph, pl, sn, cs);
+}
+
+// One FP64 Newton step on the shifted cubic g(delta) = delta^3 + b delta^2 +
+// c delta - e (as in shifted_newton), the correction divided in FP32: every
+// step's correction is orders of magnitude below the shift itself.
+__device__ __forceinline__ double shifted_step64(double dl, double b, double c, double e) {
+    const double t = fma(dl + b, dl, c);
+    const double g = fma(t, dl, -e);
+    const double gp = fma(dl, fma(2.0, dl, b), t);
+    return dl - (double)((float)g * rcp_approx((float)gp));
+}
+
+// Matter shifts delta_l = lambda_l - d_l of the sorted eigenvalues in FP64.  The
+// FP32 trigonometric seed of the depressed cubic (from p and q rounded to FP32)
+// gives each lower eigenvalue to about 1e-10 eV^2; two FP64 Newton steps on that
+// root's shifted cubic refine its shift.  The shifted cubic's coefficients
+// carry rounding relative to the shift, not to the vacuum eigenvalue, so a small
+// matter shift keeps its relative accuracy (the depressed cubic's p alone,
+// rounded at ~1e-22 eV^4, would move the roots by ~1e-18 eV^2, 1e-12 rad at
+// c_L L / E = 6e5).  The top shift follows from the trace: the shifts sum to A.
+__device__ __forceinline__ void shifts64(const Pt64 &c, double A, double &dl0, double &dl1, double &dl2) {
+    const double p = fma(fma(A, -1.0 / 3.0, c.p1), A, c.p0);
+    const double q = fma(fma(fma(A, -2.0 / 27.0, c.q2), A, c.q1), A, c.q0);
+    float s0, s1;
+    seed_depressed32((float)p, (float)q, s0, s1);
+    const double t3 = (c.T0 + A) * (1.0 / 3.0);
+    dl0 = ((double)s0 + t3) - c.d0;
+    dl1 = ((double)s1 + t3) - c.d1;
+    const double b0 = c.S0 - A, b1 = c.S1 - A;
+    const double cc0 = fma(-A, c.W0, c.PI0), cc1 = fma(-A, c.W1, c.PI1);
+    const double e0 = A * c.E0, e1 = A * c.E1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        dl0 = shifted_step64(dl0, b0, cc0, e0);
+        dl1 = shifted_step64(dl1, b1, cc1, e1);
+    }
+    dl2 = A - dl0 - dl1;
+}
+
+// P(alpha -> beta); A signed matter term [eV^2], tau = c_L L / E_true.  The
+// projectors sum to the identity, so S = delta_ba + sum_{l=1,2} C_l (e^{-i phi_l} - 1)
+// with phi_l = tau (lambda_l - lambda_0) and C_l = N_l / D_l, D_1 = -g01 g12,
+// D_2 = g02 g12 (g_ij = lambda_i - lambda_j, vacuum gap plus shift difference),
+// both from one reciprocal.
+__device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double A, const Tau64 &tau) {
+    double dl0, dl1, dl2;
+    shifts64(c, A, dl0, dl1, dl2);
+    const double L1 = c.d1 + dl1, L2 = c.d2 + dl2;
+    const double g01 = (dl0 - dl1) - c.V1, g02 = (dl0 - dl2) - c.V2, g12 = c.G12 + (dl1 - dl2);
+    const double inv = rcp64(g01 * g02 * g12);
+    const double iD1 = -g02 * inv, iD2 = g01 * inv;
     const double TA = c.T0 + A;
     const double c1 = fma(A, c.smt, c.c10);
     const double Kr = fma(A, fma(A, h.ee, h.Zr), h.Yr), Ki = fma(A, h.Zi, h.Yi);
     const double Gr = fma(A, h.ee, h.Xr), Gi = h.Xi;
     double sg, pp;
-    sg = TA - L0; pp = c1 - L0 * sg;
-    const double C0r = (Kr - sg * Gr + pp * h.diag) * iD0, C0i = (Ki - sg * Gi) * iD0;
     sg = TA - L1; pp = c1 - L1 * sg;
     const double C1r = (Kr - sg * Gr + pp * h.diag) * iD1, C1i = (Ki - sg * Gi) * iD1;
     sg = TA - L2; pp = c1 - L2 * sg;
     const double C2r = (Kr - sg * Gr + pp * h.diag) * iD2, C2i = (Ki - sg * Gi) * iD2;
     double s1, k1, s2, k2;
-    sincos(tau * (m1 - m0), &s1, &k1);
-    sincos(tau * (m2 - m0), &s2, &k2);
-    const double Sr = C0r + C1r * k1 + C1i * s1 + C2r * k2 + C2i * s2;
-    const double Si = C0i + C1i * k1 - C1r * s1 + C2i * k2 - C2r * s2;
+    sincos_gap64(tau, c.V1, dl1 - dl0, &s1, &k1);
+    sincos_gap64(tau, c.V2, dl2 - dl0, &s2, &k2);
+    // e^{-i phi} - 1 = (k - 1) - i s
+    const double a1 = k1 - 1.0, a2 = k2 - 1.0;
+    const double Sr = h.diag + C1r * a1 + C1i * s1 + C2r * a2 + C2i * s2;
+    const double Si = C1i * a1 - C1r * s1 + C2i * a2 - C2r * s2;
     return Sr * Sr + Si * Si;
 }
 

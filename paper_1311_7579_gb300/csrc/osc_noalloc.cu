@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
                     load_ch64(s->pc64, ch, h64);
                 }
                 const double Ad = p.sd.kA_rhoye * (double)E;
-                const double P = prob_fp64(c64, h64, (ch >= 9) ? -Ad : Ad, p.sd.cLL / (double)E);
+                const double P = prob_fp64(c64, h64, (ch >= 9) ? -Ad : Ad, tau64(p.sd.cLL, E));
                 acc_event_f64(r, s->acc, hp, (float)s->pc64[C64_ESCALE], er, P * (double)w, p.sd.hscale_d, true);
             }
         }
