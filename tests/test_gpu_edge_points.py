@@ -67,3 +67,35 @@ def test_extreme_points_measured_bound(L, rho, pts):
     w = _worst(synth.all_channel_sample(20_000, seed=int(L), L_km=L, rho=rho), pts)
     assert w["fp64"] <= 1e-12, w
     assert w["fp32"] <= TOL_OUTSIDE and w["fp32_f64eig"] <= TOL_OUTSIDE, w
+
+
+def test_fp64_against_40_digit_reference():
+    """FP64 path against 40-digit values (oracle/hp.py, fixture written by
+    tests/golden/make_fp64_hard_events.py) at 12000 km through 13 g/cm^3 and at
+    1300 km, E_true in [0.05, 1] GeV: the eigenvalue shifts from the shifted
+    cubics and the exactly formed phases keep the FP64 path at the level of
+    the inputs' own rounding."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fp64_hard_events.json")) as f:
+        d = json.load(f)
+    pts = np.array(d["points"])
+    bound = {12000.0: 1e-13, 1300.0: 3e-14}
+    with api.Context(0) as c:
+        api.osc_set_params(c.ptr, pts)
+        for case in d["cases"]:
+            ev = np.array(case["events"])
+            n = ev.shape[0]
+            s = {"n": n, "e_true": ev[:, 4].astype(np.float32), "e_reco": np.ones(n, np.float32),
+                 "w_mc": np.ones(n, np.float32), "flav_in": ev[:, 1].astype(np.uint8),
+                 "flav_out": ev[:, 2].astype(np.uint8), "is_nubar": ev[:, 3].astype(np.uint8),
+                 "baseline_km": case["L_km"], "density_gcc": case["density_gcc"], "ye": case["ye"]}
+            sid = api.osc_load_sample(c.ptr, s)
+            worst = 0.0
+            for k in range(pts.shape[0]):
+                sel = ev[:, 0] == k
+                p = np.zeros(n)
+                api.osc_reweight(c.ptr, sid, k, "fp64", out_prob=p)
+                worst = max(worst, float(np.max(np.abs(p[sel] - ev[sel, 5]))))
+            api.osc_unload_sample(c.ptr, sid)
+            assert worst <= bound[case["L_km"]], (case["L_km"], worst)

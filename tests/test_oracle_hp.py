@@ -1,0 +1,44 @@
+"""The FP64 oracle against 40-digit values of the same definition (Sec. 1.1),
+computed by a different algorithm -- the matrix exponential of M in mpmath
+(oracle/hp.py) rather than the oracle's Jacobi eigendecomposition -- at events
+where FP64 is hardest pressed (tests/golden/fp64_hard_events.json, written by
+tests/golden/make_fp64_hard_events.py).  Two independent implementations that
+agree to a few 1e-13 pin each other."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fp64_hard_events.json")
+# measured: 2.05e-13 at 12000 km (phases ~1e3 rad), 3.2e-14 at 1300 km
+BOUND = {12000.0: 5e-13, 1300.0: 1e-13}
+
+
+def _fixture():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", [0, 1], ids=["12000km-13gcc", "1300km"])
+def test_oracle_matches_40_digit_reference(case):
+    d = _fixture()
+    c = d["cases"][case]
+    worst = 0.0
+    for k, a, b, nb, E, pe in c["events"]:
+        pt = oracle.point_from_row(np.array(d["points"][k]))
+        po = oracle.prob(pt, c["L_km"], c["density_gcc"], c["ye"], E, a, b, nb)
+        worst = max(worst, abs(po - pe))
+    assert worst <= BOUND[c["L_km"]], worst
+
+
+def test_reference_module_reproduces_a_stored_value():
+    mp = pytest.importorskip("mpmath")
+    from oracle import hp
+    d = _fixture()
+    c = d["cases"][0]
+    k, a, b, nb, E, pe = c["events"][7]
+    assert mp.mp.dps > 0
+    assert abs(hp.prob_exact(d["points"][k], c["L_km"], c["density_gcc"], c["ye"], E, a, b, nb) - pe) <= 1e-16
