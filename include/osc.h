@@ -151,6 +151,16 @@ osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samp
                          int32_t point_begin, int32_t n_points, osc_precision prec, double lo,
                          double hi, int32_t nbins, double *out, int out_on_device);
 
+/* One fit step in one call: replaces the point table with the single point *pt
+ * (as osc_set_params(ctx, pt, 1)) and computes its histograms (as
+ * osc_histogram(ctx, sample_ids, n_samples, 0, 1, prec, lo, hi, nbins, out,
+ * out_on_device)); out holds n_samples x nbins doubles.  Same arguments, errors
+ * and synchronisation as those two calls; on an error in the point the table is
+ * left as it was. */
+osc_status osc_histogram_point(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, const osc_point *pt,
+                               osc_precision prec, double lo, double hi, int32_t nbins, double *out,
+                               int out_on_device);
+
 /* Binned ("bin-centre") PDFs: the quicker alternative that Sec. 1.1.1 contrasts
  * with event-by-event reweighting, in which each event's probability is taken
  * at the centre of its true-energy bin instead of at its own E_true (the

@@ -25,10 +25,10 @@ PRECISIONS = {"fp64": OSC_FP64, "fp32": OSC_FP32_BULK, "fp32_f64eig": OSC_FP32_F
 # Every entry point declared in include/osc.h, in declaration order.
 ENTRY_POINTS = [
     "osc_version", "osc_create", "osc_destroy", "osc_last_error", "osc_load_sample", "osc_unload_sample",
-    "osc_set_params", "osc_reweight", "osc_histogram", "osc_set_tile", "osc_enable_timing",
-    "osc_last_timing", "osc_timing_totals", "osc_launch_count", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
-    "osc_serve_stop", "osc_histogram_noalloc", "osc_histogram_bin_centre", "osc_set_layers",
-    "osc_workspace_used",
+    "osc_set_params", "osc_reweight", "osc_histogram", "osc_histogram_point", "osc_histogram_bin_centre",
+    "osc_set_layers", "osc_set_tile", "osc_enable_timing", "osc_last_timing", "osc_timing_totals",
+    "osc_launch_count", "osc_workspace_used", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
+    "osc_serve_stop", "osc_histogram_noalloc",
 ]
 
 
@@ -81,6 +81,8 @@ def load_library(path):
         "osc_reweight": (st, [vp, i32, i32, ctypes.c_int, vp, vp, ctypes.c_int]),
         "osc_histogram": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
                                ctypes.c_int]),
+        "osc_histogram_point": (st, [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(OscPoint), ctypes.c_int, d, d,
+                                     i32, vp, ctypes.c_int]),
         "osc_histogram_bin_centre": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, d, d,
                                           i32, vp, ctypes.c_int]),
         "osc_set_layers": (st, [vp, i32, i32, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
@@ -220,6 +222,21 @@ def osc_histogram(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, o
     dev = _is_device(out)
     _check(ctx, lib().osc_histogram(ctx, ids, n_ids, int(point_begin), int(n_points), PRECISIONS[prec], float(lo),
                                     float(hi), int(nbins), _ptr(out), 1 if dev else 0))
+    return out
+
+
+def osc_histogram_point(ctx, sample_ids, point, prec, lo, hi, nbins, out=None):
+    """One fit step: the point (8 fields) becomes the table and its histograms
+    are computed; out: (n_samples, 1, nbins) as for osc_histogram."""
+    ids, n_ids = _ids(sample_ids)
+    arr, n = _points(point)
+    if n != 1:
+        raise ValueError("osc_histogram_point takes exactly one point")
+    if out is None:
+        out = np.zeros((n_ids, 1, int(nbins)))
+    dev = _is_device(out)
+    _check(ctx, lib().osc_histogram_point(ctx, ids, n_ids, arr, PRECISIONS[prec], float(lo), float(hi), int(nbins),
+                                          _ptr(out), 1 if dev else 0))
     return out
 
 

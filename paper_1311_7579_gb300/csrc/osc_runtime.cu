@@ -98,21 +98,22 @@ osc_status debug_word_check(osc_ctx *c) {
 int prec_kind(osc_precision p) { return p == OSC_FP32_BULK ? kFP32 : p == OSC_FP32_F64EIG ? kMix : kFP64; }
 
 osc_status validate_point(osc_ctx *c, const osc_point &p, int i) {
-    std::ostringstream o;
-    o << "point " << i << ": ";
+    // the message is formatted only for a rejected point (this runs once per point per call)
+    const char *why = nullptr;
     if (!(is_fin(p.s2_12) && is_fin(p.s2_13) && is_fin(p.s2_23) && is_fin(p.dm21) && is_fin(p.dm32) &&
           is_fin(p.dcp) && is_fin(p.escale) && is_fin(p.norm)))
-        return fail(c, OSC_E_RANGE, o.str() + "non-finite field");
+        why = "non-finite field";
     // |U_e1|^2, |U_e2|^2, |U_e3|^2 > 0: no exact level crossing along the matter term
-    if (!(p.s2_12 > 0.0 && p.s2_12 < 1.0)) return fail(c, OSC_E_RANGE, o.str() + "sin^2 theta12 must be in (0, 1)");
-    if (!(p.s2_13 > 0.0 && p.s2_13 < 1.0)) return fail(c, OSC_E_RANGE, o.str() + "sin^2 theta13 must be in (0, 1)");
-    if (!(p.s2_23 >= 0.0 && p.s2_23 <= 1.0)) return fail(c, OSC_E_RANGE, o.str() + "sin^2 theta23 must be in [0, 1]");
-    if (!(p.dm21 > 0.0)) return fail(c, OSC_E_RANGE, o.str() + "dm21 must be > 0");
-    if (!(std::fabs(p.dm32) > p.dm21)) return fail(c, OSC_E_RANGE, o.str() + "|dm32| must exceed dm21");
+    else if (!(p.s2_12 > 0.0 && p.s2_12 < 1.0)) why = "sin^2 theta12 must be in (0, 1)";
+    else if (!(p.s2_13 > 0.0 && p.s2_13 < 1.0)) why = "sin^2 theta13 must be in (0, 1)";
+    else if (!(p.s2_23 >= 0.0 && p.s2_23 <= 1.0)) why = "sin^2 theta23 must be in [0, 1]";
+    else if (!(p.dm21 > 0.0)) why = "dm21 must be > 0";
+    else if (!(std::fabs(p.dm32) > p.dm21)) why = "|dm32| must exceed dm21";
     // the device reduces delta by pi/2 exactly only for |delta| below about 1.6e6
-    if (!(std::fabs(p.dcp) <= 1e6)) return fail(c, OSC_E_RANGE, o.str() + "|delta_CP| must be <= 1e6 rad");
-    if (!(p.escale > 0.0)) return fail(c, OSC_E_RANGE, o.str() + "escale must be > 0");
-    return OSC_OK;
+    else if (!(std::fabs(p.dcp) <= 1e6)) why = "|delta_CP| must be <= 1e6 rad";
+    else if (!(p.escale > 0.0)) why = "escale must be > 0";
+    if (!why) return OSC_OK;
+    return fail(c, OSC_E_RANGE, "point " + std::to_string(i) + ": " + why);
 }
 
 osc_status ensure_acc(osc_ctx *c, int64_t bins) {
@@ -1096,6 +1097,15 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
         return debug_word_check(ctx);
     }
     return OSC_OK;
+}
+
+extern "C" osc_status osc_histogram_point(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                                          const osc_point *pt, osc_precision prec, double lo, double hi,
+                                          int32_t nbins, double *out, int out_on_device) {
+    NvtxRange nvtx_range("osc_histogram_point");
+    const osc_status s = osc_set_params(ctx, pt, 1);
+    if (s) return s;
+    return osc_histogram(ctx, sample_ids, n_samples, 0, 1, prec, lo, hi, nbins, out, out_on_device);
 }
 
 // ------------------------------------------------------ bin-centre method

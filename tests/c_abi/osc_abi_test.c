@@ -108,6 +108,15 @@ static int gpu(const char *in_path, const char *out_path) {
     osc_point bad_pt = pts[0];
     bad_pt.dm21 = -1.0;
     CHECK(osc_set_params(ctx, &bad_pt, 1) == OSC_E_RANGE, "dm21 < 0");
+    /* the one-call fit step equals set_params + histogram over point 0, bitwise */
+    double *one = (double *)calloc(2 * (size_t)nbins, sizeof(double));
+    CHECK(one != NULL, "alloc");
+    CHECK(osc_histogram_point(ctx, &sid, 1, &pts[0], OSC_FP64, hdr[0], hdr[1], nbins, one, 0) == OSC_OK,
+          osc_last_error(ctx));
+    CHECK(memcmp(one, out, (size_t)nbins * sizeof(double)) == 0, "histogram_point != histogram of point 0");
+    CHECK(osc_histogram_point(ctx, &sid, 1, &bad_pt, OSC_FP64, hdr[0], hdr[1], nbins, one, 0) == OSC_E_RANGE,
+          "histogram_point with dm21 < 0");
+    free(one);
     CHECK(osc_sync(ctx) == OSC_OK, "sync");
     uint64_t launches = 0;
     CHECK(osc_launch_count(ctx, &launches) == OSC_OK && launches > 0, "launch count");

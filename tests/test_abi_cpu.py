@@ -65,6 +65,7 @@ def test_calls_without_context_return_arg_status():
     assert L.osc_reweight(None, 0, 0, 0, None, None, 0) == api.OSC_E_ARG
     assert L.osc_histogram(None, None, 1, 0, 1, 0, 0.0, 5.0, 100, None, 0) == api.OSC_E_ARG
     assert L.osc_histogram_bin_centre(None, None, 1, 0, 1, 0, 0.0, 10.0, 40, 0.0, 5.0, 100, None, 0) == api.OSC_E_ARG
+    assert L.osc_histogram_point(None, None, 1, None, 0, 0.0, 5.0, 100, None, 0) == api.OSC_E_ARG
     assert L.osc_set_layers(None, 0, 1, None, None, None) == api.OSC_E_ARG
     assert L.osc_sync(None) == api.OSC_E_ARG
     assert L.osc_serve_stop(None) == api.OSC_E_ARG

@@ -298,3 +298,38 @@ def test_device_outputs_match_host_outputs(ctx):
     ph, _ = _gpu_probs(ctx, sid, 2, "fp64", s["n"])
     assert np.array_equal(pd.cpu().numpy(), ph)
     api.osc_unload_sample(ctx, sid)
+
+
+def test_histogram_point_is_set_params_plus_histogram(ctx):
+    """osc_histogram_point(pt) gives the bins of osc_set_params([pt]) followed by
+    osc_histogram over point 0, bitwise, for host, page-locked and device outputs;
+    an invalid point is rejected and leaves the table as it was."""
+    torch = pytest.importorskip("torch")
+    s1 = synth.table1_sample(20000, seed=21)
+    s2 = synth.all_channel_sample(15000, seed=22, L_km=810.0, rho=2.8)
+    ids = [api.osc_load_sample(ctx, s1), api.osc_load_sample(ctx, s2)]
+    pts = synth.scan_points(3, seed=23)
+    for k in range(3):
+        for prec in ("fp32", "fp64"):
+            api.osc_set_params(ctx, pts[k:k + 1])
+            ref = api.osc_histogram(ctx, ids, 0, 1, prec, LO, HI, NB)
+            got = api.osc_histogram_point(ctx, ids, pts[k], prec, LO, HI, NB)
+            assert np.array_equal(got, ref)
+            pin = torch.zeros((2, 1, NB), dtype=torch.float64).pin_memory().numpy()
+            api.osc_histogram_point(ctx, ids, pts[k], prec, LO, HI, NB, out=pin)
+            assert np.array_equal(pin, ref)
+            dev = torch.zeros((2, 1, NB), dtype=torch.float64, device="cuda")
+            api.osc_histogram_point(ctx, ids, pts[k], prec, LO, HI, NB, out=dev)
+            api.osc_sync(ctx)
+            assert np.array_equal(dev.cpu().numpy(), ref)
+    bad = pts[0].copy()
+    bad[3] = -1.0  # dm21 <= 0
+    with pytest.raises(api.OscError) as e:
+        api.osc_histogram_point(ctx, ids, bad, "fp32", LO, HI, NB)
+    assert e.value.status == api.OSC_E_RANGE
+    # the table still holds the last valid point
+    again = api.osc_histogram(ctx, ids, 0, 1, "fp64", LO, HI, NB)
+    api.osc_set_params(ctx, pts[2:3])
+    assert np.array_equal(again, api.osc_histogram(ctx, ids, 0, 1, "fp64", LO, HI, NB))
+    for sid in ids:
+        api.osc_unload_sample(ctx, sid)
