@@ -19,12 +19,19 @@ import numpy as np
 from . import api, synth
 
 
-def poisson_loglike(data, expected) -> float:
+def log_factorials(data) -> np.ndarray:
+    """log(D_i!) of every bin (constant over a fit: computed once)."""
+    return np.array([math.lgamma(d + 1.0) for d in np.asarray(data, dtype=np.float64)])
+
+
+def poisson_loglike(data, expected, lgam=None) -> float:
     """log of Eq. (2): sum_i [D_i log(lam_i) - lam_i - log(D_i!)], with lam_i the
-    expected count of bin i (bins with lam_i = 0 contribute only if D_i = 0)."""
+    expected count of bin i (bins with lam_i = 0 contribute only if D_i = 0).
+    lgam: log_factorials(data), when the caller has them."""
     data = np.asarray(data, dtype=np.float64)
     lam = np.asarray(expected, dtype=np.float64)
-    lgam = np.array([math.lgamma(d + 1.0) for d in data])
+    if lgam is None:
+        lgam = log_factorials(data)
     with np.errstate(divide="ignore", invalid="ignore"):
         term = np.where(lam > 0, data * np.log(np.where(lam > 0, lam, 1.0)) - lam, np.where(data > 0, -np.inf, 0.0))
     return float(np.sum(term - lgam))
@@ -68,6 +75,15 @@ class ToyFit:
         self.lo, self.hi, self.nbins = lo, hi, int(nbins)
         self.prec = prec
         self.base = synth.table1_point() if base_point is None else np.asarray(base_point, dtype=np.float64)
+        self.lgam = log_factorials(self.data)
+        # one output buffer for every step, page-locked when torch can provide it
+        # (the histogram kernel then writes it directly, with no staging copy)
+        try:
+            import torch
+            self.out = torch.zeros((1, 1, self.nbins), dtype=torch.float64).pin_memory().numpy()
+        except Exception:
+            self.out = np.zeros((1, 1, self.nbins))
+        self.row = self.base.copy()
         self.calls = 0
 
     def point(self, x):
@@ -76,13 +92,13 @@ class ToyFit:
         return row
 
     def expected(self, x):
-        api.osc_set_params(self.ctx, self.point(x)[None, :])
-        h = api.osc_histogram(self.ctx, [self.sid], 0, 1, self.prec, self.lo, self.hi, self.nbins)[0, 0]
+        self.row[2], self.row[4] = x[0], x[1]
+        api.osc_histogram_point(self.ctx, [self.sid], self.row, self.prec, self.lo, self.hi, self.nbins, out=self.out)
         self.calls += 1
-        return self.exposure * h
+        return self.exposure * self.out[0, 0]
 
     def loglike(self, x):
-        return poisson_loglike(self.data, self.expected(x))
+        return poisson_loglike(self.data, self.expected(x), self.lgam)
 
 
 def fake_data(expected, seed):
