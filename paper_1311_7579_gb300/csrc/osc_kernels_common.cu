@@ -120,6 +120,50 @@ cudaError_t launch_hist_programmatic(int prec, int pt, const HistParams &p, int 
     return cudaLaunchKernelExC(&cfg, hist_kernel_fn(prec, pt), args);
 }
 
+// Serving finalize: k_final's conversion, then a completion flag in host-mapped
+// memory.  Every thread's bin stores go to host-mapped memory and are fenced at
+// system scope before its block takes a ticket; the block that takes the last
+// ticket stores the batch's sequence number with release semantics at system
+// scope, so a host thread that reads the new value and then acquires sees every
+// bin.  The host polls the flag instead of waiting for a stream callback.
+__global__ void __launch_bounds__(256) k_final_flag(const FinalFlag p) {
+    grid_dependency_wait();
+    const FinalParams &f = p.f;
+    const int64_t n = f.n_hist * (int64_t)f.nbins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long d0 = __ldcg(f.acc + 3 * i), d1 = __ldcg(f.acc + 3 * i + 1), d2 = __ldcg(f.acc + 3 * i + 2);
+        f.acc[3 * i] = 0ull;
+        f.acc[3 * i + 1] = 0ull;
+        f.acc[3 * i + 2] = 0ull;
+        f.out[i] = final_bin(d0, d1, d2, f.hmeta + 4 * (i / f.nbins), f.pc64);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(p.ticket, 1) == (int)gridDim.x - 1) {
+        *p.ticket = 0;
+        __threadfence_system();
+        asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p.flag), "l"(p.seq) : "memory");
+    }
+}
+
+cudaError_t launch_final_flag(const FinalFlag &p, cudaStream_t st) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(final_blocks(p.f.n_hist * (int64_t)p.f.nbins));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FinalFlag q = p;
+    void *args[] = {&q};
+    return cudaLaunchKernelExC(&cfg, (const void *)k_final_flag, args);
+}
+
 int final_blocks(int64_t n_bins) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n_bins + 255) / 256, 152 * 8));
 }

@@ -15,6 +15,16 @@ cudaError_t launch_final(const FinalParams &p, cudaStream_t st);
 // The finalize kernel with programmatic stream serialization (after a histogram kernel).
 cudaError_t launch_final_programmatic(const FinalParams &p, cudaStream_t st);
 int final_blocks(int64_t n_bins);
+// Serving: the finalize kernel, launched programmatically, whose last block
+// stores seq to *flag (host-mapped memory) after every bin is visible to the
+// host; ticket is a device int the kernel leaves at 0.
+struct FinalFlag {
+    FinalParams f;
+    unsigned long long *flag;
+    unsigned long long seq;
+    int32_t *ticket;
+};
+cudaError_t launch_final_flag(const FinalFlag &p, cudaStream_t st);
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st);
 // Kernel function pointers (for CUDA-graph kernel nodes and occupancy queries).
 const void *hist_kernel_fn(int prec, int pt);

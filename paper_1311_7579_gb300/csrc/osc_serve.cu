@@ -5,13 +5,18 @@
 // into batches while at most max_slots requests are in flight and a batch slot
 // (preallocated device memory, charged to the workspace cap at serve start) is
 // free.  Each batch runs on its own stream -- one input copy, constants kernel,
-// histogram kernel over (request, event range) work items whose finalize writes
-// the bins straight into pinned host memory -- so batches admitted while earlier
-// ones run overlap on the device.  A host
-// callback marks the batch complete; osc_wait hands each request's histogram
-// back.  Bins are exact integer sums, so a request's result is bitwise the same
-// alone and in any mix.
+// histogram kernel over (request, event range) work items, finalize kernel that
+// writes the bins straight into pinned host memory -- so batches admitted while
+// earlier ones run overlap on the device.  The finalize kernel's last block then
+// stores the batch's sequence number into a host-mapped flag; the scheduler
+// polls the flags of the batches in flight (no stream callback, whose wake-up
+// latency would dominate small requests), publishes the results, and osc_wait
+// hands each request's histogram back.  While batches are in flight, and for a
+// short while after, the scheduler thread spins rather than sleeps.  Bins are
+// exact integer sums, so a request's result is bitwise the same alone and in
+// any mix.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -26,6 +31,9 @@ namespace {
 
 constexpr int kBatches = 3;          // batches in flight (one stream each)
 constexpr int kMaxItems = 1 << 16;   // work items per batch
+constexpr int kFlagTicket = 4;       // int of a batch's counter block used by the finalize kernel's ticket
+// the scheduler keeps polling this long after its last batch before it sleeps
+constexpr std::chrono::microseconds kIdleSpin(200);
 
 struct Request {
     uint64_t ticket;
@@ -78,9 +86,13 @@ struct Batch {
     WorkItem *h_items = nullptr;
     double *h_out = nullptr;
     double *d_out = nullptr;
+    // completion flag: host-mapped, written by the finalize kernel's last block
+    unsigned long long *h_flag = nullptr;
+    unsigned long long *d_flag = nullptr;
+    unsigned long long seq = 0;  // sequence number of the batch last launched in this slot
     // state
     std::vector<Request> reqs;
-    bool busy = false;  // queued work not yet finished (cleared by the completion callback)
+    bool busy = false;  // launched and not yet published
 };
 
 }  // namespace
@@ -104,32 +116,27 @@ struct osc_serve {
 
 namespace {
 
-// Runs (on the CUDA callback thread) when a batch's work has finished: publishes
-// its requests' histograms, which the finalize wrote into pinned host memory, and
-// frees the batch slot -- the waiters and the scheduler are woken directly.
-void CUDART_CB on_batch_done(void *arg) {
-    auto *pr = static_cast<std::pair<osc_serve *, Batch *> *>(arg);
-    osc_serve *sv = pr->first;
-    Batch &b = *pr->second;
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        const auto now = Clock::now();
-        for (size_t r = 0; r < b.reqs.size(); ++r) {
-            Result res;
-            res.hist.assign(b.h_out + r * sv->nbins, b.h_out + (r + 1) * sv->nbins);
-            res.latency_us = std::chrono::duration<double, std::micro>(now - b.reqs[r].t_submit).count();
-            sv->results[b.reqs[r].ticket] = std::move(res);
-        }
-        sv->inflight -= (int32_t)b.reqs.size();
-        b.reqs.clear();
-        b.busy = false;
+// Publishes a finished batch's histograms, which the finalize wrote into pinned
+// host memory, and frees the batch slot (scheduler thread, lock held).
+void publish(osc_serve *sv, Batch &b) {
+    const auto now = Clock::now();
+    for (size_t r = 0; r < b.reqs.size(); ++r) {
+        Result res;
+        res.hist.assign(b.h_out + r * sv->nbins, b.h_out + (r + 1) * sv->nbins);
+        res.latency_us = std::chrono::duration<double, std::micro>(now - b.reqs[r].t_submit).count();
+        sv->results[b.reqs[r].ticket] = std::move(res);
     }
-    sv->cv_done.notify_all();
-    sv->cv.notify_all();
+    sv->inflight -= (int32_t)b.reqs.size();
+    b.reqs.clear();
+    b.busy = false;
 }
 
+// The batch's completion flag, read with acquire semantics: a value equal to
+// the batch's sequence number means every bin of it is in host memory.
+bool batch_done(const Batch &b) { return __atomic_load_n(b.h_flag, __ATOMIC_ACQUIRE) == b.seq; }
+
 // Build and enqueue one batch (called by the scheduler thread without the lock).
-osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *> *cb_arg) {
+osc_status launch_batch(osc_serve *sv, Batch &b) {
     NvtxRange nvtx_range("serving batch");
     osc_ctx *ctx = sv->ctx;
     const int n = (int)b.reqs.size();
@@ -202,11 +209,10 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
     hp.lo_f = (float)sv->lo;
     hp.inv_f = (float)((double)sv->nbins / (sv->hi - sv->lo));
     hp.nb_f = (float)sv->nbins;
-    const bool fused = fuse_finalize(n, sv->nbins, 1);
-    hp.fuse_final = fused ? 1 : 0;
-    hp.fin_n_hist = n;
-    hp.fin_hmeta = b.d_hmeta;
-    hp.fin_out = b.d_out;
+    hp.fuse_final = 0;  // the flag-writing finalize kernel below converts the bins
+    hp.fin_n_hist = 0;
+    hp.fin_hmeta = nullptr;
+    hp.fin_out = nullptr;
     int kernels = 0;
     if (n_lay > 0) {
         // layered items: their own ticket counter, finalized by the last kernel below
@@ -228,57 +234,103 @@ osc_status launch_batch(osc_serve *sv, Batch &b, std::pair<osc_serve *, Batch *>
         e = launch_hist_programmatic(prec, 1, hs, hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + 7) / 8), st);
         ++kernels;
     }
-    FinalParams fp{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter};
-    if (!e && !fused) e = launch_final_programmatic(fp, st);
-    if (!e) e = cudaLaunchHostFunc(st, on_batch_done, cb_arg);
+    FinalFlag ff{{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter}, b.d_flag, b.seq + 1,
+                 b.d_counter + kFlagTicket};
+    if (!e) e = launch_final_flag(ff, st);
     if (e) return fail_cuda(ctx, e, "serving batch launch");
-    ctx->launches += 1 + kernels + (fused ? 0 : 1);
+    ++b.seq;
+    ctx->launches += 2 + kernels;
     return OSC_OK;
+}
+
+// Fails every batch in flight after a CUDA error (lock held): their requests
+// get no result, and osc_wait reports the error.
+void fail_inflight(osc_serve *sv, const std::string &what) {
+    sv->thread_error = what;
+    sv->stop = true;
+    for (auto &b : sv->batch) {
+        sv->inflight -= (int32_t)b.reqs.size();
+        b.reqs.clear();
+        b.busy = false;
+    }
+    sv->cv_done.notify_all();
 }
 
 void scheduler(osc_serve *sv) {
     cudaSetDevice(sv->ctx->device);
-    std::pair<osc_serve *, Batch *> cb[kBatches];
-    for (int k = 0; k < kBatches; ++k) cb[k] = {sv, &sv->batch[k]};
     std::unique_lock<std::mutex> lk(sv->mu);
+    uint64_t polls = 0;
+    Clock::time_point idle_since = Clock::now();
     for (;;) {
-        sv->cv.wait(lk, [&] {
-            bool any_busy = false;
-            for (auto &b : sv->batch) any_busy |= b.busy;
-            if (sv->stop) return !any_busy;  // let in-flight batches finish
-            if (sv->pending.empty() || sv->inflight >= sv->max_slots) return false;
-            return !(sv->batch[0].busy && sv->batch[1].busy && sv->batch[2].busy);
-        });
-        if (sv->stop) break;
-        // admit: one free batch slot, up to the free request slots, one precision per batch
-        Batch *free_b = nullptr;
-        int free_k = 0;
-        for (int k = 0; k < kBatches; ++k)
-            if (!sv->batch[k].busy) {
-                free_b = &sv->batch[k];
-                free_k = k;
+        // 1. publish finished batches
+        bool any_busy = false, published = false;
+        for (auto &b : sv->batch) {
+            if (!b.busy) continue;
+            if (batch_done(b)) {
+                publish(sv, b);
+                published = true;
+            } else {
+                any_busy = true;
+            }
+        }
+        if (published) {
+            sv->cv_done.notify_all();
+            idle_since = Clock::now();
+        }
+        // every 256 polls of a busy device, ask the streams for errors (a batch
+        // whose kernels failed never raises its flag)
+        if (any_busy && (++polls & 255u) == 0) {
+            for (auto &b : sv->batch) {
+                if (!b.busy) continue;
+                const cudaError_t e = cudaStreamQuery(b.stream);
+                if (e == cudaErrorNotReady) continue;
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    fail_inflight(sv, std::string("serving batch: ") + cudaGetErrorString(e));
+                    any_busy = false;
+                } else if (!batch_done(b)) {
+                    fail_inflight(sv, "serving batch finished without its completion flag");
+                    any_busy = false;
+                }
                 break;
             }
-        if (!free_b || sv->pending.empty() || sv->inflight >= sv->max_slots) continue;
-        const int take_max = sv->max_slots - sv->inflight;
-        const int prec = sv->pending.front().prec;
-        while ((int)free_b->reqs.size() < take_max && !sv->pending.empty() && sv->pending.front().prec == prec) {
-            free_b->reqs.push_back(sv->pending.front());
-            sv->pending.pop_front();
         }
-        sv->inflight += (int32_t)free_b->reqs.size();
-        free_b->busy = true;
-        lk.unlock();
-        osc_status st = launch_batch(sv, *free_b, &cb[free_k]);
-        lk.lock();
-        if (st != OSC_OK) {
-            sv->thread_error = sv->ctx->err;
-            sv->stop = true;
-            free_b->busy = false;
-            sv->inflight -= (int32_t)free_b->reqs.size();
-            free_b->reqs.clear();
-            sv->cv_done.notify_all();
+        if (sv->stop && !any_busy) break;
+        // 2. admit one batch: a free slot, up to the free request slots, one precision per batch
+        if (!sv->stop && !sv->pending.empty() && sv->inflight < sv->max_slots) {
+            Batch *free_b = nullptr;
+            for (auto &b : sv->batch)
+                if (!b.busy) {
+                    free_b = &b;
+                    break;
+                }
+            if (free_b) {
+                const int take_max = sv->max_slots - sv->inflight;
+                const int prec = sv->pending.front().prec;
+                while ((int)free_b->reqs.size() < take_max && !sv->pending.empty() &&
+                       sv->pending.front().prec == prec) {
+                    free_b->reqs.push_back(sv->pending.front());
+                    sv->pending.pop_front();
+                }
+                sv->inflight += (int32_t)free_b->reqs.size();
+                free_b->busy = true;
+                lk.unlock();
+                const osc_status st = launch_batch(sv, *free_b);
+                lk.lock();
+                if (st != OSC_OK) fail_inflight(sv, sv->ctx->err);
+                continue;
+            }
         }
+        // 3. poll while work is in flight or queued, or shortly after the last
+        //    batch; otherwise sleep until a request arrives
+        if (any_busy || !sv->pending.empty() || Clock::now() - idle_since < kIdleSpin) {
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+            continue;
+        }
+        sv->cv.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
+        idle_since = Clock::now();
     }
 }
 
@@ -295,6 +347,7 @@ void free_serve(osc_ctx *ctx, osc_serve *sv) {
         dfree(ctx, b.d_counter);
         cudaFreeHost(b.h_stage);
         cudaFreeHost(b.h_out);
+        cudaFreeHost(b.h_flag);
     }
     delete sv;
 }
@@ -339,6 +392,11 @@ osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi
             if (!e) e = cudaHostAlloc((void **)&b.h_stage, b.lay.bytes, 0);
             if (!e) e = cudaHostAlloc((void **)&b.h_out, S * B * 8, cudaHostAllocMapped);
             if (!e) e = cudaHostGetDevicePointer((void **)&b.d_out, b.h_out, 0);
+            if (!e) e = cudaHostAlloc((void **)&b.h_flag, 64, cudaHostAllocMapped);
+            if (!e) {
+                *b.h_flag = 0;
+                e = cudaHostGetDevicePointer((void **)&b.d_flag, b.h_flag, 0);
+            }
             if (!e) e = cudaStreamSynchronize(b.stream);
             if (e) st = fail_cuda(ctx, e, "serving buffers");
         }
