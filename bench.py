@@ -69,8 +69,8 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profile_field(name):
-    """An integer field of the bench kernel's committed ncu summary, or None when
+def _profile_field(name, kind=int):
+    """A numeric field of the bench kernel's committed ncu summary, or None when
     the kernel sources changed since that capture."""
     if not os.path.exists(TRAFFIC_PROFILE):
         return None
@@ -82,7 +82,7 @@ def _profile_field(name):
     if fields.get("kernel_source_sha256_16") != _kernel_source_hash():
         return None
     try:
-        return int(fields[name])
+        return kind(fields[name])
     except (KeyError, ValueError):
         return None
 
@@ -661,6 +661,13 @@ def run_ours(args):
             issue = {"achieved": ia, "peak": issue_peak, "unit": "T warp-instructions/s", "frac": ia / issue_peak,
                      "warp_instructions_per_launch": winst,
                      "thread_instructions_per_evpt": 32.0 * winst / N_EVENTS}
+        # per-pipe view: instructions executed by each pipe, % of that pipe's peak over the
+        # kernel's active cycles (ncu, the committed summary of this kernel)
+        pipes = {k: _profile_field("pipe_%s_pct_of_peak" % k, float) for k in ("fma", "alu", "xu", "fp64")}
+        pipes = ({k: v / 100.0 for k, v in pipes.items()} if all(v is not None for v in pipes.values()) else None)
+        if pipes is not None:
+            pipes["binding"] = "instruction issue (no single pipe saturated)"
+            pipes["source"] = "ncu sm__inst_executed_pipe_*, " + os.path.relpath(TRAFFIC_PROFILE, ROOT)
         # precision study + CPU baseline (rank 0, N = 1 semantics: its own sample)
         p32 = np.zeros(N_EVENTS)
         p64 = np.zeros(N_EVENTS)
@@ -684,7 +691,7 @@ def run_ours(args):
         configs.update(configs_leg(torch, api, synth, c, stream, flush))
         serving = None
         if args.serve_seconds > 0:
-            serving = {"fp32": serving_leg(api, synth, c, (1000, 2000, 10000, 20000, 50000), args.serve_seconds,
+            serving = {"fp32": serving_leg(api, synth, c, (1000, 2000, 5000, 10000, 20000, 50000), args.serve_seconds,
                                            "fp32"),
                        "fp64": serving_leg(api, synth, c, (100,), args.serve_seconds, "fp64")}
         result = {
@@ -712,7 +719,7 @@ def run_ours(args):
                          "flop_per_evpt": FP32_FLOP_PER_EVPT,
                          "hbm_gbs_event_stream": 16.0 * N_EVENTS / (k_hist_ms * 1e-3) / 1e9,
                          "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                         "issue": issue},
+                         "issue": issue, "pipes": pipes},
             "cpu_baseline": cpu,
             "precision": prec_study,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64, "d2h_bytes_per_step": 8 * NBINS},
