@@ -236,11 +236,15 @@ osc_status osc_workspace_used(const osc_ctx *ctx, size_t *bytes);
 /* Block until all work enqueued by the context has finished. */
 osc_status osc_sync(osc_ctx *ctx);
 
-/* Continuous-batching serving loop (spec item 5; each request is one MCMC
- * step's reweight, Sec. 2.2).  A scheduler thread inside the library admits
- * queued (sample, point) requests into at most max_slots in-flight slots under
- * the workspace cap and packs them into persistent launches on the context
- * stream; each request yields one nbins histogram over [lo, hi). */
+/* Continuous-batching serving loop (each request is one MCMC step's reweight,
+ * Sec. 2.2).  A scheduler thread inside the library admits queued (sample,
+ * point) requests into at most max_slots in-flight slots under the workspace cap
+ * and packs them into batches of persistent launches, up to three batches in
+ * flight on streams of their own; each request yields one nbins histogram over
+ * [lo, hi).  The scheduler learns of a finished batch by polling a flag the
+ * batch's last kernel raises in host-mapped memory: while batches are in flight,
+ * and for 200 us after the last one, it keeps one host core busy; otherwise it
+ * sleeps until a request is submitted. */
 osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi, int32_t nbins);
 osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_precision prec,
                       uint64_t *ticket);
