@@ -171,6 +171,23 @@ def test_precision_sample_10M_full_size():
     _check(h32, s, [row], tb, 0.0, 5.0, 100, "fp32")
 
 
+def test_batched_scan_2M_x_4096_full_size():
+    """The bench's scan configuration: 2M events x 4096 points in one
+    autotuned bin-centre launch (FP32 and FP64 tables); six sampled points,
+    among them the first and last of the table, against the oracle."""
+    s = synth.scan_sample()
+    pts = synth.scan_points()
+    tb = (0.0, 10.25, 410)
+    pick = [0, 1, 777, 2048, 3001, 4095]
+    with api.Context(0) as c:
+        sid = api.osc_load_sample(c.ptr, s)
+        api.osc_set_params(c.ptr, pts)
+        h32 = api.osc_histogram_bin_centre(c.ptr, [sid], 0, 4096, "fp32", *tb, 0.0, 5.0, 100)[0]
+        h64 = api.osc_histogram_bin_centre(c.ptr, [sid], 0, 4096, "fp64", *tb, 0.0, 5.0, 100)[0]
+    _check(h32[pick], s, pts[pick], tb, 0.0, 5.0, 100, "fp32")
+    _check(h64[pick], s, pts[pick], tb, 0.0, 5.0, 100, "fp64")
+
+
 def test_bad_arguments_rejected():
     s = synth.beam_sample(100, seed=1)
     with api.Context(0) as c:
