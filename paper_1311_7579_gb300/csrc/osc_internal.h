@@ -24,7 +24,7 @@ __host__ __device__ inline int chan_id(int alpha, int beta, int nubar) { return 
 // ---- per-point constants (written by the constants kernel in FP64) ----------
 // FP32 block (floats).  Layout offsets:
 enum PC32 : int {
-    C32_P0 = 0, C32_P1, C32_Q0, C32_Q1, C32_Q2,  // depressed-cubic seed coefficients in A
+    C32_P0 = 0, C32_P1, C32_Q0, C32_Q1, C32_Q2,  // depressed cubic's -p/3 (P0, P1) and -q/2 (Q0..Q2) in A
     C32_T0, C32_C10, C32_SMT,                    // tr H0, c1(A=0), H0_mumu + H0_tautau
     C32_D0, C32_D1, C32_D2,                      // sorted vacuum eigenvalues (eV^2)
     C32_G01, C32_G02, C32_G12,                   // vacuum gaps d_i - d_j
@@ -32,6 +32,7 @@ enum PC32 : int {
     C32_S0, C32_PI0, C32_W0, C32_E0,             // shifted-cubic constants, sorted root 0
     C32_S1, C32_PI1, C32_W1, C32_E1,             // ... sorted root 1
     C32_ESCALE,
+    C32_TD0, C32_TD1,                            // T0 / 3 - d0, T0 / 3 - d1
     C32_CH = 32,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
     C32_LU = 96,                                 // U[f][l] (re, im), f flavour, l sorted vacuum root, neutrino
     C32_STRIDE = 128                             // floats, 512 B

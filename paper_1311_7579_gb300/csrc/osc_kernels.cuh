@@ -187,6 +187,7 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
         split_ff(d1 - d0, &c32[C32_V1H], &c32[C32_V1L]);
         split_ff(d2 - d0, &c32[C32_V2H], &c32[C32_V2L]);
         c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10;
+        c32[C32_TD0] = (float)(T0 / 3.0 - d0); c32[C32_TD1] = (float)(T0 / 3.0 - d1);
         c64[C64_T0] = T0; c64[C64_C10] = c10;
         c32[C32_ESCALE] = (float)P.escale;
         c64[C64_ESCALE] = P.escale;
@@ -260,7 +261,8 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
         v = fma(w3, T2 * T0, v);
         const int o32 = lane == 0 ? C32_P0 : lane == 1 ? C32_P1 : lane == 2 ? C32_Q0 : lane == 3 ? C32_Q1 : C32_Q2;
         const int o64 = lane == 0 ? C64_P0 : lane == 1 ? C64_P1 : lane == 2 ? C64_Q0 : lane == 3 ? C64_Q1 : C64_Q2;
-        c32[o32] = (float)v;
+        // FP32 seed coefficients of -p/3 and -q/2 (the forms the seed uses)
+        c32[o32] = (float)(v * (lane < 2 ? -1.0 / 3.0 : -0.5));
         c64[o64] = v;
         if (lane == 0) {
             c32[C32_SMT] = (float)smt;
@@ -273,6 +275,7 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
 __device__ __forceinline__ void load_pt32(const float *__restrict__ c, Pt32 &o) {
     o.p0 = c[C32_P0]; o.p1 = c[C32_P1]; o.q0 = c[C32_Q0]; o.q1 = c[C32_Q1]; o.q2 = c[C32_Q2];
     o.T0 = c[C32_T0]; o.c10 = c[C32_C10]; o.smt = c[C32_SMT];
+    o.td0 = c[C32_TD0]; o.td1 = c[C32_TD1];
     o.d0 = c[C32_D0]; o.d1 = c[C32_D1]; o.d2 = c[C32_D2];
     o.g01 = c[C32_G01]; o.g02 = c[C32_G02]; o.g12 = c[C32_G12];
     o.v1h = c[C32_V1H]; o.v1l = c[C32_V1L]; o.v2h = c[C32_V2H]; o.v2l = c[C32_V2L];

@@ -43,28 +43,31 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// arccos on [-1, 1] from Abramowitz & Stegun, Handbook of Mathematical
+// arccos(x) / 3 on [-1, 1] from Abramowitz & Stegun, Handbook of Mathematical
 // Functions, formula 4.4.46: acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7)
-// for 0 <= x <= 1 with |error| <= 2e-8, and acos(-x) = pi - acos(x).  Branch-free;
-// it only seeds the Newton-refined eigenvalues, which need ~1e-5 relative accuracy.
-__device__ __forceinline__ float acos_seed(float x) {
+// for 0 <= x <= 1 with |error| <= 2e-8, and acos(-x) = pi - acos(x); the
+// coefficients and pi carry the 1/3 of the cube angle.  Branch-free; it only
+// seeds the Newton-refined eigenvalues, which need ~1e-5 relative accuracy.
+__device__ __forceinline__ float acos_third(float x) {
+    constexpr float k = 1.0f / 3.0f;
     const float ax = fabsf(x);
-    float p = -0.0012624911f;
-    p = fmaf(p, ax, 0.0066700901f);
-    p = fmaf(p, ax, -0.0170881256f);
-    p = fmaf(p, ax, 0.0308918810f);
-    p = fmaf(p, ax, -0.0501743046f);
-    p = fmaf(p, ax, 0.0889789874f);
-    p = fmaf(p, ax, -0.2145988016f);
-    p = fmaf(p, ax, 1.5707963050f);
+    float p = -0.0012624911f * k;
+    p = fmaf(p, ax, 0.0066700901f * k);
+    p = fmaf(p, ax, -0.0170881256f * k);
+    p = fmaf(p, ax, 0.0308918810f * k);
+    p = fmaf(p, ax, -0.0501743046f * k);
+    p = fmaf(p, ax, 0.0889789874f * k);
+    p = fmaf(p, ax, -0.2145988016f * k);
+    p = fmaf(p, ax, 1.5707963050f * k);
     float sq;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(1.0f - ax));
     const float r = sq * p;
-    return x < 0.0f ? 3.14159265358979323846f - r : r;
+    return x < 0.0f ? 3.14159265358979323846f * k - r : r;
 }
 
 struct Pt32 {
-    float p0, p1, q0, q1, q2, T0, c10, smt;
+    float p0, p1, q0, q1, q2, T0, c10, smt;  // p*: -p/3, q*: -q/2 of the depressed cubic, in powers of A
+    float td0, td1;                          // T0 / 3 - d0, T0 / 3 - d1
     float d0, d1, d2, g01, g02, g12;
     float v1h, v1l, v2h, v2l;
     float S0, PI0, W0, E0, S1, PI1, W1, E1;
@@ -105,27 +108,36 @@ __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float v
 }
 
 // Trigonometric FP32 seed of the two lower roots m0 <= m1 of the depressed
-// cubic mu^3 + p mu + q (Viete's form with the arccos and cube-angle above).
-__device__ __forceinline__ void seed_depressed32(float p, float q, float &m0, float &m1) {
-    const float mp3 = fmaxf(p * (-1.0f / 3.0f), 1e-30f);
+// cubic mu^3 + p mu + q (Viete's form with the arccos and cube-angle above),
+// from mp3 = -p/3 and qh = -q/2: mu = 2 r cos(theta/3 + 2 pi k/3) with
+// r = sqrt(mp3) and cos(theta) = qh / r^3.
+__device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, float &m1) {
+    mp3 = fmaxf(mp3, 1e-30f);
     const float ir = rsqrt_approx(mp3);
     const float r = mp3 * ir;
-    float cth = -0.5f * q * (ir * ir * ir);
+    float cth = qh * ir * ir * ir;
     cth = fminf(fmaxf(cth, -1.0f), 1.0f);
-    const float th3 = acos_seed(cth) * (1.0f / 3.0f);
+    const float th3 = acos_third(cth);
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;
     m0 = -rc - rsn;  // smallest root
     m1 = -rc + rsn;  // middle root
 }
+__device__ __forceinline__ void seed_depressed32(float p, float q, float &m0, float &m1) {
+    seed_core32(p * (-1.0f / 3.0f), -0.5f * q, m0, m1);
+}
 
-// The same seed for the characteristic cubic of one event, as roots mu of the
-// depressed cubic (lambda = mu + (T0 + A) / 3).
+// The same seed for the characteristic cubic of one event, from the point's
+// pre-scaled coefficients: -p/3 = P0 + P1 A + A^2/9, -q/2 = Q0 + Q1 A + Q2 A^2 + A^3/27.
+__device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1) {
+    const float mp3 = fmaf(fmaf(A, 1.0f / 9.0f, c.p1), A, c.p0);
+    const float qh = fmaf(fmaf(fmaf(A, 1.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
+    seed_core32(mp3, qh, m0, m1);
+}
+// As roots mu of the depressed cubic (lambda = mu + (T0 + A) / 3).
 __device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3) {
-    const float p = fmaf(fmaf(A, -1.0f / 3.0f, c.p1), A, c.p0);
-    const float q = fmaf(fmaf(fmaf(A, -2.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
-    seed_depressed32(p, q, m0, m1);
+    seed_scaled32(c, A, m0, m1);
     t3 = (c.T0 + A) * (1.0f / 3.0f);
 }
 
@@ -134,28 +146,28 @@ __device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, 
 // coefficients C_l = N_l / D_l; the projectors sum to the identity, so
 // S = delta_ba + sum_{l=1,2} C_l (e^{-i phi_l} - 1) needs no C_0, and
 // e^{-i phi} - 1 = -2 sin(phi/2) (sin(phi/2) + i cos(phi/2)) keeps small phase
-// differences accurate.  The factor -2 is folded into 1/D_l:
-// D_1 = (L1 - L0)(L1 - L2) = -g01 g12, D_2 = (L2 - L0)(L2 - L1) = g02 g12.
+// differences accurate.  The factor -2 sin(phi_l / 2) is folded into 1/D_l:
+// D_1 = (L1 - L0)(L1 - L2) = -g01 g12, D_2 = (L2 - L0)(L2 - L1) = g02 g12, so
+// w_l = -2 sin(phi_l / 2) / D_l and S = delta_ba + sum_l N_l w_l (sin + i cos)(phi_l / 2).
 __device__ __forceinline__ float amplitude2_32(const Pt32 &c, const Ch32 &h, float A, float L1, float L2, float g01,
                                               float g02, float g12, float h1, float h2) {
-    const float inv = rcp_approx(g01 * g02 * g12);
-    const float iD1 = 2.0f * g02 * inv, iD2 = -2.0f * g01 * inv;
+    float s1, k1, s2, k2;
+    __sincosf(h1, &s1, &k1);
+    __sincosf(h2, &s2, &k2);
+    const float inv2 = 2.0f * rcp_approx(g01 * g02 * g12);
+    const float w1 = (g02 * s1) * inv2, w2 = (g01 * s2) * -inv2;
     const float TA = c.T0 + A;
     const float c1 = fmaf(A, c.smt, c.c10);
     const float Kr = fmaf(A, fmaf(A, h.ee, h.Zr), h.Yr), Ki = fmaf(A, h.Zi, h.Yi);
     const float Gr = fmaf(A, h.ee, h.Xr), Gi = h.Xi;
     float sg, pp;
     sg = TA - L1; pp = fmaf(-L1, sg, c1);
-    const float C1r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD1, C1i = fmaf(-sg, Gi, Ki) * iD1;
+    const float u1 = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * w1, v1 = fmaf(-sg, Gi, Ki) * w1;
     sg = TA - L2; pp = fmaf(-L2, sg, c1);
-    const float C2r = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * iD2, C2i = fmaf(-sg, Gi, Ki) * iD2;
-    float s1, k1, s2, k2;
-    __sincosf(h1, &s1, &k1);
-    __sincosf(h2, &s2, &k2);
-    const float a1 = s1 * s1, b1 = s1 * k1, a2 = s2 * s2, b2 = s2 * k2;
-    // S = delta_ba + sum_l C'_l (a_l + i b_l), C'_l = -2 C_l
-    const float Sr = h.diag + fmaf(C1r, a1, -C1i * b1) + fmaf(C2r, a2, -C2i * b2);
-    const float Si = fmaf(C1r, b1, C1i * a1) + fmaf(C2r, b2, C2i * a2);
+    const float u2 = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * w2, v2 = fmaf(-sg, Gi, Ki) * w2;
+    // S = delta_ba + sum_l (u_l + i v_l)(s_l + i k_l)
+    const float Sr = fmaf(u1, s1, fmaf(-v1, k1, fmaf(u2, s2, fmaf(-v2, k2, h.diag))));
+    const float Si = fmaf(u1, k1, fmaf(v1, s1, fmaf(u2, k2, v2 * s2)));
     return fmaf(Sr, Sr, Si * Si);
 }
 
@@ -163,10 +175,11 @@ __device__ __forceinline__ float amplitude2_32(const Pt32 &c, const Ch32 &h, flo
 // trigonometric seed, then one Newton step on each lower root's shifted cubic;
 // the top shift follows from the trace (sum of shifts = A).
 __device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
-    float m0, m1, t3;
-    seed_roots32(c, A, m0, m1, t3);
-    dl0 = shifted_newton(t3 + m0 - c.d0, A, c.S0, c.PI0, c.W0, c.E0);
-    dl1 = shifted_newton(t3 + m1 - c.d1, A, c.S1, c.PI1, c.W1, c.E1);
+    float m0, m1;
+    seed_scaled32(c, A, m0, m1);
+    // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) + m_l
+    dl0 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td0) + m0, A, c.S0, c.PI0, c.W0, c.E0);
+    dl1 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td1) + m1, A, c.S1, c.PI1, c.W1, c.E1);
     dl2 = A - dl0 - dl1;
 }
 
