@@ -189,10 +189,12 @@ __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A
     float dl0, dl1, dl2;
     shifts32(c, A, dl0, dl1, dl2);
     const float L1 = c.d1 + dl1, L2 = c.d2 + dl2;
-    const float g01 = c.g01 + (dl0 - dl1), g02 = c.g02 + (dl0 - dl2), g12 = c.g12 + (dl1 - dl2);
+    // shift differences relative to root 0, shared by the gaps and the phases
+    const float dd1 = dl1 - dl0, dd2 = dl2 - dl0;
+    const float g01 = c.g01 - dd1, g02 = c.g02 - dd2, g12 = c.g12 + (dd1 - dd2);
     // half phases relative to root 0: pi * revolutions
-    const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dl1 - dl0);
-    const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dl2 - dl0);
+    const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dd1);
+    const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dd2);
     return amplitude2_32(c, h, A, L1, L2, g01, g02, g12, 3.14159265358979323846f * f1,
                          3.14159265358979323846f * f2);
 }
