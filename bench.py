@@ -44,8 +44,11 @@ FLUSH_BYTES = 256 << 20
 
 # Algorithmic FP32 operations per (event, point) of the FP32-bulk path, counted
 # from osc_math.cuh / osc_kernels.cuh (FMA = 2, add/mul = 1; transcendental and
-# reciprocal calls counted separately as SFU operations, conversions not counted).
-FP32_FLOP_PER_EVPT = 173
+# reciprocal calls counted separately as SFU operations -- 12 per event-point --,
+# conversions, comparisons, selects and integer work not counted): event terms 11,
+# matter shifts 75 (seed 43, two Newton steps 30, trace 2), gaps and phases 32,
+# amplitude 60, weight and bin 4.
+FP32_FLOP_PER_EVPT = 182
 SFU_PER_EVPT = 11
 
 

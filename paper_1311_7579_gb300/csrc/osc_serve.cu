@@ -107,8 +107,10 @@ struct osc_serve {
     std::deque<Request> pending;
     std::unordered_map<uint64_t, Result> results;
     uint64_t next_ticket = 1;
-    int32_t inflight = 0;
-    bool stop = false;
+    int32_t inflight = 0;                 // scheduler thread only
+    bool stop = false;                    // under mu
+    std::atomic<bool> stop_flag{false};   // the same, for the scheduler's lock-free polling
+    std::atomic<int64_t> n_pending{0};    // requests in the pending queue
     std::string thread_error;
     Batch batch[kBatches];
     std::thread th;
@@ -248,6 +250,7 @@ osc_status launch_batch(osc_serve *sv, Batch &b) {
 void fail_inflight(osc_serve *sv, const std::string &what) {
     sv->thread_error = what;
     sv->stop = true;
+    sv->stop_flag.store(true);
     for (auto &b : sv->batch) {
         sv->inflight -= (int32_t)b.reqs.size();
         b.reqs.clear();
@@ -256,24 +259,32 @@ void fail_inflight(osc_serve *sv, const std::string &what) {
     sv->cv_done.notify_all();
 }
 
+// The scheduler thread.  Batch state (busy, reqs, seq) and the in-flight count
+// belong to this thread; the lock guards only what other threads touch: the
+// pending queue, the results and the stop state.  Polling reads the completion
+// flags and the atomic count of pending requests without the lock, so waiting
+// submitters and waiters are never held off by the spinning thread.
 void scheduler(osc_serve *sv) {
     cudaSetDevice(sv->ctx->device);
-    std::unique_lock<std::mutex> lk(sv->mu);
     uint64_t polls = 0;
     Clock::time_point idle_since = Clock::now();
     for (;;) {
         // 1. publish finished batches
-        bool any_busy = false, published = false;
+        Batch *done[kBatches];
+        int n_done = 0;
+        bool any_busy = false;
         for (auto &b : sv->batch) {
             if (!b.busy) continue;
-            if (batch_done(b)) {
-                publish(sv, b);
-                published = true;
-            } else {
+            if (batch_done(b))
+                done[n_done++] = &b;
+            else
                 any_busy = true;
-            }
         }
-        if (published) {
+        if (n_done) {
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                for (int k = 0; k < n_done; ++k) publish(sv, *done[k]);
+            }
             sv->cv_done.notify_all();
             idle_since = Clock::now();
         }
@@ -284,52 +295,63 @@ void scheduler(osc_serve *sv) {
                 if (!b.busy) continue;
                 const cudaError_t e = cudaStreamQuery(b.stream);
                 if (e == cudaErrorNotReady) continue;
+                std::string what;
                 if (e != cudaSuccess) {
                     cudaGetLastError();
-                    fail_inflight(sv, std::string("serving batch: ") + cudaGetErrorString(e));
-                    any_busy = false;
+                    what = std::string("serving batch: ") + cudaGetErrorString(e);
                 } else if (!batch_done(b)) {
-                    fail_inflight(sv, "serving batch finished without its completion flag");
+                    what = "serving batch finished without its completion flag";
+                }
+                if (!what.empty()) {
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    fail_inflight(sv, what);
                     any_busy = false;
                 }
                 break;
             }
         }
-        if (sv->stop && !any_busy) break;
+        const bool stopping = sv->stop_flag.load();
+        if (stopping && !any_busy) break;
         // 2. admit one batch: a free slot, up to the free request slots, one precision per batch
-        if (!sv->stop && !sv->pending.empty() && sv->inflight < sv->max_slots) {
-            Batch *free_b = nullptr;
-            for (auto &b : sv->batch)
-                if (!b.busy) {
-                    free_b = &b;
-                    break;
-                }
-            if (free_b) {
+        Batch *free_b = nullptr;
+        for (auto &b : sv->batch)
+            if (!b.busy) {
+                free_b = &b;
+                break;
+            }
+        if (!stopping && free_b && sv->n_pending.load() > 0 && sv->inflight < sv->max_slots) {
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
                 const int take_max = sv->max_slots - sv->inflight;
-                const int prec = sv->pending.front().prec;
+                const int prec = sv->pending.empty() ? 0 : sv->pending.front().prec;
                 while ((int)free_b->reqs.size() < take_max && !sv->pending.empty() &&
                        sv->pending.front().prec == prec) {
                     free_b->reqs.push_back(sv->pending.front());
                     sv->pending.pop_front();
                 }
+                sv->n_pending.fetch_sub((int64_t)free_b->reqs.size());
+            }
+            if (!free_b->reqs.empty()) {
                 sv->inflight += (int32_t)free_b->reqs.size();
                 free_b->busy = true;
-                lk.unlock();
                 const osc_status st = launch_batch(sv, *free_b);
-                lk.lock();
-                if (st != OSC_OK) fail_inflight(sv, sv->ctx->err);
+                if (st != OSC_OK) {
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    fail_inflight(sv, sv->ctx->err);
+                }
                 continue;
             }
         }
         // 3. poll while work is in flight or queued, or shortly after the last
         //    batch; otherwise sleep until a request arrives
-        if (any_busy || !sv->pending.empty() || Clock::now() - idle_since < kIdleSpin) {
-            lk.unlock();
+        if (any_busy || sv->n_pending.load() > 0 || Clock::now() - idle_since < kIdleSpin) {
             std::this_thread::yield();
-            lk.lock();
             continue;
         }
-        sv->cv.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
+        }
         idle_since = Clock::now();
     }
 }
@@ -440,6 +462,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
         r.ticket = sv->next_ticket++;
         r.t_submit = Clock::now();
         sv->pending.push_back(r);
+        sv->n_pending.fetch_add(1);
         *ticket = r.ticket;
     }
     sv->cv.notify_all();
@@ -472,6 +495,8 @@ osc_status osc_serve_stop(osc_ctx *ctx) {
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
+        sv->stop_flag.store(true);
+        sv->n_pending.fetch_sub((int64_t)sv->pending.size());
         sv->pending.clear();
     }
     sv->cv.notify_all();
