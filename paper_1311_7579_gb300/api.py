@@ -240,6 +240,38 @@ def osc_histogram_point(ctx, sample_ids, point, prec, lo, hi, nbins, out=None):
     return out
 
 
+class PointHistogram:
+    """``osc_histogram_point`` with its arguments marshalled once, for a caller
+    that evaluates many points on the same samples, range and output buffer (a
+    fit).  ``point`` is a writable float64[8] view of the point that the next
+    call sends (the fields of ``osc_point`` in order); ``call(p)`` copies ``p``
+    there first, ``call()`` sends it as it stands.  Each call writes the
+    histograms into ``out`` (n_samples, 1, nbins) and returns it.  Like the C
+    call, an instance is not safe to use from two threads at once."""
+
+    def __init__(self, ctx, sample_ids, prec, lo, hi, nbins, out=None):
+        ids, n_ids = _ids(sample_ids)
+        if out is None:
+            out = np.zeros((n_ids, 1, int(nbins)))
+        self.out = out
+        self._ctx = ctx
+        self._ids = ids
+        self._buf = (ctypes.c_double * 8)()
+        self.point = np.ctypeslib.as_array(self._buf)
+        self._fn = lib().osc_histogram_point
+        self._args = (ctx, ids, ctypes.c_int32(n_ids), ctypes.cast(self._buf, ctypes.POINTER(OscPoint)),
+                      ctypes.c_int(PRECISIONS[prec]), ctypes.c_double(float(lo)), ctypes.c_double(float(hi)),
+                      ctypes.c_int32(int(nbins)), ctypes.c_void_p(_ptr(out)), ctypes.c_int(1 if _is_device(out) else 0))
+
+    def __call__(self, point=None):
+        if point is not None:
+            self.point[:] = point
+        status = self._fn(*self._args)
+        if status != OSC_OK:
+            _check(self._ctx, status)
+        return self.out
+
+
 def osc_histogram_bin_centre(ctx, sample_ids, point_begin, n_points, prec, t_lo, t_hi, t_nbins, lo, hi, nbins,
                              out=None):
     """Binned-method histograms (probability at the centre of each event's

@@ -119,22 +119,40 @@ __device__ __forceinline__ cplx64 pmns_entry(const double *t, int f, int m) {
     return {fma(bs, cd, ax * ay), bs * (g * sd)};
 }
 
+// Barrier of warps 0 and 1 only (named barrier id 1..15; warps 2, 3 never wait).
+__device__ __forceinline__ void pair_barrier(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
 // One block of four warps (one per scheduler) per point.  FP64 runs at a small
 // fraction of the FP32 rate on this GPU: a warp instruction occupies its
-// scheduler's FP64 unit for many cycles whatever the number of active lanes, so
-// the kernel's latency is the number of FP64 instructions on its longest path.
-// Independent work therefore runs on different warps, and parallel work as one
-// instruction stream over lanes with per-lane operands (never as divergent
-// branches, which would issue each path in turn):
-//   1. warp 0 lanes 0-5: the six square roots | warp 1 lanes 0-1: sin, cos delta
-//      | warp 2 lanes 0-1: shifted-cubic constants of sorted root lane (from the
-//      sorted vacuum spectrum and |U_e|^2 = products of the s^2 inputs)
-//      | warp 3: sorted spectrum, gaps, float-float differences, T0, c1(0), systematics
-//   2. warp 0 lanes 0-8: one PMNS entry each
-//   3. warp 0 lanes 0-8: one entry each of H0 = U diag(m) U^dagger and H0^2
-//      | warp 2 lanes 1-9: U with its columns in the sorted vacuum order
-//   4. warp 0 lanes 0-8: one channel each | warp 2 lanes 0-4: one
-//      depressed-cubic coefficient each
+// scheduler's FP64 unit for many cycles whatever the number of active lanes, and
+// a dependent one waits about a hundred cycles, so the kernel's latency is the
+// number of FP64 instructions on its longest path.  Independent work therefore
+// runs on different warps, and parallel work as one instruction stream over
+// lanes with per-lane operands (never as divergent branches, which would issue
+// each path in turn).  Only the chain s^2, delta -> U -> H0, H0^2 -> channel
+// fields needs barriers; it runs on warps 0 and 1, which wait for each other
+// alone, while warps 2 and 3 write everything that depends on the inputs
+// directly and never wait:
+//   warp 0 lanes 0-5: the six square roots | warp 1 lanes 0-1: sin, cos delta
+//   -- barrier --
+//   warp 0 lanes 0-8: one PMNS entry each
+//   -- barrier --
+//   warp 0 lanes 0-8: one entry each of H0 = U diag(m) U^dagger and H0^2
+//   | warp 1 lanes 0-8: U with its columns in the sorted vacuum order
+//   -- barrier --
+//   warps 0, 1 lanes 0-26: one field of one channel each
+// | warp 2 lanes 0-1: shifted-cubic constants of sorted root lane (from the
+//   sorted vacuum spectrum and |U_e|^2 = products of the s^2 inputs), then
+//   lanes 0-4: one depressed-cubic coefficient each
+// | warp 3 lanes 0-13: one each of the sorted spectrum, gaps (float-float
+//   differences), T0, c1(0), T0 / 3 - d0,1 and the systematics.
+// The cubic's coefficients need two invariants of H0 besides T0 and c1(0), and
+// both follow from the s^2 inputs alone (the eigenvalues in matter depend on U
+// only through |U_e|^2):
+//   smt = H0_mumu + H0_tautau = T0 - H0_ee,  H0_ee = dm21 |U_e2|^2 + dm31 |U_e3|^2,
+//   mee = H0_mumu H0_tautau - |H0_mutau|^2 = (adj H0)_ee = dm21 dm31 |U_e1|^2,
+// since adj(U D U^dagger) = U adj(D) U^dagger and adj(diag(0, dm21, dm31)) =
+// diag(dm21 dm31, 0, 0); written this way neither carries a cancellation.
 constexpr int kConstThreads = 128;
 __device__ inline void point_consts_block(const osc_point &P, float *c32, double *c64) {
     __shared__ double t[8];
@@ -148,125 +166,140 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
     // inverted dm31, 0, dm21) and the matching |U_e|^2
     const bool no = dm31 > 0;
     const double d0 = no ? 0.0 : dm31, d1 = no ? dm21 : 0.0, d2 = no ? dm31 : dm21;
-    if (warp == 0 && lane < 6) {
-        const double x = (lane == 0) ? P.s2_12 : (lane == 1) ? 1.0 - P.s2_12 : (lane == 2) ? P.s2_13
-                       : (lane == 3) ? 1.0 - P.s2_13 : (lane == 4) ? P.s2_23 : 1.0 - P.s2_23;
-        t[lane] = sqrt(x);
-    }
-    if (warp == 1 && lane < 2) {
-        double sn, cs;
-        sincos_lanes(P.dcp, lane, &sn, &cs);
-        if (lane == 0) {
-            t[6] = sn;
-            t[7] = cs;
+    if (warp <= 1) {
+        if (warp == 0 && lane < 6) {
+            const double x = (lane == 0) ? P.s2_12 : (lane == 1) ? 1.0 - P.s2_12 : (lane == 2) ? P.s2_13
+                           : (lane == 3) ? 1.0 - P.s2_13 : (lane == 4) ? P.s2_23 : 1.0 - P.s2_23;
+            t[lane] = sqrt(x);
         }
-    }
-    if (warp == 2 && lane < 2) {
-        // sorted root l = lane and the other two j, k: a_j = d_l - d_j, a_k = d_l - d_k
+        if (warp == 1 && lane < 2) {
+            double sn, cs;
+            sincos_lanes(P.dcp, lane, &sn, &cs);
+            if (lane == 0) {
+                t[6] = sn;
+                t[7] = cs;
+            }
+        }
+        pair_barrier(1);
+        if (warp == 0 && lane < 9) Us[lane] = pmns_entry(t, lane / 3, lane % 3);
+        pair_barrier(2);
+        if (warp == 0 && lane < 9) {
+            // entry (b, a) of H0 and H0^2: sum over the mass columns 1, 2 (column 0 carries m = 0)
+            const int b = lane / 3, a = lane % 3;
+            const double m[3] = {0.0, dm21, dm31};
+            cplx64 h = {0, 0}, h2 = {0, 0};
+            for (int k = 1; k < 3; ++k) {
+                const cplx64 q = cmul_conj(Us[3 * b + k], m[k], Us[3 * a + k]);
+                h.re += q.re; h.im += q.im;
+                h2.re += q.re * m[k]; h2.im += q.im * m[k];
+            }
+            Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
+        }
+        if (warp == 1 && lane < 9) {
+            // PMNS entry U[f][m] with its mass column m in the sorted vacuum order,
+            // for the mass-basis propagation through layered matter
+            const int f = lane / 3, l = lane % 3;
+            const int m = no ? l : (l + 2) % 3;
+            const cplx64 u = Us[3 * f + m];
+            c32[C32_LU + 2 * lane] = (float)u.re;
+            c32[C32_LU + 2 * lane + 1] = (float)u.im;
+            c64[C64_LU + 2 * lane] = u.re;
+            c64[C64_LU + 2 * lane + 1] = u.im;
+        }
+        pair_barrier(3);
+        if (lane < 27) {
+            // channel (alpha -> beta) = ch (alpha * 3 + beta), field j of
+            // (Xr, Xi, Yr, Yi, Zr, Zi) with X = M0_ba, Y = (M0^2)_ba,
+            // Z = M0_be [alpha = e] + [beta = e] M0_ea: one field per lane of warps 0, 1
+            const int ch = lane / 3, j = 3 * warp + lane % 3;
+            const int a = ch / 3, b = ch % 3;
+            const int cmp = j < 4 ? j : j - 4;
+            const double z = (a == 0 ? Hs[cmp][3 * b] : 0.0) + (b == 0 ? Hs[cmp][a] : 0.0);
+            const double v = j < 4 ? Hs[cmp][3 * b + a] : z;
+            c32[C32_CH + 6 * ch + j] = (float)v;
+            c64[C64_CH + 6 * ch + j] = v;
+        }
+    } else if (warp == 2) {
+        // |U_e1|^2, |U_e2|^2, |U_e3|^2 and their sorted-order counterparts
         const double ze0 = (1.0 - P.s2_12) * (1.0 - P.s2_13), ze1 = P.s2_12 * (1.0 - P.s2_13), ze2 = P.s2_13;
-        const double z0 = no ? ze0 : ze2, z1 = no ? ze1 : ze0, z2 = no ? ze2 : ze1;
-        const double dl = lane ? d1 : d0, dj = lane ? d2 : d1, dk = lane ? d0 : d2;
-        const double zl = lane ? z1 : z0, zj = lane ? z2 : z1, zk = lane ? z0 : z2;
-        const double aj = dl - dj, ak = dl - dk;
-        const int o = lane ? (C32_S1 - C32_S0) : 0;
-        const double S = aj + ak, PI = aj * ak, W = zl * (aj + ak) + zj * ak + zk * aj, E = zl * aj * ak;
-        c32[C32_S0 + o] = (float)S;
-        c32[C32_PI0 + o] = (float)PI;
-        c32[C32_W0 + o] = (float)W;
-        c32[C32_E0 + o] = (float)E;
-        c64[C64_SH + 4 * lane] = S;
-        c64[C64_SH + 4 * lane + 1] = PI;
-        c64[C64_SH + 4 * lane + 2] = W;
-        c64[C64_SH + 4 * lane + 3] = E;
-    }
-    if (warp == 3 && lane == 0) {
-        c32[C32_D0] = (float)d0; c32[C32_D1] = (float)d1; c32[C32_D2] = (float)d2;
-        c64[C64_LD] = d0; c64[C64_LD + 1] = d1; c64[C64_LD + 2] = d2;
-        c64[C64_VG] = d1 - d0; c64[C64_VG + 1] = d2 - d0; c64[C64_VG + 2] = d1 - d2;
-        c32[C32_G01] = (float)(d0 - d1); c32[C32_G02] = (float)(d0 - d2); c32[C32_G12] = (float)(d1 - d2);
-        split_ff(d1 - d0, &c32[C32_V1H], &c32[C32_V1L]);
-        split_ff(d2 - d0, &c32[C32_V2H], &c32[C32_V2L]);
-        c32[C32_T0] = (float)T0; c32[C32_C10] = (float)c10;
-        c32[C32_TD0] = (float)(T0 / 3.0 - d0); c32[C32_TD1] = (float)(T0 / 3.0 - d1);
-        c64[C64_T0] = T0; c64[C64_C10] = c10;
-        c32[C32_ESCALE] = (float)P.escale;
-        c64[C64_ESCALE] = P.escale;
-        c64[C64_NORM] = P.norm;
-    }
-    __syncthreads();
-    if (warp == 0 && lane < 9) Us[lane] = pmns_entry(t, lane / 3, lane % 3);
-    __syncthreads();
-    if (warp == 0 && lane < 9) {
-        // entry (b, a) of H0 and H0^2: sum over the mass columns 1, 2 (column 0 carries m = 0)
-        const int b = lane / 3, a = lane % 3;
-        const double m[3] = {0.0, dm21, dm31};
-        cplx64 h = {0, 0}, h2 = {0, 0};
-        for (int k = 1; k < 3; ++k) {
-            const cplx64 q = cmul_conj(Us[3 * b + k], m[k], Us[3 * a + k]);
-            h.re += q.re; h.im += q.im;
-            h2.re += q.re * m[k]; h2.im += q.im * m[k];
+        if (lane < 2) {
+            // sorted root l = lane and the other two j, k: a_j = d_l - d_j, a_k = d_l - d_k
+            const double z0 = no ? ze0 : ze2, z1 = no ? ze1 : ze0, z2 = no ? ze2 : ze1;
+            const double dl = lane ? d1 : d0, dj = lane ? d2 : d1, dk = lane ? d0 : d2;
+            const double zl = lane ? z1 : z0, zj = lane ? z2 : z1, zk = lane ? z0 : z2;
+            const double aj = dl - dj, ak = dl - dk;
+            const int o = lane ? (C32_S1 - C32_S0) : 0;
+            const double S = aj + ak, PI = aj * ak, W = zl * (aj + ak) + zj * ak + zk * aj, E = zl * aj * ak;
+            c32[C32_S0 + o] = (float)S;
+            c32[C32_PI0 + o] = (float)PI;
+            c32[C32_W0 + o] = (float)W;
+            c32[C32_E0 + o] = (float)E;
+            c64[C64_SH + 4 * lane] = S;
+            c64[C64_SH + 4 * lane + 1] = PI;
+            c64[C64_SH + 4 * lane + 2] = W;
+            c64[C64_SH + 4 * lane + 3] = E;
         }
-        Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
-    }
-    if (warp == 2 && lane >= 1 && lane <= 9) {
-        // PMNS entry U[f][m] with its mass column m in the sorted vacuum order,
-        // for the mass-basis propagation through layered matter
-        const int f = (lane - 1) / 3, l = (lane - 1) % 3;
-        const int m = no ? l : (l + 2) % 3;
-        const cplx64 u = Us[3 * f + m];
-        c32[C32_LU + 2 * (lane - 1)] = (float)u.re;
-        c32[C32_LU + 2 * (lane - 1) + 1] = (float)u.im;
-        c64[C64_LU + 2 * (lane - 1)] = u.re;
-        c64[C64_LU + 2 * (lane - 1) + 1] = u.im;
-    }
-    __syncthreads();
-    if (warp == 0 && lane < 9) {
-        // channel (alpha -> beta) = lane (alpha * 3 + beta):
-        // X = M0_ba, Y = (M0^2)_ba, Z = M0_be [alpha = e] + [beta = e] M0_ea
-        const int a = lane / 3, b = lane % 3;
-        const int o = 6 * lane;
-        const double Zr = (a == 0 ? Hs[0][3 * b] : 0.0) + (b == 0 ? Hs[0][a] : 0.0);
-        const double Zi = (a == 0 ? Hs[1][3 * b] : 0.0) + (b == 0 ? Hs[1][a] : 0.0);
-        const int ba = 3 * b + a;
-        const double v[6] = {Hs[0][ba], Hs[1][ba], Hs[2][ba], Hs[3][ba], Zr, Zi};
-        for (int k = 0; k < 6; ++k) {
-            c32[C32_CH + o + k] = (float)v[k];
-            c64[C64_CH + o + k] = v[k];
+        if (lane < 5) {
+            // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
+            //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee;
+            // lane j forms coefficient j of (p0, p1, q0, q1, q2) as one weighted sum
+            //   w3 T0^3 + w2 T0^2 + w1 T0 + wc c10 + wct c10 T0 + ws smt + wst smt T0 - [j = 3] mee
+            constexpr double k3 = 1.0 / 3.0, k9 = 1.0 / 9.0, k27 = 1.0 / 27.0;
+            const double smt = T0 - fma(dm21, ze1, dm31 * ze2);
+            const double mee = c10 * ze0;
+            const double w3 = lane == 2 ? -2.0 * k27 : 0.0;
+            const double w2 = lane == 0 ? -k3 : lane == 3 ? -2.0 * k9 : 0.0;
+            const double w1 = lane == 1 ? -2.0 * k3 : lane == 4 ? -2.0 * k9 : 0.0;
+            const double wc = lane == 0 ? 1.0 : lane == 3 ? k3 : 0.0;
+            const double wct = lane == 2 ? k3 : 0.0;
+            const double ws = lane == 1 ? 1.0 : lane == 4 ? k3 : 0.0;
+            const double wst = lane == 3 ? k3 : 0.0;
+            const double wm = lane == 3 ? -1.0 : 0.0;
+            const double T2 = T0 * T0;
+            double v = wm * mee;
+            v = fma(wst, smt * T0, v);
+            v = fma(ws, smt, v);
+            v = fma(wct, c10 * T0, v);
+            v = fma(wc, c10, v);
+            v = fma(w1, T0, v);
+            v = fma(w2, T2, v);
+            v = fma(w3, T2 * T0, v);
+            const int o32 = lane == 0 ? C32_P0 : lane == 1 ? C32_P1 : lane == 2 ? C32_Q0 : lane == 3 ? C32_Q1 : C32_Q2;
+            const int o64 = lane == 0 ? C64_P0 : lane == 1 ? C64_P1 : lane == 2 ? C64_Q0 : lane == 3 ? C64_Q1 : C64_Q2;
+            // FP32 seed coefficients of -p/3 and -q/2 (the forms the seed uses)
+            c32[o32] = (float)(v * (lane < 2 ? -1.0 / 3.0 : -0.5));
+            c64[o64] = v;
+            if (lane == 0) {
+                c32[C32_SMT] = (float)smt;
+                c64[C64_SMT] = smt;
+            }
         }
-    }
-    if (warp == 2 && lane < 5) {
-        // depressed cubic mu^3 + p mu + q, lambda = mu + (T0 + A) / 3:
-        //   p = c1 - c2^2/3, q = -2 c2^3/27 + c1 c2 / 3 - c0, c2 = T0 + A, c1 = c10 + A smt, c0 = A mee;
-        // lane j forms coefficient j of (p0, p1, q0, q1, q2) as one weighted sum
-        //   w3 T0^3 + w2 T0^2 + w1 T0 + wc c10 + wct c10 T0 + ws smt + wst smt T0 - [j = 3] mee
-        constexpr double k3 = 1.0 / 3.0, k9 = 1.0 / 9.0, k27 = 1.0 / 27.0;
-        const double smt = Hs[0][4] + Hs[0][8];
-        const double mee = fma(Hs[0][4], Hs[0][8], -fma(Hs[0][5], Hs[0][5], Hs[1][5] * Hs[1][5]));
-        const double w3 = lane == 2 ? -2.0 * k27 : 0.0;
-        const double w2 = lane == 0 ? -k3 : lane == 3 ? -2.0 * k9 : 0.0;
-        const double w1 = lane == 1 ? -2.0 * k3 : lane == 4 ? -2.0 * k9 : 0.0;
-        const double wc = lane == 0 ? 1.0 : lane == 3 ? k3 : 0.0;
-        const double wct = lane == 2 ? k3 : 0.0;
-        const double ws = lane == 1 ? 1.0 : lane == 4 ? k3 : 0.0;
-        const double wst = lane == 3 ? k3 : 0.0;
-        const double wm = lane == 3 ? -1.0 : 0.0;
-        const double T2 = T0 * T0;
-        double v = wm * mee;
-        v = fma(wst, smt * T0, v);
-        v = fma(ws, smt, v);
-        v = fma(wct, c10 * T0, v);
-        v = fma(wc, c10, v);
-        v = fma(w1, T0, v);
-        v = fma(w2, T2, v);
-        v = fma(w3, T2 * T0, v);
-        const int o32 = lane == 0 ? C32_P0 : lane == 1 ? C32_P1 : lane == 2 ? C32_Q0 : lane == 3 ? C32_Q1 : C32_Q2;
-        const int o64 = lane == 0 ? C64_P0 : lane == 1 ? C64_P1 : lane == 2 ? C64_Q0 : lane == 3 ? C64_Q1 : C64_Q2;
-        // FP32 seed coefficients of -p/3 and -q/2 (the forms the seed uses)
-        c32[o32] = (float)(v * (lane < 2 ? -1.0 / 3.0 : -0.5));
-        c64[o64] = v;
-        if (lane == 0) {
-            c32[C32_SMT] = (float)smt;
-            c64[C64_SMT] = smt;
+    } else if (lane < 14) {
+        // warp 3: one value per lane, x = a s - b: the sorted spectrum, its gaps
+        // (two as float-float), T0, c1(0), T0 / 3 - d0, T0 / 3 - d1 and the
+        // systematics; o64 / o32 are its FP64 / FP32 slots (-1: none)
+        const double a = lane == 0 || lane == 6 || lane == 7 ? d0
+                       : lane == 1 || lane == 3 || lane == 5 ? d1
+                       : lane == 2 || lane == 4            ? d2
+                       : lane == 9                         ? c10
+                       : lane == 12                        ? P.escale
+                       : lane == 13                        ? P.norm
+                                                           : T0;
+        const double b = lane == 3 || lane == 4 || lane == 10 ? d0
+                       : lane == 6 || lane == 11            ? d1
+                       : lane == 5 || lane == 7             ? d2
+                                                            : 0.0;
+        const double x = fma(a, (lane == 10 || lane == 11) ? 1.0 / 3.0 : 1.0, -b);
+        const int o64 = lane <= 2 ? C64_LD + lane : (lane >= 3 && lane <= 5) ? C64_VG + lane - 3
+                      : lane == 8 ? C64_T0 : lane == 9 ? C64_C10 : lane == 12 ? C64_ESCALE : lane == 13 ? C64_NORM : -1;
+        const int o32 = lane <= 2 ? C32_D0 + lane : lane == 3 ? C32_V1H : lane == 4 ? C32_V2H : lane == 5 ? C32_G12
+                      : lane == 6 ? C32_G01 : lane == 7 ? C32_G02 : lane == 8 ? C32_T0 : lane == 9 ? C32_C10
+                      : lane == 10 ? C32_TD0 : lane == 11 ? C32_TD1 : lane == 12 ? C32_ESCALE : -1;
+        if (o64 >= 0) c64[o64] = x;
+        if (lane == 3 || lane == 4) {
+            split_ff(x, &c32[o32], &c32[lane == 3 ? C32_V1L : C32_V2L]);
+        } else if (o32 >= 0) {
+            c32[o32] = (float)x;
         }
     }
 }

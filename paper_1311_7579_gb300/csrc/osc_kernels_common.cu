@@ -13,8 +13,12 @@ __global__ void __launch_bounds__(kConstThreads) k_point_consts(const osc_point 
     point_consts_block(pts[i], pc32 + (int64_t)i * C32_STRIDE, pc64 + (int64_t)i * C64_STRIDE);
 }
 
+// The table is read in place from the parameter space (a grid constant): the
+// block's point is selected by a run-time index, which would otherwise make the
+// compiler copy it to the thread's stack first.
 template <int N>
-__global__ void __launch_bounds__(kConstThreads) k_point_consts_v(const PointsByValueT<N> pv, float *pc32, double *pc64) {
+__global__ void __launch_bounds__(kConstThreads)
+    k_point_consts_v(const __grid_constant__ PointsByValueT<N> pv, float *pc32, double *pc64) {
     grid_dependents_launch();
     const int i = blockIdx.x;
     if (i >= pv.n) return;
@@ -91,8 +95,10 @@ static cudaError_t launch_by_value(const osc_point *h_pts, int n, float *pc32, d
 
 cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
     if (n < 1 || n > kPointsByValue) return cudaErrorInvalidValue;
-    // a small parameter block launches faster than the full one
-    return n <= 8 ? launch_by_value<8>(h_pts, n, pc32, pc64, st) : launch_by_value<kPointsByValue>(h_pts, n, pc32, pc64, st);
+    // a small parameter block launches faster than the full one (one point: a fit step)
+    return n == 1   ? launch_by_value<1>(h_pts, n, pc32, pc64, st)
+           : n <= 8 ? launch_by_value<8>(h_pts, n, pc32, pc64, st)
+                    : launch_by_value<kPointsByValue>(h_pts, n, pc32, pc64, st);
 }
 
 cudaError_t launch_hist(int prec, int pt, const HistParams &p, int grid, cudaStream_t st) {

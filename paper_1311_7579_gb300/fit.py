@@ -83,7 +83,10 @@ class ToyFit:
             self.out = torch.zeros((1, 1, self.nbins), dtype=torch.float64).pin_memory().numpy()
         except Exception:
             self.out = np.zeros((1, 1, self.nbins))
-        self.row = self.base.copy()
+        # the step's call with its arguments marshalled once; each step writes
+        # the two fitted fields into its point buffer
+        self.call = api.PointHistogram(ctx, [sample_id], prec, lo, hi, self.nbins, out=self.out)
+        self.call.point[:] = self.base
         self.calls = 0
 
     def point(self, x):
@@ -92,8 +95,10 @@ class ToyFit:
         return row
 
     def expected(self, x):
-        self.row[2], self.row[4] = x[0], x[1]
-        api.osc_histogram_point(self.ctx, [self.sid], self.row, self.prec, self.lo, self.hi, self.nbins, out=self.out)
+        p = self.call.point
+        p[2] = x[0]
+        p[4] = x[1]
+        self.call()
         self.calls += 1
         return self.exposure * self.out[0, 0]
 

@@ -333,3 +333,42 @@ def test_histogram_point_is_set_params_plus_histogram(ctx):
     assert np.array_equal(again, api.osc_histogram(ctx, ids, 0, 1, "fp64", LO, HI, NB))
     for sid in ids:
         api.osc_unload_sample(ctx, sid)
+
+
+def test_prepared_point_histogram_matches_the_plain_call(ctx):
+    """api.PointHistogram (arguments marshalled once) gives, bitwise, the bins of
+    osc_histogram_point for each point, whether the point is passed to the call
+    or written into its point buffer; a rejected point raises and leaves the
+    output as it was."""
+    torch = pytest.importorskip("torch")
+    s1 = synth.table1_sample(20000, seed=31)
+    s2 = synth.all_channel_sample(15000, seed=32, L_km=810.0, rho=2.8)
+    ids = [api.osc_load_sample(ctx, s1), api.osc_load_sample(ctx, s2)]
+    pts = synth.scan_points(4, seed=33)
+    for prec in ("fp32", "fp64"):
+        pin = torch.zeros((2, 1, NB), dtype=torch.float64).pin_memory().numpy()
+        dev = torch.zeros((2, 1, NB), dtype=torch.float64, device="cuda")
+        calls = [api.PointHistogram(ctx, ids, prec, LO, HI, NB),
+                 api.PointHistogram(ctx, ids, prec, LO, HI, NB, out=pin),
+                 api.PointHistogram(ctx, ids, prec, LO, HI, NB, out=dev)]
+        for k in range(4):
+            ref = api.osc_histogram_point(ctx, ids, pts[k], prec, LO, HI, NB)
+            for j, call in enumerate(calls):
+                if k % 2:
+                    call.point[:] = pts[k]
+                    got = call()
+                else:
+                    got = call(pts[k:k + 1])
+                if j == 2:
+                    api.osc_sync(ctx)
+                    got = got.cpu().numpy()
+                assert np.array_equal(got, ref), (prec, k, j)
+        before = calls[1].out.copy()
+        bad = pts[0].copy()
+        bad[4] = 0.0  # dm32 = 0
+        with pytest.raises(api.OscError) as e:
+            calls[1](bad)
+        assert e.value.status == api.OSC_E_RANGE
+        assert np.array_equal(calls[1].out, before)
+    for sid in ids:
+        api.osc_unload_sample(ctx, sid)
