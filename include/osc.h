@@ -67,6 +67,15 @@ typedef enum {
     OSC_E_BUSY = 7     /* serving queue full */
 } osc_status;
 
+/* Domain of the two FP32 precisions: the matter term |A| = k_A rho Y_e E_true of
+ * every event at most 1000 |dm31| (dm31 = dm32 + dm21) of the point.  Beyond it
+ * two eigenvalues in matter form a near-double pair at the scale of the
+ * eigenvalue cubic, which FP32 cannot resolve (the error grows from ~1e-4 to
+ * O(1) between 1000 and 3000 |dm31|).  A call in an FP32 precision whose points
+ * and samples include a pair outside the domain (with the sample's largest
+ * E_true and its densest layer) therefore runs wholly in OSC_FP64: the results
+ * are the FP64 results.  Physical parameters stay far inside: through the
+ * Earth's core at 50 GeV, |A| is about 20 |dm31|. */
 typedef enum {
     OSC_FP64 = 0,         /* all-FP64 path: closed-form cubic eigenvalues, FP64 amplitude */
     OSC_FP32_BULK = 1,    /* FP32 bulk with FP64-derived per-point constants: eigenvalues as
@@ -287,7 +296,9 @@ osc_status osc_serve_stop(osc_ctx *ctx);
  * calls that overlap on the GPU (other threads, other streams) race and must
  * not be issued.
  *
- * prec is OSC_FP64 or OSC_FP32_BULK.
+ * prec is OSC_FP64 or OSC_FP32_BULK.  With OSC_FP32_BULK, an event outside the
+ * FP32 domain (see osc_precision) is found on the device and the call then runs
+ * again in OSC_FP64.
  *
  * Errors: OSC_E_ARG (null pointer, bad precision, n outside [1, 2^31 - 1],
  * nbins outside [1, 4096]), OSC_E_RANGE (invalid scalars or point; or, found

@@ -28,6 +28,8 @@ struct Sample {
     double L = 0, rho = 0, ye = 0;
     int32_t frac_bits = 96;
     uint32_t chan_mask = 0;  // bit c set when channel id c occurs in the sample
+    float e_max = 0.0f;      // largest E_true
+    double ka_max = 0.0;     // largest k_A rho Y_e over the path's layers (max |A| = ka_max e_max)
     float4 *ev = nullptr;
     int32_t *perm = nullptr;
     void *lay = nullptr;     // layered path: float4[n_layers] then double2[n_layers]
@@ -136,6 +138,11 @@ osc_status ensure_acc(osc_ctx *c, int64_t bins);
 int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items);
 bool fuse_finalize(int64_t n_hist, int32_t nbins, int32_t pt);
 int prec_kind(osc_precision p);
+// the kernel precision a call runs in: an FP32 precision with any (point,
+// sample) pair outside the FP32 domain (kFp32MatterRatio) runs in FP64
+bool fp32_in_domain(const osc_point &p, const Sample *s);
+int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
+              int32_t n_points);
 cudaEvent_t pool_event(osc_ctx *c);
 osc_status drain_timing(osc_ctx *c);
 void build_items(const std::vector<const Sample *> &ss, int32_t point_base, int32_t n_points, int32_t pt,

@@ -94,6 +94,13 @@ struct HistParams {
 
 // Points passed to the constants kernel by value (no host-to-device copy).
 constexpr int kPointsByValue = 256;
+
+// Domain of the FP32 paths: the matter term at most kFp32MatterRatio |dm31|.
+// Beyond it two eigenvalues in matter form a near-double pair at the scale of
+// the eigenvalue cubic, which FP32 constants cannot resolve (errors grow from
+// ~1e-4 to O(1) between 1e3 and 3e3); calls with a (point, sample) outside it
+// run in FP64.
+constexpr double kFp32MatterRatio = 1000.0;
 template <int N>
 struct PointsByValueT {
     int32_t n;

@@ -111,12 +111,14 @@ __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float v
 // cubic mu^3 + p mu + q (Viete's form with the arccos and cube-angle above),
 // from mp3 = -p/3 and qh = -q/2: mu = 2 r cos(theta/3 + 2 pi k/3) with
 // r = sqrt(mp3) and cos(theta) = qh / r^3.
-__device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, float &m1) {
+// Also returns cos(theta): near +-1 the angle is ill-conditioned (see near_double_pair64).
+__device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, float &m1, float &cth_out) {
     mp3 = fmaxf(mp3, 1e-30f);
     const float ir = rsqrt_approx(mp3);
     const float r = mp3 * ir;
     float cth = qh * ir * ir * ir;
     cth = fminf(fmaxf(cth, -1.0f), 1.0f);
+    cth_out = cth;
     const float th3 = acos_third(cth);
     float sn, cs;
     __sincosf(th3, &sn, &cs);
@@ -124,20 +126,52 @@ __device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, floa
     m0 = -rc - rsn;  // smallest root
     m1 = -rc + rsn;  // middle root
 }
-__device__ __forceinline__ void seed_depressed32(float p, float q, float &m0, float &m1) {
-    seed_core32(p * (-1.0f / 3.0f), -0.5f * q, m0, m1);
+__device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, float &m1) {
+    float cth;
+    seed_core32(mp3, qh, m0, m1, cth);
+}
+__device__ __forceinline__ void seed_depressed32(float p, float q, float &m0, float &m1, float &cth) {
+    seed_core32(p * (-1.0f / 3.0f), -0.5f * q, m0, m1, cth);
+}
+
+// The trigonometric seed loses a near-double pair of roots: where two roots of
+// mu^3 + p mu + q are close (gap << r = sqrt(-p/3)), cos(theta) is within
+// (gap / r)^2 of +-1, and an FP32 rounding of it moves theta, and the pair's
+// seeds, by up to r sqrt(2 eps): as much as the gap when the matter term dwarfs
+// the vacuum splittings.  Past |cos(theta)| = kNearDouble (seed error / gap up to
+// about 1e-4, which two Newton steps take to FP64 rounding) the pair is seeded
+// by deflation instead: the isolated root mi (the top one for cos(theta) > 0,
+// the bottom one otherwise) is well conditioned, so two Newton steps from its
+// FP32 seed fix it in FP64; the pair are the roots of the deflated quadratic
+// mu^2 + mi mu + (p + mi^2), whose discriminant -3 mi^2 - 4 p is the squared gap.
+// s0, s1: the FP32 seeds of the two lower roots; returns the lower two roots.
+constexpr float kNearDouble = 0.999f;
+static __device__ __noinline__ double2 near_double_pair64(double p, double q, float cth, float s0, float s1) {
+    double mi = cth > 0.0f ? -((double)s0 + (double)s1) : (double)s0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double f = fma(fma(mi, mi, p), mi, q);
+        const double fp = fma(3.0 * mi, mi, p);
+        mi -= (double)((float)f * rcp_approx((float)fp));
+    }
+    const double sq = sqrt(fmax(fma(-3.0 * mi, mi, -4.0 * p), 0.0));
+    return cth > 0.0f ? make_double2(-0.5 * (mi + sq), 0.5 * (sq - mi)) : make_double2(mi, -0.5 * (mi + sq));
 }
 
 // The same seed for the characteristic cubic of one event, from the point's
 // pre-scaled coefficients: -p/3 = P0 + P1 A + A^2/9, -q/2 = Q0 + Q1 A + Q2 A^2 + A^3/27.
-__device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1) {
+__device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1, float &cth) {
     const float mp3 = fmaf(fmaf(A, 1.0f / 9.0f, c.p1), A, c.p0);
     const float qh = fmaf(fmaf(fmaf(A, 1.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
-    seed_core32(mp3, qh, m0, m1);
+    seed_core32(mp3, qh, m0, m1, cth);
+}
+__device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1) {
+    float cth;
+    seed_scaled32(c, A, m0, m1, cth);
 }
 // As roots mu of the depressed cubic (lambda = mu + (T0 + A) / 3).
-__device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3) {
-    seed_scaled32(c, A, m0, m1);
+__device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3, float &cth) {
+    seed_scaled32(c, A, m0, m1, cth);
     t3 = (c.T0 + A) * (1.0f / 3.0f);
 }
 
@@ -311,11 +345,17 @@ __device__ __forceinline__ double shifted_step64(double dl, double b, double c, 
 __device__ __forceinline__ void shifts64(const Pt64 &c, double A, double &dl0, double &dl1, double &dl2) {
     const double p = fma(fma(A, -1.0 / 3.0, c.p1), A, c.p0);
     const double q = fma(fma(fma(A, -2.0 / 27.0, c.q2), A, c.q1), A, c.q0);
-    float s0, s1;
-    seed_depressed32((float)p, (float)q, s0, s1);
+    float s0, s1, cth;
+    seed_depressed32((float)p, (float)q, s0, s1, cth);
+    double m0 = s0, m1 = s1;
+    if (fabsf(cth) > kNearDouble) {
+        const double2 m = near_double_pair64(p, q, cth, s0, s1);
+        m0 = m.x;
+        m1 = m.y;
+    }
     const double t3 = (c.T0 + A) * (1.0 / 3.0);
-    dl0 = ((double)s0 + t3) - c.d0;
-    dl1 = ((double)s1 + t3) - c.d1;
+    dl0 = (m0 + t3) - c.d0;
+    dl1 = (m1 + t3) - c.d1;
     const double b0 = c.S0 - A, b1 = c.S1 - A;
     const double cc0 = fma(-A, c.W0, c.PI0), cc1 = fma(-A, c.W1, c.PI1);
     const double e0 = A * c.E0, e1 = A * c.E1;
@@ -368,12 +408,17 @@ __device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double
 // FP32), the top root from the zero sum of the depressed roots.
 __device__ __forceinline__ void roots_mix(const Pt32 &c, const Pt64 &c64, double Ad, double &m0, double &m1,
                                           double &m2, double &t3) {
-    float s0, s1, t3f;
-    seed_roots32(c, (float)Ad, s0, s1, t3f);
+    float s0, s1, t3f, cth;
+    seed_roots32(c, (float)Ad, s0, s1, t3f, cth);
     const double p = fma(fma(Ad, -1.0 / 3.0, c64.p1), Ad, c64.p0);
     const double q = fma(fma(fma(Ad, -2.0 / 27.0, c64.q2), Ad, c64.q1), Ad, c64.q0);
     m0 = (double)s0;
     m1 = (double)s1;
+    if (fabsf(cth) > kNearDouble) {
+        const double2 m = near_double_pair64(p, q, cth, s0, s1);
+        m0 = m.x;
+        m1 = m.y;
+    }
     m0 -= (double)((float)fma(fma(m0, m0, p), m0, q) / (float)fma(3.0 * m0, m0, p));
     m1 -= (double)((float)fma(fma(m1, m1, p), m1, q) / (float)fma(3.0 * m1, m1, p));
     m2 = -m0 - m1;

@@ -27,7 +27,7 @@ struct NoAllocScratch {
     float pc32[C32_STRIDE];
     unsigned long long acc[3 * kNoAllocMaxBins];  // bin digit columns, as in the main path
     int counter;                                  // work-item counter
-    int error;                                    // set by the kernel on an invalid event
+    int error;                                    // bit 0: an invalid event; bit 1: FP32 outside its domain
 };
 
 // The scratch array (about 97 KB).  Host code must not use this name as an
@@ -41,6 +41,7 @@ struct NoAllocParams {
     int32_t chunk, n_items;
     SampleDev sd;        // only the scalar fields are used
     float lo_f, inv_f, nb_f, w_abs_max;
+    float a_lim;         // FP32 domain: |A| <= kFp32MatterRatio |dm31|
     int32_t nbins;
     NoAllocScratch *s;
 };
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
                 }
                 float A, th, tl;
                 event_terms32(p.sd, E, ch, A, th, tl);
+                if (fabsf(A) > p.a_lim) atomicOr(&s->error, 2);  // the host re-runs the call in FP64
                 const float P = prob_fp32(c32, h32, A, th, tl);
                 acc_event_f32(r, s->acc, hp, s->pc32[C32_ESCALE], er, P * w, p.sd.frac_bits - 150, true);
             } else {
@@ -216,44 +218,57 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
     p.inv_f = (float)((double)nbins / (hi - lo));
     p.nb_f = (float)nbins;
     p.w_abs_max = (float)w_abs_max;
+    p.a_lim = (float)(kFp32MatterRatio * std::fabs(P.dm32 + P.dm21));
     p.nbins = nbins;
     p.s = s;
-    int n_sm = 0, per_sm = 1;
+    int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const void *fn = prec == OSC_FP32_BULK ? (const void *)k_noalloc_hist<kFP32> : (const void *)k_noalloc_hist<kFP64>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNT, 0);
-    per_sm = std::max(per_sm, 1);
-    const int64_t warps = (int64_t)std::max(n_sm, 1) * per_sm * (kNT / 32);
-    int64_t chunk = (n + 4 * warps - 1) / (4 * warps);
-    chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
-    p.chunk = (int32_t)chunk;
-    p.n_items = (int32_t)((n + chunk - 1) / chunk);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)n_sm * per_sm, (p.n_items + 7) / 8));
-    // Calls share the scratch and it keeps the previous call's contents: clear
-    // the accumulators, the counter and the error flag first.
-    cudaError_t e = cudaMemsetAsync(s->acc, 0, sizeof(unsigned long long) * 3 * (size_t)nbins, st);
-    if (!e) e = cudaMemsetAsync(&s->counter, 0, 2 * sizeof(int), st);
-    if (e) {
-        put_err(err, err_len, "cudaMemsetAsync on the scratch array failed");
-        return OSC_E_CUDA;
-    }
-    k_noalloc_consts<<<1, kConstThreads, 0, st>>>(P, s);
-    if (prec == OSC_FP32_BULK)
-        k_noalloc_hist<kFP32><<<grid, kNT, 0, st>>>(p);
-    else
-        k_noalloc_hist<kFP64><<<grid, kNT, 0, st>>>(p);
-    k_noalloc_final<<<(nbins + 255) / 256, 256, 0, st>>>(d_out, nbins, std::ldexp(1.0, 64 - F), std::ldexp(1.0, -F), s);
-    e = cudaGetLastError();
+    // The FP32 kernel flags events outside its domain; the call then runs again in FP64.
+    bool fp32 = prec == OSC_FP32_BULK;
     int flag = 0;
-    if (!e) e = cudaMemcpyAsync(&flag, &s->error, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (!e) e = cudaStreamSynchronize(st);
-    if (e) {
-        char buf[256];
-        std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
-        put_err(err, err_len, buf);
-        return OSC_E_CUDA;
+    for (;;) {
+        int per_sm = 1;
+        const void *fn = fp32 ? (const void *)k_noalloc_hist<kFP32> : (const void *)k_noalloc_hist<kFP64>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNT, 0);
+        per_sm = std::max(per_sm, 1);
+        const int64_t warps = (int64_t)std::max(n_sm, 1) * per_sm * (kNT / 32);
+        int64_t chunk = (n + 4 * warps - 1) / (4 * warps);
+        chunk = std::max<int64_t>(64, (chunk + 63) / 64 * 64);
+        p.chunk = (int32_t)chunk;
+        p.n_items = (int32_t)((n + chunk - 1) / chunk);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)n_sm * per_sm, (p.n_items + 7) / 8));
+        // Calls share the scratch and it keeps the previous call's contents: clear
+        // the accumulators, the counter and the error flag first.
+        cudaError_t e = cudaMemsetAsync(s->acc, 0, sizeof(unsigned long long) * 3 * (size_t)nbins, st);
+        if (!e) e = cudaMemsetAsync(&s->counter, 0, 2 * sizeof(int), st);
+        if (e) {
+            put_err(err, err_len, "cudaMemsetAsync on the scratch array failed");
+            return OSC_E_CUDA;
+        }
+        k_noalloc_consts<<<1, kConstThreads, 0, st>>>(P, s);
+        if (fp32)
+            k_noalloc_hist<kFP32><<<grid, kNT, 0, st>>>(p);
+        else
+            k_noalloc_hist<kFP64><<<grid, kNT, 0, st>>>(p);
+        k_noalloc_final<<<(nbins + 255) / 256, 256, 0, st>>>(d_out, nbins, std::ldexp(1.0, 64 - F),
+                                                              std::ldexp(1.0, -F), s);
+        e = cudaGetLastError();
+        flag = 0;
+        if (!e) e = cudaMemcpyAsync(&flag, &s->error, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaStreamSynchronize(st);
+        if (e) {
+            char buf[256];
+            std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
+            put_err(err, err_len, buf);
+            return OSC_E_CUDA;
+        }
+        if (fp32 && flag == 2) {
+            fp32 = false;
+            continue;
+        }
+        break;
     }
-    if (flag) {
+    if (flag & 1) {
         put_err(err, err_len, "invalid event (E_true <= 0 or non-finite, non-finite E_reco, |w_mc| > w_abs_max, "
                               "or bad flavour); output left unwritten");
         return OSC_E_RANGE;

@@ -97,6 +97,27 @@ osc_status debug_word_check(osc_ctx *c) {
 
 int prec_kind(osc_precision p) { return p == OSC_FP32_BULK ? kFP32 : p == OSC_FP32_F64EIG ? kMix : kFP64; }
 
+bool fp32_in_domain(const osc_point &p, const Sample *s) {
+    return s->ka_max * (double)s->e_max <= kFp32MatterRatio * std::fabs(p.dm32 + p.dm21);
+}
+
+int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
+              int32_t n_points) {
+    const int pr = prec_kind(prec);
+    if (pr == kFP64) return pr;
+    double a_max = 0.0;
+    for (int32_t i = 0; i < n_ids; ++i) {
+        const Sample *s = c->samples[ids[i]];
+        a_max = std::max(a_max, s->ka_max * (double)s->e_max);
+    }
+    const double lim = a_max / kFp32MatterRatio;
+    for (int32_t k = point_begin; k < point_begin + n_points; ++k) {
+        const osc_point &p = c->pts[k];
+        if (!(std::fabs(p.dm32 + p.dm21) >= lim)) return kFP64;
+    }
+    return pr;
+}
+
 osc_status validate_point(osc_ctx *c, const osc_point &p, int i) {
     // the message is formatted only for a rejected point (this runs once per point per call)
     const char *why = nullptr;
@@ -467,8 +488,10 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     double wsum = 0.0, wmax = 0.0;
     uint32_t mask = 0;
     std::vector<uint8_t> ch((size_t)n);
+    float e_max = 0.0f;
     for (int64_t i = 0; i < n; ++i) {
         const float e = d->e_true[i], r = d->e_reco[i], w = d->w_mc[i];
+        e_max = std::max(e_max, e);
         if (!(std::isfinite(e) && e > 0.0f)) {
             std::ostringstream o;
             o << "event " << i << ": E_true must be finite and > 0";
@@ -515,6 +538,8 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     s->ye = d->ye;
     s->frac_bits = F;
     s->chan_mask = mask;
+    s->e_max = e_max;
+    s->ka_max = matter_k_A() * d->density_gcc * d->ye;
     osc_status st = OSC_OK;
     void *p;
     if ((st = dalloc(ctx, &p, n_pad * sizeof(float4))) == OSC_OK) s->ev = (float4 *)p;
@@ -578,6 +603,8 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
     if (ctx->serve) return fail(ctx, OSC_E_STATE, "cannot change a sample's path while serving runs");
     Sample *s = it->second;
     void *lay = nullptr;
+    double ka_max = 0.0;
+    for (int k = 0; k < n_layers; ++k) ka_max = std::max(ka_max, matter_k_A() * density_gcc[k] * ye[k]);
     if (n_layers > 1) {
         std::vector<float4> l32(n_layers);
         std::vector<double2> l64(n_layers);
@@ -602,6 +629,7 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
     cudaStreamSynchronize(ctx->stream);
     dfree(ctx, s->lay);
     s->lay = lay;
+    s->ka_max = ka_max;
     SampleDev &sd = s->dev;
     if (n_layers == 1) {
         s->L = length_km[0];
@@ -770,10 +798,11 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
     rp.norm = ctx->pts[point].norm;
     rp.out_prob = dp;
     rp.out_weight = dw;
+    const int pr = call_prec(ctx, prec, &sample_id, 1, point, 1);
     if (s->dev.n_layers > 1)
-        CK(launch_reweight_layers(prec_kind(prec), rp, ctx->stream));
+        CK(launch_reweight_layers(pr, rp, ctx->stream));
     else
-        CK(launch_reweight(prec_kind(prec), rp, ctx->stream));
+        CK(launch_reweight(pr, rp, ctx->stream));
     ctx->launches += 1;
     if (!out_on_device) {
         if (out_prob) CK(cudaMemcpyAsync(out_prob, dp, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1030,7 +1059,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     std::vector<int32_t> ids(sample_ids, sample_ids + n_samples);
     for (int32_t id : ids)
         if (!ctx->samples.count(id)) return fail(ctx, OSC_E_ARG, "unknown sample id");
-    const int pr = prec_kind(prec);
+    const int pr = call_prec(ctx, prec, ids.data(), n_samples, point_begin, n_points);
     const int64_t bins = (int64_t)n_samples * n_points * nbins;
     osc_status st = ensure_acc(ctx, bins);
     if (st) return st;
@@ -1282,7 +1311,7 @@ extern "C" osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *samp
     std::vector<int32_t> ids(sample_ids, sample_ids + n_samples);
     for (int32_t id : ids)
         if (!ctx->samples.count(id)) return fail(ctx, OSC_E_ARG, "unknown sample id");
-    const int pr = prec_kind(prec);
+    const int pr = call_prec(ctx, prec, ids.data(), n_samples, point_begin, n_points);
     const int64_t bins = (int64_t)n_samples * n_points * nbins;
     osc_status st = ensure_acc(ctx, bins);
     if (st) return st;

@@ -69,6 +69,116 @@ def test_extreme_points_measured_bound(L, rho, pts):
     assert w["fp32"] <= TOL_OUTSIDE and w["fp32_f64eig"] <= TOL_OUTSIDE, w
 
 
+def _golden_worst(name, precs):
+    """Worst |P - P_exact| per precision over a 40-digit fixture, per case."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        d = json.load(f)
+    pts = np.array(d["points"])
+    out = []
+    with api.Context(0) as c:
+        api.osc_set_params(c.ptr, pts)
+        for case in d["cases"]:
+            ev = np.array(case["events"])
+            n = ev.shape[0]
+            s = {"n": n, "e_true": ev[:, 4].astype(np.float32), "e_reco": np.ones(n, np.float32),
+                 "w_mc": np.ones(n, np.float32), "flav_in": ev[:, 1].astype(np.uint8),
+                 "flav_out": ev[:, 2].astype(np.uint8), "is_nubar": ev[:, 3].astype(np.uint8),
+                 "baseline_km": case["L_km"], "density_gcc": case["density_gcc"], "ye": case["ye"]}
+            sid = api.osc_load_sample(c.ptr, s)
+            worst = {}
+            for prec in precs:
+                w = 0.0
+                for k in range(pts.shape[0]):
+                    sel = ev[:, 0] == k
+                    p = np.zeros(n)
+                    api.osc_reweight(c.ptr, sid, k, prec, out_prob=p)
+                    w = max(w, float(np.max(np.abs(p[sel] - ev[sel, 5]))))
+                worst[prec] = w
+            api.osc_unload_sample(c.ptr, sid)
+            out.append((case["L_km"], worst))
+    return out
+
+
+def test_near_double_roots_in_matter_against_40_digit_reference():
+    """Matter terms up to 0.05 eV^2 against vacuum splittings down to 1e-6 eV^2
+    (fixture written by tests/golden/make_fp64_near_double_events.py): two
+    eigenvalues in matter lie a few 1e-6 eV^2 apart on a cubic of scale 0.02,
+    where the trigonometric seed's angle is ill-conditioned.  The FP64 path
+    seeds such a pair by deflation from the isolated root and must stay at the
+    level of the inputs' rounding."""
+    for L, worst in _golden_worst("fp64_near_double_events.json", ("fp64", "fp32_f64eig", "fp32")):
+        print("near-double", L, worst)
+        assert worst["fp64"] <= 1e-12, (L, worst)
+        # the FP32 precisions: points outside their domain run in FP64 (next test),
+        # the two physical ones stay within the FP32 tolerance at these matter terms
+        assert worst["fp32"] <= 1e-4 and worst["fp32_f64eig"] <= 1e-4, (L, worst)
+
+
+K_A = 1.526493e-4  # eV^2 per GeV per g/cm^3 (k_A of the matter term)
+
+
+def test_fp32_precisions_outside_their_domain_run_in_fp64():
+    """Where the matter term exceeds 1000 |dm31| (a near-double pair of
+    eigenvalues at the cubic's scale), FP32 cannot resolve the eigenstructure, so
+    calls in OSC_FP32_BULK or OSC_FP32_F64EIG with such a (point, sample) run in
+    FP64: reweight, histogram and the no-allocation call give the FP64 results
+    bit for bit; points inside the domain keep the FP32 path."""
+    torch = pytest.importorskip("torch")
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fp64_near_double_events.json")) as f:
+        d = json.load(f)
+    pts = np.array(d["points"])
+    case = d["cases"][0]
+    ev = np.array(case["events"])
+    n = ev.shape[0]
+    s = {"n": n, "e_true": ev[:, 4].astype(np.float32), "e_reco": (ev[:, 4] * 0.1).astype(np.float32),
+         "w_mc": np.ones(n, np.float32), "flav_in": ev[:, 1].astype(np.uint8),
+         "flav_out": ev[:, 2].astype(np.uint8), "is_nubar": ev[:, 3].astype(np.uint8),
+         "baseline_km": case["L_km"], "density_gcc": case["density_gcc"], "ye": case["ye"]}
+    a_max = K_A * case["density_gcc"] * case["ye"] * float(s["e_true"].max())
+    outside = [abs(p[4] + p[3]) * 1000.0 < a_max for p in pts]
+    assert any(outside) and not all(outside)
+    with api.Context(0) as c:
+        sid = api.osc_load_sample(c.ptr, s)
+        api.osc_set_params(c.ptr, pts)
+        for k in range(len(pts)):
+            p64 = np.zeros(n)
+            api.osc_reweight(c.ptr, sid, k, "fp64", out_prob=p64)
+            h64 = api.osc_histogram(c.ptr, [sid], k, 1, "fp64", 0.0, 5.0, 50)
+            for prec in ("fp32", "fp32_f64eig"):
+                p = np.zeros(n)
+                api.osc_reweight(c.ptr, sid, k, prec, out_prob=p)
+                h = api.osc_histogram(c.ptr, [sid], k, 1, prec, 0.0, 5.0, 50)
+                if outside[k]:
+                    assert np.array_equal(p, p64) and np.array_equal(h, h64), (k, prec)
+                else:
+                    assert not np.array_equal(p, p64), (k, prec)
+        # a histogram call mixing inside and outside points runs wholly in FP64
+        hall = api.osc_histogram(c.ptr, [sid], 0, len(pts), "fp32", 0.0, 5.0, 50)
+        assert np.array_equal(hall, api.osc_histogram(c.ptr, [sid], 0, len(pts), "fp64", 0.0, 5.0, 50))
+        api.osc_unload_sample(c.ptr, sid)
+    # the no-allocation call: the FP32 kernel flags the events and the call runs again in FP64
+    dev = torch.device("cuda", 0)
+    t = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(dev) for k in
+         ("e_true", "e_reco", "w_mc", "flav_in", "flav_out", "is_nubar")}
+    for k in range(len(pts)):
+        outs = {}
+        for prec in ("fp32", "fp64"):
+            o = torch.zeros(50, dtype=torch.float64, device=dev)
+            api.osc_histogram_noalloc(t["e_true"], t["e_reco"], t["w_mc"], t["flav_in"], t["flav_out"],
+                                      t["is_nubar"], case["L_km"], case["density_gcc"], case["ye"], 2.0,
+                                      pts[k], prec, 0.0, 5.0, 50, o)
+            torch.cuda.synchronize()
+            outs[prec] = o.cpu().numpy()
+        if outside[k]:
+            assert np.array_equal(outs["fp32"], outs["fp64"]), k
+        else:
+            assert not np.array_equal(outs["fp32"], outs["fp64"]), k
+
+
 def test_fp64_against_40_digit_reference():
     """FP64 path against 40-digit values (oracle/hp.py, fixture written by
     tests/golden/make_fp64_hard_events.py) at 12000 km through 13 g/cm^3 and at
