@@ -197,3 +197,41 @@ def test_serving_layered_and_single_layer_requests(prec):
                 assert np.array_equal(h, ref), (which, k)
         finally:
             api.osc_serve_stop(c.ptr)
+
+
+def test_fp32_domain_uses_the_densest_layer_and_serving_applies_it():
+    """The FP32 domain rule (matter term at most 1000 |dm31|, else the call runs in
+    FP64) takes a layered sample's densest layer: a tiny-splitting point is
+    outside it only because of the dense middle layer, and its FP32 and
+    FP32_F64EIG results then equal FP64 bit for bit, through osc_histogram,
+    osc_reweight and served requests; a physical point keeps the FP32 path."""
+    s = synth.all_channel_sample(20_000, seed=41, L_km=6000.0, rho=1.0, e_lo=2.0, e_hi=40.0)
+    tiny = np.array([0.311, 0.0251, 0.5, 1.0e-6, 1.4e-5, 0.7, 1.0, 1.0])   # |dm31| = 1.5e-5 eV^2
+    phys = synth.table1_point()
+    pts = np.stack([tiny, phys])
+    # |A|max = k_A rho Y_e E_max: 1.526e-4 * 1.0 * 0.5 * 40 = 3.1e-3 -> 204 |dm31| for the thin
+    # layers, 12 * 204 = 2.4e3 |dm31| for the 12 g/cm^3 middle layer
+    layers = [(2000.0, 1.0, 0.5), (2000.0, 12.0, 0.5), (2000.0, 1.0, 0.5)]
+    lo, hi, nb = 0.0, 40.0, 20
+    with api.Context(0) as c:
+        sid = api.osc_load_sample(c.ptr, s)
+        api.osc_set_params(c.ptr, pts)
+        # one thin layer: inside the domain, FP32 stays FP32
+        h32 = api.osc_histogram(c.ptr, [sid], 0, 1, "fp32", lo, hi, nb)
+        assert not np.array_equal(h32, api.osc_histogram(c.ptr, [sid], 0, 1, "fp64", lo, hi, nb))
+        api.osc_set_layers(c.ptr, sid, layers)
+        h64 = api.osc_histogram(c.ptr, [sid], 0, 1, "fp64", lo, hi, nb)
+        p64, _ = _reweight(c.ptr, sid, 0, "fp64", s["n"])
+        for prec in ("fp32", "fp32_f64eig"):
+            assert np.array_equal(api.osc_histogram(c.ptr, [sid], 0, 1, prec, lo, hi, nb), h64), prec
+            assert np.array_equal(_reweight(c.ptr, sid, 0, prec, s["n"])[0], p64), prec
+        # the physical point through the same layers keeps the FP32 path
+        p32 = _reweight(c.ptr, sid, 1, "fp32", s["n"])[0]
+        assert not np.array_equal(p32, _reweight(c.ptr, sid, 1, "fp64", s["n"])[0])
+        api.osc_serve_start(c.ptr, 8, lo, hi, nb)
+        try:
+            h, _ = api.osc_wait(c.ptr, api.osc_submit(c.ptr, sid, tiny, "fp32"), nb, 20000)
+            assert np.array_equal(h, h64[0, 0])
+        finally:
+            api.osc_serve_stop(c.ptr)
+        api.osc_unload_sample(c.ptr, sid)
