@@ -74,8 +74,11 @@ typedef enum {
  * O(1) between 1000 and 3000 |dm31|).  A call in an FP32 precision whose points
  * and samples include a pair outside the domain (with the sample's largest
  * E_true and its densest layer) therefore runs wholly in OSC_FP64: the results
- * are the FP64 results.  Physical parameters stay far inside: through the
- * Earth's core at 50 GeV, |A| is about 20 |dm31|. */
+ * are the FP64 results.  Through layers (osc_set_layers) OSC_FP32_BULK also
+ * needs dm21 >= 5e-3 |dm31|: below it the FP32 seeds of the two solar roots
+ * cannot resolve their gap, which the layer update divides by.  Physical
+ * parameters stay far inside: through the Earth's core at 50 GeV, |A| is about
+ * 20 |dm31|, and dm21 is about 0.03 |dm31|. */
 typedef enum {
     OSC_FP64 = 0,         /* all-FP64 path: closed-form cubic eigenvalues, FP64 amplitude */
     OSC_FP32_BULK = 1,    /* FP32 bulk with FP64-derived per-point constants: eigenvalues as

@@ -138,9 +138,16 @@ osc_status ensure_acc(osc_ctx *c, int64_t bins);
 int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items);
 bool fuse_finalize(int64_t n_hist, int32_t nbins, int32_t pt);
 int prec_kind(osc_precision p);
+// FP32-bulk through layers also needs dm21 >= kFp32LayerSolarRatio |dm31|: with a
+// smaller solar splitting the FP32 seeds of the two solar roots (a near-double
+// pair at the cubic's scale) leave shift errors comparable to the vacuum gap,
+// which the layer update's eigenvector weights divide by (|dP| reached O(1) at
+// 1.2e-4, 1e-4 at 3e-3).  The single-layer Sylvester form stays below 1e-3 there,
+// and FP32_F64EIG (FP64 shifts) below 1.2e-5 through layers.
+constexpr double kFp32LayerSolarRatio = 5e-3;
 // the kernel precision a call runs in: an FP32 precision with any (point,
-// sample) pair outside the FP32 domain (kFp32MatterRatio) runs in FP64
-bool fp32_in_domain(const osc_point &p, const Sample *s);
+// sample) pair outside its domain (kFp32MatterRatio, kFp32LayerSolarRatio) runs in FP64
+bool fp32_in_domain(const osc_point &p, const Sample *s, int prec);
 int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
               int32_t n_points);
 cudaEvent_t pool_event(osc_ctx *c);

@@ -452,7 +452,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
         if (it == ctx->samples.end()) return OSC_E_ARG;
         r.sd = it->second->dev;
         r.frac_bits = it->second->frac_bits;
-        r.prec = fp32_in_domain(*pt, it->second) ? prec_kind(prec) : kFP64;
+        r.prec = fp32_in_domain(*pt, it->second, prec_kind(prec)) ? prec_kind(prec) : kFP64;
     }
     r.pt = *pt;
     {

@@ -235,3 +235,28 @@ def test_fp32_domain_uses_the_densest_layer_and_serving_applies_it():
         finally:
             api.osc_serve_stop(c.ptr)
         api.osc_unload_sample(c.ptr, sid)
+
+
+def test_fp32_bulk_through_layers_needs_a_resolved_solar_splitting():
+    """FP32-bulk through layers also needs dm21 >= 5e-3 |dm31| (the layer update
+    divides by the solar gap, which FP32 seeds cannot resolve below that): a
+    point with dm21 = 4e-4 |dm31| runs in FP64 on a layered sample, bit for bit,
+    while FP32_F64EIG (FP64 shifts) keeps its own path and a single-layer sample
+    keeps FP32-bulk."""
+    s = synth.all_channel_sample(20_000, seed=43, L_km=3000.0, rho=3.0)
+    pt = np.array([[0.311, 0.0251, 0.5, 1.0e-6, 2.5e-3, 0.7, 1.0, 1.0]])
+    lo, hi, nb = 0.0, 30.0, 20
+    with api.Context(0) as c:
+        sid = api.osc_load_sample(c.ptr, s)
+        api.osc_set_params(c.ptr, pt)
+        single32 = _reweight(c.ptr, sid, 0, "fp32", s["n"])[0]
+        assert not np.array_equal(single32, _reweight(c.ptr, sid, 0, "fp64", s["n"])[0])
+        api.osc_set_layers(c.ptr, sid, PROFILE)
+        p64 = _reweight(c.ptr, sid, 0, "fp64", s["n"])[0]
+        assert np.array_equal(_reweight(c.ptr, sid, 0, "fp32", s["n"])[0], p64)
+        assert np.array_equal(api.osc_histogram(c.ptr, [sid], 0, 1, "fp32", lo, hi, nb),
+                              api.osc_histogram(c.ptr, [sid], 0, 1, "fp64", lo, hi, nb))
+        pmix = _reweight(c.ptr, sid, 0, "fp32_f64eig", s["n"])[0]
+        assert not np.array_equal(pmix, p64)
+        assert np.max(np.abs(pmix - p64)) <= TOL32
+        api.osc_unload_sample(c.ptr, sid)
