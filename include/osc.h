@@ -75,8 +75,10 @@ typedef enum {
  * and samples include a pair outside the domain (with the sample's largest
  * E_true and its densest layer) therefore runs wholly in OSC_FP64: the results
  * are the FP64 results.  Through layers (osc_set_layers) OSC_FP32_BULK also
- * needs dm21 >= 5e-3 |dm31|: below it the FP32 seeds of the two solar roots
- * cannot resolve their gap, which the layer update divides by.  Physical
+ * needs dm21 >= 5e-3 |dm31| (below it the FP32 seeds of the two solar roots
+ * cannot resolve their gap, which the layer update divides by) and a matter
+ * term at most 100 |dm31| (the layer update meets the matter-dominated pair
+ * earlier than the single-layer form).  Physical
  * parameters stay far inside: through the Earth's core at 50 GeV, |A| is about
  * 20 |dm31|, and dm21 is about 0.03 |dm31|. */
 typedef enum {

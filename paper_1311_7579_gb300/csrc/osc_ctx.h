@@ -145,8 +145,13 @@ int prec_kind(osc_precision p);
 // 1.2e-4, 1e-4 at 3e-3).  The single-layer Sylvester form stays below 1e-3 there,
 // and FP32_F64EIG (FP64 shifts) below 1.2e-5 through layers.
 constexpr double kFp32LayerSolarRatio = 5e-3;
+// ... and a matter term at most kFp32LayerMatterRatio |dm31|: the layer update meets
+// the matter-dominated near-double pair earlier than the single-layer form
+// (|dP| 6e-3 to 1e-2 at 300-480 |dm31| through five layers, 8e-4 at 107, 5e-5
+// at 49, against at most 7.5e-4 up to 1500 for one layer).
+constexpr double kFp32LayerMatterRatio = 100.0;
 // the kernel precision a call runs in: an FP32 precision with any (point,
-// sample) pair outside its domain (kFp32MatterRatio, kFp32LayerSolarRatio) runs in FP64
+// sample) pair outside its domain (the three ratios above) runs in FP64
 bool fp32_in_domain(const osc_point &p, const Sample *s, int prec);
 int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
               int32_t n_points);

@@ -99,27 +99,34 @@ int prec_kind(osc_precision p) { return p == OSC_FP32_BULK ? kFP32 : p == OSC_FP
 
 bool fp32_in_domain(const osc_point &p, const Sample *s, int prec) {
     const double dm31 = std::fabs(p.dm32 + p.dm21);
-    if (!(s->ka_max * (double)s->e_max <= kFp32MatterRatio * dm31)) return false;
-    return !(prec == kFP32 && s->dev.n_layers > 1 && !(p.dm21 >= kFp32LayerSolarRatio * dm31));
+    const double a_max = s->ka_max * (double)s->e_max;
+    if (!(a_max <= kFp32MatterRatio * dm31)) return false;
+    if (prec != kFP32 || s->dev.n_layers <= 1) return true;
+    return p.dm21 >= kFp32LayerSolarRatio * dm31 && a_max <= kFp32LayerMatterRatio * dm31;
 }
 
 int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
               int32_t n_points) {
     const int pr = prec_kind(prec);
     if (pr == kFP64) return pr;
-    double a_max = 0.0;
+    double a_max = 0.0, a_max_layered = 0.0;
     bool layered = false;
     for (int32_t i = 0; i < n_ids; ++i) {
         const Sample *s = c->samples[ids[i]];
-        a_max = std::max(a_max, s->ka_max * (double)s->e_max);
-        layered = layered || s->dev.n_layers > 1;
+        const double a = s->ka_max * (double)s->e_max;
+        a_max = std::max(a_max, a);
+        if (s->dev.n_layers > 1) {
+            layered = true;
+            a_max_layered = std::max(a_max_layered, a);
+        }
     }
-    const double lim = a_max / kFp32MatterRatio;
     for (int32_t k = point_begin; k < point_begin + n_points; ++k) {
         const osc_point &p = c->pts[k];
         const double dm31 = std::fabs(p.dm32 + p.dm21);
-        if (!(dm31 >= lim)) return kFP64;
-        if (pr == kFP32 && layered && !(p.dm21 >= kFp32LayerSolarRatio * dm31)) return kFP64;
+        if (!(a_max <= kFp32MatterRatio * dm31)) return kFP64;
+        if (pr == kFP32 && layered &&
+            !(p.dm21 >= kFp32LayerSolarRatio * dm31 && a_max_layered <= kFp32LayerMatterRatio * dm31))
+            return kFP64;
     }
     return pr;
 }
