@@ -88,3 +88,28 @@ def test_cubic_from_invariants_has_the_eigenvalues_in_matter(nubar):
             # and the three roots of the cubic are the eigenvalues
             roots = np.sort(np.roots([1.0, -c2, c1, -c0]).real)
             assert np.allclose(roots, lam, rtol=0, atol=1e-12 * (abs(dm31) + abs(a)))
+
+
+def test_deflation_of_a_depressed_cubic_gives_the_pair_and_its_gap():
+    """The FP64 solver's seed for a near-double pair: if mu_i is one root of
+    mu^3 + p mu + q (the roots sum to zero), the other two are the roots of
+    mu^2 + mu_i mu + (p + mu_i^2), and its discriminant -3 mu_i^2 - 4 p is the
+    squared difference of the pair -- for well separated and near-double pairs,
+    with the isolated root at the top (cos theta near +1) or at the bottom."""
+    rng = np.random.default_rng(99)
+    for _ in range(200):
+        scale = np.exp(rng.uniform(np.log(1e-6), np.log(1e-1)))
+        gap = scale * np.exp(rng.uniform(np.log(1e-6), 0.0))
+        centre = rng.choice([-1.0, 1.0]) * scale
+        a, b = centre - gap / 2, centre + gap / 2
+        mi = -(a + b)                    # the isolated root (depressed: roots sum to zero)
+        p = a * b + mi * (a + b)         # mu^3 + p mu + q = (mu - a)(mu - b)(mu - mi)
+        q = -a * b * mi
+        assert abs(mi ** 3 + p * mi + q) <= 1e-12 * abs(mi) ** 3
+        disc = -3 * mi * mi - 4 * p
+        assert abs(disc - gap * gap) <= 1e-12 * mi * mi
+        lo = (-mi - np.sqrt(max(disc, 0.0))) / 2
+        hi = (-mi + np.sqrt(max(disc, 0.0))) / 2
+        # the pair's roots to the discriminant's rounding: eps mi^2 / gap
+        tol = 1e-15 * abs(mi) + 8e-16 * mi * mi / gap
+        assert abs(lo - a) <= tol and abs(hi - b) <= tol, (scale, gap)
