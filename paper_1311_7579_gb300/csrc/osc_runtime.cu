@@ -1036,7 +1036,7 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
 static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t pb, int32_t np, int prec,
                              int32_t nbins, double lo, double hi, int32_t pt, int32_t chunk, double *ms) {
     NvtxRange nvtx_range("autotune candidate");
-    Plan *p;
+    Plan *p = nullptr;
     osc_status st = get_plan(ctx, ids, pb, np, prec, nbins, pt, chunk, &p);
     if (st) return st;
     st = ensure_buf(ctx, &ctx->d_out, &ctx->out_cap, p->n_hist * nbins);
@@ -1103,7 +1103,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
                     int32_t ch = (k == 0) ? d0 : (k == 1) ? std::max(q, (d0 / 4 + q - 1) / q * q) : d0 * 4;
                     ch = std::min(ch, 1 << 20);
                     if (k == 1 && ch == d0) continue;
-                    double ms;
+                    double ms = 0.0;
                     st = time_shape(ctx, ids, point_begin, n_points, pr, nbins, lo, hi, c, ch, &ms);
                     if (st) return st;
                     if (ms < best_ms) {
@@ -1120,7 +1120,7 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
         }
     }
     if (chunk == 0) chunk = default_chunk(ctx, ids, n_points, pt, pr);
-    Plan *p;
+    Plan *p = nullptr;
     st = get_plan(ctx, ids, point_begin, n_points, pr, nbins, pt, chunk, &p, layered ? kLayered : kEventByEvent);
     if (st) return st;
     double *d_out = out;
@@ -1328,7 +1328,7 @@ extern "C" osc_status osc_histogram_bin_centre(osc_ctx *ctx, const int32_t *samp
     const int64_t bins = (int64_t)n_samples * n_points * nbins;
     osc_status st = ensure_acc(ctx, bins);
     if (st) return st;
-    Plan *p;
+    Plan *p = nullptr;
     st = get_bc_plan(ctx, ids, point_begin, n_points, pr, nbins, t_lo, t_hi, t_nbins, &p);
     if (st) return st;
     double *d_out = out;
