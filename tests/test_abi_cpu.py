@@ -73,6 +73,28 @@ def test_calls_without_context_return_arg_status():
     L.osc_destroy(None)  # no-op
 
 
+def test_prepared_point_histogram_marshalling_without_a_gpu():
+    """api.PointHistogram marshals once: its point buffer is a writable float64[8]
+    view that a call with a point overwrites, the output is allocated with the
+    call's shape, and the library's status comes back as OscError (a null
+    context is rejected before any device work)."""
+    import numpy as np
+    call = api.PointHistogram(None, [3, 5], "fp32", 0.0, 5.0, 100)
+    assert call.point.dtype == np.float64 and call.point.shape == (8,) and call.point.flags.writeable
+    assert call.out.shape == (2, 1, 100)
+    p = np.arange(1.0, 9.0)
+    with pytest.raises(api.OscError) as e:
+        call(p)
+    assert e.value.status == api.OSC_E_ARG and "no context" in str(e.value)
+    assert np.array_equal(call.point, p)
+    call.point[4] = -2.5e-3
+    with pytest.raises(api.OscError):
+        call()
+    assert call.point[4] == -2.5e-3
+    with pytest.raises(ValueError):
+        call(np.zeros(7))
+
+
 def test_create_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():
