@@ -1,5 +1,5 @@
 """Plants plausible mistakes in a private copy of the oracle's C source and
-checks that the pins in test_oracle_pins.py catch every one of them (CPU only).
+checks that the pins in test_oracle_pins.py (and test_oracle_pins_ext.py) catch every one of them (CPU only).
 
 Each mutation is applied to a copy in a temporary directory, built there, and
 the pin tests run in a subprocess against that copy; the committed oracle is
@@ -37,6 +37,13 @@ MUTATIONS = [
      "p = orc_prob(pt, L_km, rho, ye, (double)e_true[i] + 0.0 * t,", EXT),
     ("binned method keeps events below the range", "if (t >= 0)\n            p = orc_prob",
      "if (t >= -1)\n            p = orc_prob", EXT),
+    ("reweight swaps initial and final flavour", "(double)e_true[i], flav_in[i], flav_out[i],",
+     "(double)e_true[i], flav_out[i], flav_in[i],"),
+    ("histogram ignores the point's energy scale", "scratch_w, pts[p].escale, lo, hi, nbins, compensated,",
+     "scratch_w, pts[0].escale, lo, hi, nbins, compensated,"),
+    ("histogram rows written at the wrong offset", "out + (int64_t)p * nbins);", "out + (int64_t)0 * nbins);"),
+    ("histogram weights every point with the first point", "ye, &pts[p], 0,\n                     scratch_w);",
+     "ye, &pts[0], 0,\n                     scratch_w);"),
     ("layers multiplied against the order of travel", "mat_mul(Sk, S, S);", "mat_mul(S, Sk, S);", EXT),
     ("every layer at the first layer's density", "orc_matter_A(rho[k], ye[k], E_GeV)",
      "orc_matter_A(rho[0], ye[0], E_GeV)", EXT),
