@@ -67,20 +67,33 @@ typedef enum {
     OSC_E_BUSY = 7     /* serving queue full */
 } osc_status;
 
-/* Domain of the two FP32 precisions: the matter term |A| = k_A rho Y_e E_true of
- * every event at most 1000 |dm31| (dm31 = dm32 + dm21) of the point.  Beyond it
- * two eigenvalues in matter form a near-double pair at the scale of the
- * eigenvalue cubic, which FP32 cannot resolve (the error grows from ~1e-4 to
- * O(1) between 1000 and 3000 |dm31|).  A call in an FP32 precision whose points
- * and samples include a pair outside the domain (with the sample's largest
- * E_true and its densest layer) therefore runs wholly in OSC_FP64: the results
- * are the FP64 results.  Through layers (osc_set_layers) OSC_FP32_BULK also
- * needs dm21 >= 5e-3 |dm31| (below it the FP32 seeds of the two solar roots
- * cannot resolve their gap, which the layer update divides by) and a matter
- * term at most 100 |dm31| (the layer update meets the matter-dominated pair
- * earlier than the single-layer form).  Physical
- * parameters stay far inside: through the Earth's core at 50 GeV, |A| is about
- * 20 |dm31|, and dm21 is about 0.03 |dm31|. */
+/* Precisions.  OSC_FP64 is the plain path.  The two FP32 precisions return, for
+ * every event, a probability within |dP| <= 1e-5 of the FP64 definition:
+ *   - Per event: the FP32 amplitude (Sylvester numerators in the vacuum mass
+ *     basis) bounds its own rounding error; an event whose bound exceeds the
+ *     tolerance (narrow resonances: small mixing angles at a level crossing,
+ *     eigenvalues nearly degenerate in matter), or whose FP32 eigenvalue seed is
+ *     ill-conditioned, is recomputed with the FP64 path's arithmetic.  In a
+ *     histogram such events are added by a second pass over the marked work
+ *     items; the bins stay exact and deterministic.
+ *   - Per call: OSC_FP32_BULK forms the eigenvalue shifts and phases in FP32.  A
+ *     call whose points and samples include a pair with the sample's matter
+ *     phase c_L L k_A rho Y_e above 3 rad (summed over layers) or its largest
+ *     matter term above 10 |dm31| runs as OSC_FP32_F64EIG (shifts and phases in
+ *     FP64).  Beam baselines stay far inside: 1300 km at 2.85 g/cm^3 is 0.72 rad,
+ *     and |A| <= 5 |dm31| up to 45 GeV there; a 12000 km path through 13 g/cm^3
+ *     is 30 rad.
+ *   - Per call: both FP32 precisions run wholly in OSC_FP64 where a (point,
+ *     sample) pair has a matter term above 1000 |dm31| (with the sample's largest
+ *     E_true and densest layer), where two eigenvalues in matter form a
+ *     near-double pair that FP32 cannot resolve.  Through layers (osc_set_layers)
+ *     OSC_FP32_BULK also needs dm21 >= 5e-3 |dm31| and a matter term at most
+ *     100 |dm31|, else it runs in FP64.
+ *   The layered kernels do not estimate their error per event: through layers
+ *   the tolerance rests on the per-call rules above, measured over random layer
+ *   profiles and points across the whole accepted domain.
+ * Physical parameters stay far inside every limit: through the Earth's core at
+ * 50 GeV, |A| is about 20 |dm31|, and dm21 is about 0.03 |dm31|. */
 typedef enum {
     OSC_FP64 = 0,         /* all-FP64 path: closed-form cubic eigenvalues, FP64 amplitude */
     OSC_FP32_BULK = 1,    /* FP32 bulk with FP64-derived per-point constants: eigenvalues as
@@ -174,6 +187,44 @@ osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samp
 osc_status osc_histogram_point(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, const osc_point *pt,
                                osc_precision prec, double lo, double hi, int32_t nbins, double *out,
                                int out_on_device);
+
+/* Exact histograms over several GPUs.  The path shards naturally (Sec. 2.1: one
+ * event per thread, every event independent): by parameter points (each rank
+ * calls osc_histogram for a slice of the point table; the slices are only
+ * gathered) or by events (each rank holds a slice of a sample's events).  For
+ * the event split the one exchange step is a sum of partial histograms, and
+ * these three calls make it exact, so that the merged bins equal bit for bit
+ * those of one osc_histogram call over all events:
+ *
+ * osc_sample_set_bounds: every rank sets, for its slice of a sample, the bounds
+ *   of the whole sample: w_abs_max >= the largest |w_mc| and e_true_max >= the
+ *   largest E_true over all ranks' events (an all-reduce of two maxima).  They
+ *   fix the fixed-point scale F = 62 - ceil(log2 w_abs_max) (as osc_load_sample
+ *   derives it from its own events) and the precision routing (osc_precision),
+ *   so every rank sums and routes as one call over all events would.  Each
+ *   bound must be at least the slice's own (OSC_E_RANGE otherwise); OSC_E_STATE
+ *   while serving runs.  Cached launch plans are dropped.
+ * osc_histogram_digits: osc_histogram with the same arguments, except that it
+ *   returns each bin's exact fixed-point sum instead of a double: kDigits = 4
+ *   uint64 words per bin, digits[((s * n_points + p) * nbins + b) * 4 + q], whose
+ *   value is (d0 + d1 2^32 + d2 2^64 + (int64)d3 2^96) 2^-F before the point's
+ *   norm.  Word-wise uint64 sums of these arrays over ranks (an all-reduce with
+ *   integer wrap-around) are the digits of the exact total, as long as the
+ *   ranks' events of a sample number fewer than 2^32 in all.  Host or device
+ *   memory as for osc_histogram.
+ * osc_histogram_from_digits: converts summed digits to bins exactly as every
+ *   histogram call does (each sample's F from the sample, each point's norm
+ *   from the current point table): out[s][p][b] for the same sample ids, point
+ *   range and nbins as the digits call.  digits and out are both host
+ *   (on_device == 0; the call returns when out is written) or both device
+ *   memory (on_device == 1; the call returns once the work is enqueued). */
+osc_status osc_sample_set_bounds(osc_ctx *ctx, int32_t sample_id, double w_abs_max, double e_true_max);
+osc_status osc_histogram_digits(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
+                                int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
+                                uint64_t *digits, int out_on_device);
+osc_status osc_histogram_from_digits(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                                     int32_t point_begin, int32_t n_points, int32_t nbins, const uint64_t *digits,
+                                     double *out, int on_device);
 
 /* Binned ("bin-centre") PDFs: the quicker alternative that Sec. 1.1.1 contrasts
  * with event-by-event reweighting, in which each event's probability is taken
@@ -290,20 +341,25 @@ osc_status osc_serve_stop(osc_ctx *ctx);
  * doubles.  Work runs on cuda_stream (NULL = legacy default stream) on the
  * current device, and the call returns after it has finished.
  *
- * Its working memory is one fixed file-scope device array of about 97 KB
- * (point constants, 3 x 4096 accumulator words, a counter and an error flag),
+ * Its working memory is one fixed file-scope device array of about 130 KB
+ * (point constants, 4 x 4096 accumulator words, a counter and an error flag),
  * held by every GPU that loads this library until the process exits; nbins is
  * therefore limited to 4096, and larger values are rejected with OSC_E_ARG.
- * No cudaMalloc, cudaFree or allocating library routine is called.  The first
- * call on each device resolves the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * Every call shares the array: the call clears what must start at zero, and
- * calls that overlap on the GPU (other threads, other streams) race and must
- * not be issued.
+ * The accumulators hold 32-bit digit columns, so their bin sums stay exact for
+ * any event order up to n = 2^31 - 1.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  The first call on each device resolves the
+ * array's device address (cudaGetSymbolAddress), so make that first call before
+ * any stream capture.  Every call shares the array: the call clears what must
+ * start at zero, and calls that overlap on the GPU (other threads, other
+ * streams) race and must not be issued.
  *
- * prec is OSC_FP64 or OSC_FP32_BULK.  With OSC_FP32_BULK, an event outside the
- * FP32 domain (see osc_precision) is found on the device and the call then runs
- * again in OSC_FP64.
+ * prec is OSC_FP64, OSC_FP32_BULK or OSC_FP32_F64EIG, with the precision rules
+ * above: FP32 events whose error estimate exceeds the tolerance are recomputed
+ * in FP64; an OSC_FP32_BULK call whose matter phase exceeds 3 rad runs as
+ * OSC_FP32_F64EIG; and since the host does not see the events, the kernel
+ * flags any event outside its precision's matter-term limit (10 |dm31| for
+ * FP32 bulk, 1000 |dm31| for F64EIG) and the call then runs again in the next
+ * precision (FP32 bulk -> FP32_F64EIG -> FP64).
  *
  * Errors: OSC_E_ARG (null pointer, bad precision, n outside [1, 2^31 - 1],
  * nbins outside [1, 4096]), OSC_E_RANGE (invalid scalars or point; or, found

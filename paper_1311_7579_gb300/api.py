@@ -28,7 +28,8 @@ ENTRY_POINTS = [
     "osc_set_params", "osc_reweight", "osc_histogram", "osc_histogram_point", "osc_histogram_bin_centre",
     "osc_set_layers", "osc_set_tile", "osc_enable_timing", "osc_last_timing", "osc_timing_totals",
     "osc_launch_count", "osc_workspace_used", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
-    "osc_serve_stop", "osc_histogram_noalloc",
+    "osc_serve_stop", "osc_histogram_noalloc", "osc_sample_set_bounds", "osc_histogram_digits",
+    "osc_histogram_from_digits",
 ]
 
 
@@ -99,6 +100,10 @@ def load_library(path):
         "osc_serve_stop": (st, [vp]),
         "osc_histogram_noalloc": (st, [vp, vp, vp, vp, vp, vp, i64, d, d, d, d, ctypes.POINTER(OscPoint),
                                        ctypes.c_int, d, d, i32, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "osc_sample_set_bounds": (st, [vp, i32, d, d]),
+        "osc_histogram_digits": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
+                                      ctypes.c_int]),
+        "osc_histogram_from_digits": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, i32, vp, vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -222,6 +227,41 @@ def osc_histogram(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, o
     dev = _is_device(out)
     _check(ctx, lib().osc_histogram(ctx, ids, n_ids, int(point_begin), int(n_points), PRECISIONS[prec], float(lo),
                                     float(hi), int(nbins), _ptr(out), 1 if dev else 0))
+    return out
+
+
+def osc_sample_set_bounds(ctx, sample_id, w_abs_max, e_true_max):
+    """The whole sample's bounds for this rank's slice of it (event sharding)."""
+    _check(ctx, lib().osc_sample_set_bounds(ctx, int(sample_id), float(w_abs_max), float(e_true_max)))
+
+
+def osc_histogram_digits(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, out=None):
+    """Exact bin sums as digit columns: numpy uint64 (n_samples, n_points, nbins, 4)
+    (allocated if None) or a torch int64/uint64 CUDA tensor of that shape."""
+    ids, n_ids = _ids(sample_ids)
+    if out is None:
+        out = np.zeros((n_ids, int(n_points), int(nbins), 4), dtype=np.uint64)
+    dev = _is_device(out)
+    _check(ctx, lib().osc_histogram_digits(ctx, ids, n_ids, int(point_begin), int(n_points), PRECISIONS[prec],
+                                           float(lo), float(hi), int(nbins), _ptr(out), 1 if dev else 0))
+    return out
+
+
+def osc_histogram_from_digits(ctx, sample_ids, point_begin, n_points, nbins, digits, out=None):
+    """Bins (n_samples, n_points, nbins) from digit columns summed over ranks.
+    digits and out: both numpy (host) or both torch CUDA tensors."""
+    ids, n_ids = _ids(sample_ids)
+    dev = _is_device(digits)
+    if out is None:
+        out = np.zeros((n_ids, int(n_points), int(nbins)))
+    if _is_device(out) != dev:
+        raise OscError(OSC_E_ARG, "digits and out must both be host or both be device arrays")
+    if not dev:
+        digits = np.ascontiguousarray(digits)
+        if digits.dtype not in (np.uint64, np.int64) or digits.size != n_ids * int(n_points) * int(nbins) * 4:
+            raise OscError(OSC_E_ARG, "digits must be 64-bit integers, 4 per bin")
+    _check(ctx, lib().osc_histogram_from_digits(ctx, ids, n_ids, int(point_begin), int(n_points), int(nbins),
+                                                _ptr(digits), _ptr(out), 1 if dev else 0))
     return out
 
 
@@ -360,10 +400,31 @@ def osc_serve_stop(ctx):
 def osc_histogram_noalloc(e_true, e_reco, w_mc, flav_in, flav_out, is_nubar, baseline_km, density_gcc, ye,
                           w_abs_max, point, prec, lo, hi, nbins, out, cuda_stream=None):
     """One-point histogram with no allocation inside the library: every array
-    (inputs and the nbins-long float64 output) is a caller-owned torch CUDA tensor."""
+    (inputs and the nbins-long float64 output) is a caller-owned torch CUDA tensor.
+
+    The library sees only device pointers and n, so the arrays are checked here,
+    before the call: CUDA and contiguous, float32 energies and weights, uint8
+    flavour flags, all six of the same length n >= 1, and a float64 output of at
+    least nbins elements.  A violation raises OscError(OSC_E_ARG)."""
     arr, _ = _points(point)
+    ins = {"e_true": (e_true, "float32"), "e_reco": (e_reco, "float32"), "w_mc": (w_mc, "float32"),
+           "flav_in": (flav_in, "uint8"), "flav_out": (flav_out, "uint8"), "is_nubar": (is_nubar, "uint8")}
+    n = None
+    for name, (t, dt) in ins.items():
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise OscError(OSC_E_ARG, "%s must be a contiguous CUDA tensor" % name)
+        if str(t.dtype) != "torch." + dt:
+            raise OscError(OSC_E_ARG, "%s must be %s, got %s" % (name, dt, t.dtype))
+        if n is None:
+            n = int(t.numel())
+        elif int(t.numel()) != n:
+            raise OscError(OSC_E_ARG, "all six event arrays must have the same length (%s has %d, not %d)"
+                           % (name, int(t.numel()), n))
+    if not (hasattr(out, "is_cuda") and out.is_cuda and out.is_contiguous()) or str(out.dtype) != "torch.float64":
+        raise OscError(OSC_E_ARG, "out must be a contiguous float64 CUDA tensor")
+    if int(out.numel()) < int(nbins):
+        raise OscError(OSC_E_ARG, "out holds %d values, fewer than nbins = %d" % (int(out.numel()), int(nbins)))
     buf = ctypes.create_string_buffer(256)
-    n = int(e_true.numel())
     s = lib().osc_histogram_noalloc(_ptr(e_true), _ptr(e_reco), _ptr(w_mc), _ptr(flav_in), _ptr(flav_out),
                                     _ptr(is_nubar), n, float(baseline_km), float(density_gcc), float(ye),
                                     float(w_abs_max), arr, PRECISIONS[prec], float(lo), float(hi), int(nbins),

@@ -93,7 +93,10 @@ __global__ void __launch_bounds__(kBcTableThreads) k_bc_table(const BcParams b) 
             load_ch32(pc, ch, h);
             float A, th, tl;
             event_terms32(sd, E, ch, A, th, tl);
-            b.tab32[idx] = prob_fp32(c, h, A, th, tl);
+            bool x;
+            float P = prob_fp32(c, h, A, th, tl, x);
+            if (x) P = (float)prob_redo64(b.h.pc64 + (int64_t)rw.point * C64_STRIDE, ch, E, sd.kA_rhoye, sd.cLL);
+            b.tab32[idx] = P;
         } else if (PREC == kMix) {
             const float *pc = b.h.pc32 + (int64_t)rw.point * C32_STRIDE;
             Pt32 c;
@@ -105,7 +108,10 @@ __global__ void __launch_bounds__(kBcTableThreads) k_bc_table(const BcParams b) 
             float A, th, tl;
             event_terms32(sd, E, ch, A, th, tl);
             const double Ad = sd.kA_rhoye * (double)E;
-            b.tab32[idx] = prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl);
+            bool x;
+            float P = prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl, x);
+            if (x) P = (float)prob_redo64(b.h.pc64 + (int64_t)rw.point * C64_STRIDE, ch, E, sd.kA_rhoye, sd.cLL);
+            b.tab32[idx] = P;
         } else {
             const double *pc = b.h.pc64 + (int64_t)rw.point * C64_STRIDE;
             Pt64 c;
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
                              : prm.pc32[(int64_t)wi.point_base * C32_STRIDE + C32_ESCALE];
         const int sh = sd.frac_bits - 150;
         const int32_t *rmap = b.row_map + wi.acc_base * kChannels;
-        unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
+        unsigned long long *accp = prm.acc + kDigits * wi.acc_base * (int64_t)prm.nbins;
         RunAcc r{0ull, 0ull, -1};
         int cur_ch = -1;
         int64_t row_off = 0;
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
                     if (keep && tr >= 0.0f && ur < prm.nb_f) {
                         const int bn = __float2int_rz(ur);
                         if (bn != r.cur_b) {
-                            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+                            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + kDigits * r.cur_b, r.lo, r.hi);
                             r.lo = r.hi = 0;
                             r.cur_b = bn;
                         }

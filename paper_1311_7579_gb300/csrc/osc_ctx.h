@@ -28,8 +28,10 @@ struct Sample {
     double L = 0, rho = 0, ye = 0;
     int32_t frac_bits = 96;
     uint32_t chan_mask = 0;  // bit c set when channel id c occurs in the sample
-    float e_max = 0.0f;      // largest E_true
+    float e_max = 0.0f;      // largest E_true (or the bound osc_sample_set_bounds set)
+    double w_abs = 0.0;      // largest |w_mc|
     double ka_max = 0.0;     // largest k_A rho Y_e over the path's layers (max |A| = ka_max e_max)
+    double matter_phase = 0.0;  // sum over the path's layers of c_L L k_A rho Y_e [rad] (energy independent)
     float4 *ev = nullptr;
     int32_t *perm = nullptr;
     void *lay = nullptr;     // layered path: float4[n_layers] then double2[n_layers]
@@ -47,10 +49,12 @@ struct Plan {
     WorkItem *d_items = nullptr;
     SampleDev *d_samples = nullptr;
     double *d_hmeta = nullptr;
+    uint8_t *d_redo = nullptr;  // FP32 precisions: per work item, marked for the FP64 recomputation pass
     // timing mode: the step as a CUDA graph with event-record nodes around each kernel
     cudaGraph_t graph_t = nullptr;
     cudaGraphExec_t exec_t = nullptr;
-    cudaGraphNode_t t_hist_node = nullptr, t_final_node = nullptr, t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphNode_t t_hist_node = nullptr, t_redo_node = nullptr, t_final_node = nullptr,
+                    t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // bin-centre plans: true-energy binning, probability table and its rows
     double t_lo = 0, t_hi = 0;
     int32_t t_nbins = 0, n_rows = 0;
@@ -94,6 +98,8 @@ struct osc_ctx {
     int64_t out_cap = 0;
     double *d_rw = nullptr;
     int64_t rw_cap = 0;
+    double *d_aux = nullptr;  // staging of osc_histogram_from_digits
+    int64_t aux_cap = 0;
 
     std::list<osc::Plan *> plans;
     uint64_t plan_clock = 0;
@@ -150,9 +156,13 @@ constexpr double kFp32LayerSolarRatio = 5e-3;
 // (|dP| 6e-3 to 1e-2 at 300-480 |dm31| through five layers, 8e-4 at 107, 5e-5
 // at 49, against at most 7.5e-4 up to 1500 for one layer).
 constexpr double kFp32LayerMatterRatio = 100.0;
-// the kernel precision a call runs in: an FP32 precision with any (point,
-// sample) pair outside its domain (the three ratios above) runs in FP64
-bool fp32_in_domain(const osc_point &p, const Sample *s, int prec);
+// The kernel precision of one (point, sample) pair for a requested precision:
+// FP64 outside the FP32 precisions' domain (the matter ratio of osc_internal.h
+// and, through layers, the two ratios above); OSC_FP32_BULK becomes FP32_F64EIG
+// where its FP32 shifts and phases would not hold (the sample's matter phase
+// above kFp32BulkMatterPhase or its matter term above kFp32BulkMatterRatio
+// |dm31|).  A call runs in the most precise kernel any of its pairs needs.
+int pair_prec(const osc_point &p, const Sample *s, int prec);
 int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
               int32_t n_points);
 cudaEvent_t pool_event(osc_ctx *c);

@@ -33,8 +33,11 @@ enum PC32 : int {
     C32_S1, C32_PI1, C32_W1, C32_E1,             // ... sorted root 1
     C32_ESCALE,
     C32_TD0, C32_TD1,                            // T0 / 3 - d0, T0 / 3 - d1
-    C32_CH = 32,                                 // 9 channels x (Xr, Xi, Yr, Yi, Zr, Zi), neutrino
-    C32_LU = 96,                                 // U[f][l] (re, im), f flavour, l sorted vacuum root, neutrino
+    C32_SD02, C32_SD01,                          // d0 + d2, d0 + d1 (T0 less one sorted vacuum eigenvalue)
+    C32_CH = 32,                                 // 9 channels x (X0r, X0i, X1r, X1i, X2r, X2i, Zr, Zi), neutrino:
+                                                 // X_m = U_bm conj(U_am) (m a sorted vacuum state),
+                                                 // Z = [alpha = e] H0_be + [beta = e] H0_ea
+    C32_LU = 104,                                // U[f][l] (re, im), f flavour, l sorted vacuum root, neutrino
     C32_STRIDE = 128                             // floats, 512 B
 };
 // FP64 block (doubles).
@@ -47,6 +50,13 @@ enum PC64 : int {
     C64_VG = 104,                                // vacuum gaps d1 - d0, d2 - d0, d1 - d2
     C64_STRIDE = 112                             // doubles, 896 B
 };
+
+// ---- histogram accumulators -------------------------------------------------
+// A bin's exact 128-bit fixed-point sum is held as kDigits integer columns of
+// 32-bit digits (u64 each): a flush adds each digit of its 128-bit value, so a
+// column absorbs 2^32 flushes before it could wrap -- more than the events of
+// any call (n < 2^31), even when every event flushes.
+constexpr int kDigits = 4;
 
 // ---- resident sample as seen by a kernel ----------------------------------
 struct SampleDev {
@@ -82,9 +92,12 @@ struct HistParams {
     const SampleDev *samples;
     const float *pc32;
     const double *pc64;
-    unsigned long long *acc;  // fixed-point bins: three integer digit columns per bin
+    unsigned long long *acc;  // fixed-point bins: kDigits integer digit columns per bin
     int32_t *counter;         // dynamic work counter (reset by the finalize kernel)
     float lo_f, inv_f, nb_f;
+    // FP32 precisions: per work item, set when an event of the item needs the FP64
+    // recomputation (the histogram kernel leaves such events out; k_redo adds them)
+    uint8_t *redo;
     // fused finalize (small outputs): the last block converts the bins
     int32_t fuse_final;
     int64_t fin_n_hist;
@@ -101,6 +114,24 @@ constexpr int kPointsByValue = 256;
 // ~1e-4 to O(1) between 1e3 and 3e3); calls with a (point, sample) outside it
 // run in FP64.
 constexpr double kFp32MatterRatio = 1000.0;
+// OSC_FP32_BULK forms the eigenvalue shifts and the phases in FP32.  Their
+// rounding, amplified near narrow resonances, grows with the phase the matter
+// term adds over the baseline (c_L L k_A rho Y_e, energy independent) and with
+// the matter term itself; a call with a (point, sample) whose matter phase
+// exceeds kFp32BulkMatterPhase rad or whose largest matter term exceeds
+// kFp32BulkMatterRatio |dm31| takes its shifts and phases in FP64
+// (OSC_FP32_F64EIG).  Beam baselines stay far inside (1300 km at 2.85 g/cm^3:
+// 0.72 rad, and |A| <= 5 |dm31| up to 45 GeV).
+constexpr double kFp32BulkMatterPhase = 3.0;
+constexpr double kFp32BulkMatterRatio = 10.0;
+// Per-event error estimate of the FP32 amplitude (units of the FP32 rounding
+// unit 2^-24): an event whose estimate exceeds kFp32EstMax, or (FP32-bulk)
+// whose trigonometric seed has |cos theta| above kFp32SeedCos (a near-double
+// pair the single Newton step may not resolve), is recomputed in FP64.
+// kFp32EstMax = 30 keeps the estimated FP32 error below 30 * 2^-24 * 2 = 3.6e-6
+// in P, which with the sine/cosine and phase rounding stays under 1e-5.
+constexpr float kFp32EstMax = 30.0f;
+constexpr float kFp32SeedCos = 0.9995f;
 template <int N>
 struct PointsByValueT {
     int32_t n;
@@ -153,6 +184,10 @@ struct BcParams {
 // its buffers.
 enum DebugCode : unsigned { kDbgItem = 1u, kDbgBin = 2u, kDbgRow = 4u, kDbgLayers = 8u };
 constexpr int kDebugWord = 15;
+// Ints of a launch's counter block used by the FP64 recomputation: the number of
+// work items marked for it, and the completion ticket of the redo kernel.
+constexpr int kRedoCount = 8;
+constexpr int kRedoTicket = 9;
 
 // Precision of a kernel instantiation.
 enum Prec { kFP64 = 0, kFP32 = 1, kMix = 2 };  // kMix: FP64 eigen-solve and phases, FP32 amplitude

@@ -52,9 +52,12 @@ __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddep
 struct cplx64 {
     double re, im;
 };
+// The constants are written with explicit fma wherever a product is added, so
+// that every kernel inlining them (the constants kernels, the allocation-free
+// call) rounds identically and gives bitwise the same constants.
 __device__ __forceinline__ cplx64 cmul_conj(cplx64 a, double m, cplx64 b) {
     // a * m * conj(b)
-    return {m * (a.re * b.re + a.im * b.im), m * (a.im * b.re - a.re * b.im)};
+    return {m * fma(a.re, b.re, a.im * b.im), m * fma(a.im, b.re, -(a.re * b.im))};
 }
 
 __device__ __forceinline__ void split_ff(double v, float *hi, float *lo) {
@@ -191,7 +194,7 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
             for (int k = 1; k < 3; ++k) {
                 const cplx64 q = cmul_conj(Us[3 * b + k], m[k], Us[3 * a + k]);
                 h.re += q.re; h.im += q.im;
-                h2.re += q.re * m[k]; h2.im += q.im * m[k];
+                h2.re = fma(q.re, m[k], h2.re); h2.im = fma(q.im, m[k], h2.im);
             }
             Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
         }
@@ -208,16 +211,30 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
         }
         pair_barrier(3);
         if (lane < 27) {
-            // channel (alpha -> beta) = ch (alpha * 3 + beta), field j of
+            // FP64 block: channel (alpha -> beta) = ch (alpha * 3 + beta), field j of
             // (Xr, Xi, Yr, Yi, Zr, Zi) with X = M0_ba, Y = (M0^2)_ba,
             // Z = M0_be [alpha = e] + [beta = e] M0_ea: one field per lane of warps 0, 1
             const int ch = lane / 3, j = 3 * warp + lane % 3;
             const int a = ch / 3, b = ch % 3;
             const int cmp = j < 4 ? j : j - 4;
             const double z = (a == 0 ? Hs[cmp][3 * b] : 0.0) + (b == 0 ? Hs[cmp][a] : 0.0);
-            const double v = j < 4 ? Hs[cmp][3 * b + a] : z;
-            c32[C32_CH + 6 * ch + j] = (float)v;
-            c64[C64_CH + 6 * ch + j] = v;
+            c64[C64_CH + 6 * ch + j] = j < 4 ? Hs[cmp][3 * b + a] : z;
+        }
+        // FP32 block: the channels in the vacuum mass basis, field j of
+        // (X0r, X0i, X1r, X1i, X2r, X2i, Zr, Zi) with X_l = U_bm conj(U_am) (m the mass
+        // state of sorted vacuum root l) and Z as above; 72 fields over the 64 lanes
+        for (int f = 32 * warp + lane; f < 72; f += 64) {
+            const int ch = f >> 3, j = f & 7, a = ch / 3, b = ch % 3;
+            double v;
+            if (j < 6) {
+                const int l = j >> 1, m = no ? l : (l + 2) % 3;
+                const cplx64 ub = Us[3 * b + m], ua = Us[3 * a + m];
+                v = (j & 1) ? fma(ub.im, ua.re, -(ub.re * ua.im)) : fma(ub.re, ua.re, ub.im * ua.im);
+            } else {
+                const int cmp = j - 6;
+                v = (a == 0 ? Hs[cmp][3 * b] : 0.0) + (b == 0 ? Hs[cmp][a] : 0.0);
+            }
+            c32[C32_CH + 8 * ch + j] = (float)v;
         }
     } else if (warp == 2) {
         // |U_e1|^2, |U_e2|^2, |U_e3|^2 and their sorted-order counterparts
@@ -229,7 +246,7 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
             const double zl = lane ? z1 : z0, zj = lane ? z2 : z1, zk = lane ? z0 : z2;
             const double aj = dl - dj, ak = dl - dk;
             const int o = lane ? (C32_S1 - C32_S0) : 0;
-            const double S = aj + ak, PI = aj * ak, W = zl * (aj + ak) + zj * ak + zk * aj, E = zl * aj * ak;
+            const double S = aj + ak, PI = aj * ak, W = fma(zl, aj + ak, fma(zj, ak, zk * aj)), E = zl * aj * ak;
             c32[C32_S0 + o] = (float)S;
             c32[C32_PI0 + o] = (float)PI;
             c32[C32_W0 + o] = (float)W;
@@ -274,7 +291,11 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
                 c64[C64_SMT] = smt;
             }
         }
-    } else if (lane < 14) {
+    } else if (lane >= 14) {
+        // warp 3, lanes 14, 15: T0 less one sorted vacuum eigenvalue (the e -> e term of the FP32 amplitude)
+        if (lane == 14) c32[C32_SD02] = (float)(d0 + d2);
+        if (lane == 15) c32[C32_SD01] = (float)(d0 + d1);
+    } else {
         // warp 3: one value per lane, x = a s - b: the sorted spectrum, its gaps
         // (two as float-float), T0, c1(0), T0 / 3 - d0, T0 / 3 - d1 and the
         // systematics; o64 / o32 are its FP64 / FP32 slots (-1: none)
@@ -314,15 +335,19 @@ __device__ __forceinline__ void load_pt32(const float *__restrict__ c, Pt32 &o) 
     o.v1h = c[C32_V1H]; o.v1l = c[C32_V1L]; o.v2h = c[C32_V2H]; o.v2l = c[C32_V2L];
     o.S0 = c[C32_S0]; o.PI0 = c[C32_PI0]; o.W0 = c[C32_W0]; o.E0 = c[C32_E0];
     o.S1 = c[C32_S1]; o.PI1 = c[C32_PI1]; o.W1 = c[C32_W1]; o.E1 = c[C32_E1];
+    o.sd02 = c[C32_SD02]; o.sd01 = c[C32_SD01];
 }
 __device__ __forceinline__ void load_ch32(const float *__restrict__ c, int ch, Ch32 &o) {
     const int nubar = ch >= 9;
     const int ab = ch - 9 * nubar;
-    const float *v = c + C32_CH + 6 * ab;
-    const float sg = nubar ? -1.0f : 1.0f;  // antineutrino: M0 -> conj(M0)
-    o.Xr = v[0]; o.Xi = sg * v[1]; o.Yr = v[2]; o.Yi = sg * v[3]; o.Zr = v[4]; o.Zi = sg * v[5];
+    const float *v = c + C32_CH + 8 * ab;
+    const float sg = nubar ? -1.0f : 1.0f;  // antineutrino: U -> conj(U)
+    o.X0r = v[0]; o.X0i = sg * v[1]; o.X1r = v[2]; o.X1i = sg * v[3]; o.X2r = v[4]; o.X2i = sg * v[5];
+    o.Zr = v[6]; o.Zi = sg * v[7];
     o.ee = (ab == 0) ? 1.0f : 0.0f;
     o.diag = (ab == 0 || ab == 4 || ab == 8) ? 1.0f : 0.0f;
+    o.zm = fabsf(o.Zr) + fabsf(o.Zi);
+    o.real = ab == 4 || ab == 8;
 }
 __device__ __forceinline__ void load_pt64(const double *__restrict__ c, Pt64 &o) {
     o.p0 = c[C64_P0]; o.p1 = c[C64_P1]; o.q0 = c[C64_Q0]; o.q1 = c[C64_Q1]; o.q2 = c[C64_Q2];
@@ -341,6 +366,21 @@ __device__ __forceinline__ void load_ch64(const double *__restrict__ c, int ch, 
     o.ee = (ab == 0) ? 1.0 : 0.0;
     o.diag = (ab == 0 || ab == 4 || ab == 8) ? 1.0 : 0.0;
 }
+
+// The FP64 path's probability of one event for one point, for the FP32
+// precisions' events whose error estimate exceeds the tolerance (pc64: the
+// point's FP64 constants; ch: channel id; E: E_true).  Out of line, so the FP32
+// kernels' main loops keep their registers; it runs for few events.
+static __device__ __noinline__ double prob_redo64(const double *__restrict__ pc64, int ch, float E, double kA_rhoye,
+                                                  double cLL) {
+    Pt64 c;
+    Ch64 h;
+    load_pt64(pc64, c);
+    load_ch64(pc64, ch, h);
+    const double Ad = kA_rhoye * (double)E;
+    return prob_fp64(c, h, (ch >= 9) ? -Ad : Ad, tau64(cLL, E));
+}
+
 
 // -------------------------------------------------- 128-bit fixed-point bins
 // A bin holds sum(w) * 2^F as a two's-complement 128-bit integer (lo, hi).
@@ -376,38 +416,53 @@ __device__ __forceinline__ void fx_add_f64(unsigned long long &lo, unsigned long
     const unsigned long long l = __double2ull_rz((y - fl) * 18446744073709551616.0);
     fx_add(lo, hi, l, (unsigned long long)h);
 }
-// Global bins hold three integer columns: a flushed 128-bit value v is split
-// into digits v = d0 + d1 2^40 + d2 2^80 (d0, d1 in [0, 2^40), d2 signed) and
-// each digit is added with a fire-and-forget reduction.  Column sums are plain
-// integer sums, so the result is exact and independent of the flush order;
+// Global bins hold kDigits integer columns: a flushed 128-bit value v is split
+// into 32-bit digits v = d0 + d1 2^32 + d2 2^64 + d3 2^96 (d0, d1, d2 in
+// [0, 2^32), d3 signed) and each digit is added with a fire-and-forget
+// reduction.  Column sums are plain integer sums, so the result is exact and
+// independent of the flush order, and a column wraps only after 2^32 flushes;
 // the finalize kernel recombines the columns.
 __device__ __forceinline__ void fx_flush(unsigned long long *p, unsigned long long lo, unsigned long long hi) {
-    constexpr unsigned long long M40 = (1ull << 40) - 1ull;
-    const unsigned long long d0 = lo & M40;
-    const unsigned long long d1 = ((lo >> 40) | (hi << 24)) & M40;
-    const long long d2 = (long long)hi >> 16;
+    constexpr unsigned long long M32 = 0xFFFFFFFFull;
+    const unsigned long long d0 = lo & M32, d1 = lo >> 32, d2 = hi & M32;
+    const long long d3 = (long long)hi >> 32;
     if (d0) atomicAdd(p, d0);
     if (d1) atomicAdd(p + 1, d1);
-    if (d2) atomicAdd(p + 2, (unsigned long long)d2);
+    if (d2) atomicAdd(p + 2, d2);
+    if (d3) atomicAdd(p + 3, (unsigned long long)d3);
 }
 
-// Value of a bin: the three digit columns depend on how runs were split into
+// The kDigits columns of bin i of an accumulator array (L2 loads: other SMs' reductions).
+struct Digits {
+    unsigned long long d[kDigits];
+};
+__device__ __forceinline__ Digits load_digits(const unsigned long long *acc, int64_t i) {
+    Digits g;
+#pragma unroll
+    for (int k = 0; k < kDigits; ++k) g.d[k] = __ldcg(acc + kDigits * i + k);
+    return g;
+}
+__device__ __forceinline__ void clear_digits(unsigned long long *acc, int64_t i) {
+#pragma unroll
+    for (int k = 0; k < kDigits; ++k) acc[kDigits * i + k] = 0ull;
+}
+
+// Value of a bin: the digit columns depend on how runs were split into
 // flushes; their combination, the exact 128-bit sum, does not, and only that
 // is converted: (hi 2^64 + lo) 2^-F times the point's norm, with m0 = 2^(64-F)
 // and m1 = 2^-F (both products exact, so the result does not depend on how the
 // sum is contracted).
-__device__ __forceinline__ double bin_value(unsigned long long d0, unsigned long long d1, unsigned long long d2,
-                                            double m0, double m1, double norm) {
-    const unsigned __int128 v = (unsigned __int128)d0 + ((unsigned __int128)d1 << 40) +
-                                ((unsigned __int128)(__int128)(long long)d2 << 80);
+__device__ __forceinline__ double bin_value(const Digits &g, double m0, double m1, double norm) {
+    const unsigned __int128 v = (unsigned __int128)g.d[0] + ((unsigned __int128)g.d[1] << 32) +
+                                ((unsigned __int128)g.d[2] << 64) +
+                                ((unsigned __int128)(__int128)(long long)g.d[3] << 96);
     const long long hi = (long long)(unsigned long long)(v >> 64);
     const unsigned long long lo = (unsigned long long)v;
     return ((double)hi * m0 + (double)lo * m1) * norm;
 }
 // m: the histogram's (2^(64-F), 2^-F, unused, point index)
-__device__ __forceinline__ double final_bin(unsigned long long d0, unsigned long long d1, unsigned long long d2,
-                                            const double *m, const double *pc64) {
-    return bin_value(d0, d1, d2, m[0], m[1], pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM]);
+__device__ __forceinline__ double final_bin(const Digits &g, const double *m, const double *pc64) {
+    return bin_value(g, m[0], m[1], pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM]);
 }
 
 // Small outputs (one conversion round: up to 256 bins for a block, 128 for a
@@ -425,17 +480,16 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // events left to the FP64 recomputation: the redo kernel adds them, then converts
+    if (prm.redo && __ldcg(prm.counter + kRedoCount) > 0) return;
     const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long d0 = __ldcg(prm.acc + 3 * i), d1 = __ldcg(prm.acc + 3 * i + 1),
-                                 d2 = __ldcg(prm.acc + 3 * i + 2);
+        const Digits g = load_digits(prm.acc, i);
         const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
         const double m0 = m[0], m1 = m[1];
         const double nm = prm.pc64[(int64_t)m[3] * C64_STRIDE + C64_NORM];
-        prm.acc[3 * i] = 0ull;
-        prm.acc[3 * i + 1] = 0ull;
-        prm.acc[3 * i + 2] = 0ull;
-        prm.fin_out[i] = bin_value(d0, d1, d2, m0, m1, nm);
+        clear_digits(prm.acc, i);
+        prm.fin_out[i] = bin_value(g, m0, m1, nm);
     }
     if (threadIdx.x == 0) {
         prm.counter[0] = 0;
@@ -445,6 +499,7 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
 
 // Per-warp variant for one-point items: warps that finish early exit without
 // waiting at a block barrier; the last warp converts four bins per lane per round.
+__device__ __forceinline__ void convert_bins_warp(const HistParams &prm);
 __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     const int lane = threadIdx.x & 31;
     __threadfence();
@@ -454,20 +509,27 @@ __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
+    // events left to the FP64 recomputation: the redo kernel adds them, then converts
+    if (prm.redo && __ldcg(prm.counter + kRedoCount) > 0) return;
+    convert_bins_warp(prm);
+}
+// The last warp's conversion of the fused finalize (four bins per lane per round,
+// all loads of a round issued before any conversion), then the counter reset.
+__device__ __forceinline__ void convert_bins_warp(const HistParams &prm) {
+    const int lane = threadIdx.x & 31;
     constexpr int kU = 4;
     const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
     for (int64_t i0 = 0; i0 < n; i0 += 32 * kU) {
-        unsigned long long d[kU][3];
+        Digits d[kU];
         double m0[kU], m1[kU], nm[kU];
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
             const int64_t i = i0 + lane + 32 * k;
-            d[k][0] = d[k][1] = d[k][2] = 0ull;
+#pragma unroll
+            for (int q = 0; q < kDigits; ++q) d[k].d[q] = 0ull;
             m0[k] = m1[k] = nm[k] = 0.0;
             if (i < n) {
-                d[k][0] = __ldcg(prm.acc + 3 * i);
-                d[k][1] = __ldcg(prm.acc + 3 * i + 1);
-                d[k][2] = __ldcg(prm.acc + 3 * i + 2);
+                d[k] = load_digits(prm.acc, i);
                 const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
                 m0[k] = m[0];
                 m1[k] = m[1];
@@ -481,10 +543,8 @@ __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
         for (int k = 0; k < kU; ++k) {
             const int64_t i = i0 + lane + 32 * k;
             if (i < n) {
-                prm.acc[3 * i] = 0ull;
-                prm.acc[3 * i + 1] = 0ull;
-                prm.acc[3 * i + 2] = 0ull;
-                prm.fin_out[i] = bin_value(d[k][0], d[k][1], d[k][2], m0[k], m1[k], nm[k]);
+                clear_digits(prm.acc, i);
+                prm.fin_out[i] = bin_value(d[k], m0[k], m1[k], nm[k]);
             }
         }
     }
@@ -509,7 +569,7 @@ __device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *acc
         const int b = __float2int_rz(u);
         if (!debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) return;
         if (b != r.cur_b) {
-            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + kDigits * r.cur_b, r.lo, r.hi);
             r.lo = r.hi = 0;
             r.cur_b = b;
         }
@@ -525,7 +585,7 @@ __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *acc
         const int b = __float2int_rz(u);
         if (!debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) return;
         if (b != r.cur_b) {
-            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + kDigits * r.cur_b, r.lo, r.hi);
             r.lo = r.hi = 0;
             r.cur_b = b;
         }
@@ -533,7 +593,7 @@ __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *acc
     }
 }
 __device__ __forceinline__ void acc_finish(RunAcc &r, unsigned long long *accp) {
-    if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + 3 * r.cur_b, r.lo, r.hi);
+    if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + kDigits * r.cur_b, r.lo, r.hi);
 }
 // End of a per-warp work item: lanes that end in the same bin (the lanes hold
 // consecutive sorted events, so such lanes are normally contiguous) first sum
@@ -558,7 +618,7 @@ __device__ __forceinline__ void acc_finish_warp(RunAcc &r, unsigned long long *a
         const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, d);
         if (lane + d < end) fx_add(lo, hi, l2, h2);
     }
-    if (has && lane == first && (lo | hi)) fx_flush(accp + 3 * r.cur_b, lo, hi);
+    if (has && lane == first && (lo | hi)) fx_flush(accp + kDigits * r.cur_b, lo, hi);
 }
 
 // FP32 matter term and c_L L / (2 pi E) float-float of one event.
@@ -579,7 +639,7 @@ struct Stage32 {
 };
 struct Stage64 {
     double a[kET];
-    double tau[kET];     // c_L L / E as hi + lo (the FP32-amplitude variant uses hi only)
+    double tau[kET];     // c_L L / E as hi + lo (FP32_F64EIG: c_L L / (2 pi E), revolutions per eV^2)
     double tau_lo[kET];
     float2 ew[kET];  // (e_reco, w_mc)
     int ch[kET];
@@ -602,6 +662,19 @@ __device__ __forceinline__ void stage_one64(Stage64 &s, int j, const SampleDev &
     s.ch[j] = ch;
 }
 
+// FP32_F64EIG: the FP64 matter term and c_L L / (2 pi E) [revolutions per eV^2]
+// from the float-float of event_terms32, as the one-point path forms it (so both
+// paths, and the FP64 recomputation, take the same decisions on the same events).
+__device__ __forceinline__ void stage_one_mix(Stage64 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
+    float A, th, tl;
+    event_terms32(sd, E, ch, A, th, tl);
+    const double Ad = sd.kA_rhoye * (double)E;
+    s.a[j] = (ch >= 9) ? -Ad : Ad;
+    s.tau[j] = (double)th + (double)tl;
+    s.ew[j] = make_float2(er, w);
+    s.ch[j] = ch;
+}
+
 template <int PREC>
 struct StageOf { using T = Stage32; };
 template <>
@@ -620,6 +693,8 @@ __device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const S
             const float4 r = sd.ev[base + j];
             if (PREC == kFP32)
                 stage_one32(reinterpret_cast<Stage32 &>(s), j, sd, r.x, r.y, r.z, __float_as_int(r.w));
+            else if (PREC == kMix)
+                stage_one_mix(reinterpret_cast<Stage64 &>(s), j, sd, r.x, r.y, r.z, __float_as_int(r.w));
             else
                 stage_one64(reinterpret_cast<Stage64 &>(s), j, sd, r.x, r.y, r.z, __float_as_int(r.w));
         }
@@ -702,8 +777,9 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 sf = (float)pc64[C64_ESCALE];
             }
         }
-        unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
+        unsigned long long *accp = prm.acc + kDigits * wi.acc_base * (int64_t)prm.nbins;
         RunAcc r{0ull, 0ull, -1};
+        bool redo = false;  // an event of this item is left to the FP64 recomputation (k_redo)
         int e = lane;
         if (PREC == kFP32) {
             const int sh = sd.frac_bits - 150;
@@ -724,10 +800,19 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                     float Aa, tha, tla, Ab, thb, tlb;
                     event_terms32(sd, Ea, ca, Aa, tha, tla);
                     event_terms32(sd, Eb, cb, Ab, thb, tlb);
-                    const float Pa = prob_fp32(c32, h32, Aa, tha, tla);
-                    const float Pb = prob_fp32(c32, h32, Ab, thb, tlb);
-                    acc_event_f32(r, accp, prm, sf, ra, Pa * wa, sh, true);
-                    acc_event_f32(r, accp, prm, sf, rb, Pb * wb, sh, has_b);
+                    bool xa, xb;
+                    float Pa, Pb;
+                    if (h32.real) {
+                        Pa = prob_fp32<true>(c32, h32, Aa, tha, tla, xa);
+                        Pb = prob_fp32<true>(c32, h32, Ab, thb, tlb, xb);
+                    } else {
+                        Pa = prob_fp32<false>(c32, h32, Aa, tha, tla, xa);
+                        Pb = prob_fp32<false>(c32, h32, Ab, thb, tlb, xb);
+                    }
+                    xb = xb && has_b;
+                    redo = redo || xa || xb;
+                    acc_event_f32(r, accp, prm, sf, ra, Pa * wa, sh, !xa);
+                    acc_event_f32(r, accp, prm, sf, rb, Pb * wb, sh, has_b && !xb);
                 } else {
                     for (int k = 0; k < 2; ++k) {
                         const float E = k ? Eb : Ea, er = k ? rb : ra, w = k ? wb : wa;
@@ -739,8 +824,10 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                         }
                         float A, th, tl;
                         event_terms32(sd, E, ch, A, th, tl);
-                        const float P = prob_fp32(c32, h32, A, th, tl);
-                        acc_event_f32(r, accp, prm, sf, er, P * w, sh, true);
+                        bool x;
+                        const float P = prob_fp32(c32, h32, A, th, tl, x);
+                        redo = redo || x;
+                        acc_event_f32(r, accp, prm, sf, er, P * w, sh, !x);
                     }
                 }
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
@@ -772,8 +859,10 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                     float A, th, tl;
                     event_terms32(sd, E, ch, A, th, tl);
                     const double Ad = sd.kA_rhoye * (double)E;
-                    const float P = prob_mix(c32, h32, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl);
-                    acc_event_f32(r, accp, prm, sf, er, P * w, sh, true);
+                    bool x;
+                    const float P = prob_mix(c32, h32, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl, x);
+                    redo = redo || x;
+                    acc_event_f32(r, accp, prm, sf, er, P * w, sh, !x);
                 }
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
@@ -807,6 +896,14 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 }
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
+            }
+        }
+        if (PREC != kFP64) {
+            // mark the item for the FP64 recomputation of its left-out events
+            const bool any = __any_sync(0xffffffffu, redo);
+            if (any && lane == 0) {
+                prm.redo[it] = 1;
+                atomicAdd(prm.counter + kRedoCount, 1);
             }
         }
         // move to the ticket held ahead and fetch the one after it, or (few
@@ -868,9 +965,10 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                 continue;
             const bool active = lp < wi.n_pts;
             const int pidx = wi.point_base + (active ? lp : wi.n_pts - 1);
-            unsigned long long *accp = prm.acc + 3 * (wi.acc_base + lp) * (int64_t)prm.nbins;
+            unsigned long long *accp = prm.acc + kDigits * (wi.acc_base + lp) * (int64_t)prm.nbins;
             RunAcc r{0ull, 0ull, -1};
             int cur_ch = -1;
+            bool redo = false;  // an event of this item is left to the FP64 recomputation (k_redo)
             if (PREC == kFP32) {
                 const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
                 Pt32 c;
@@ -891,10 +989,19 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                         const float2 aeb = s.ae[has_b ? j2 : j], ttb = s.tt[has_b ? j2 : j], wcb = s.wc[has_b ? j2 : j];
                         const int ca = __float_as_int(wca.y), cb = __float_as_int(wcb.y);
                         if (ca == cur_ch && cb == cur_ch) {
-                            const float Pa = prob_fp32(c, h, aea.x, tta.x, tta.y);
-                            const float Pb = prob_fp32(c, h, aeb.x, ttb.x, ttb.y);
-                            acc_event_f32(r, accp, prm, sf, aea.y, Pa * wca.x, sh, active);
-                            acc_event_f32(r, accp, prm, sf, aeb.y, Pb * wcb.x, sh, active && has_b);
+                            bool xa, xb;
+                            float Pa, Pb;
+                            if (h.real) {
+                                Pa = prob_fp32<true>(c, h, aea.x, tta.x, tta.y, xa);
+                                Pb = prob_fp32<true>(c, h, aeb.x, ttb.x, ttb.y, xb);
+                            } else {
+                                Pa = prob_fp32<false>(c, h, aea.x, tta.x, tta.y, xa);
+                                Pb = prob_fp32<false>(c, h, aeb.x, ttb.x, ttb.y, xb);
+                            }
+                            xb = xb && has_b;
+                            redo = redo || (active && (xa || xb));
+                            acc_event_f32(r, accp, prm, sf, aea.y, Pa * wca.x, sh, active && !xa);
+                            acc_event_f32(r, accp, prm, sf, aeb.y, Pb * wcb.x, sh, active && has_b && !xb);
                         } else {
                             for (int k = 0; k < 2; ++k) {
                                 if (k && !has_b) break;
@@ -904,8 +1011,10 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                                     cur_ch = ch;
                                     load_ch32(pc, ch, h);
                                 }
-                                const float P = prob_fp32(c, h, ae.x, tt.x, tt.y);
-                                acc_event_f32(r, accp, prm, sf, ae.y, P * wc.x, sh, active);
+                                bool x;
+                                const float P = prob_fp32(c, h, ae.x, tt.x, tt.y, x);
+                                redo = redo || (active && x);
+                                acc_event_f32(r, accp, prm, sf, ae.y, P * wc.x, sh, active && !x);
                             }
                         }
                     }
@@ -919,7 +1028,6 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                 Ch32 h;
                 const float sf = pc[C32_ESCALE];
                 const int sh = sd.frac_bits - 150;
-                constexpr double inv2pi = 0.15915494309189533577;
                 for (int t0 = 0; t0 < wi.ev_count; t0 += kET) {
                     const int nt = min(kET, wi.ev_count - t0);
                     __syncthreads();
@@ -932,9 +1040,11 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                             cur_ch = ch;
                             load_ch32(pc, ch, h);
                         }
-                        const float P = prob_mix(c, h, c64, s.a[j], s.tau[j] * inv2pi);
+                        bool x;
+                        const float P = prob_mix(c, h, c64, s.a[j], s.tau[j], x);
+                        redo = redo || (active && x);
                         const float2 ew = s.ew[j];
-                        acc_event_f32(r, accp, prm, sf, ew.x, P * ew.y, sh, active);
+                        acc_event_f32(r, accp, prm, sf, ew.x, P * ew.y, sh, active && !x);
                     }
                 }
             } else {
@@ -962,9 +1072,93 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                     }
                 }
             }
+            if (PREC != kFP64) {
+                // mark the item for the FP64 recomputation of its left-out events
+                if (__syncthreads_or(redo) && tid == 0) {
+                    prm.redo[it] = 1;
+                    atomicAdd(prm.counter + kRedoCount, 1);
+                }
+            }
             acc_finish(r, accp);
         }
         if (prm.fuse_final) fused_final(prm);
+    }
+}
+
+// ------------------------------------------------- FP64 recomputation pass
+// The FP32 precisions' histogram kernels leave out every event whose error
+// estimate exceeds the tolerance (prob_fp32 / prob_mix) and mark its work item.
+// This kernel, launched programmatically after each such histogram kernel,
+// returns at once when no item is marked.  Otherwise one warp per marked item
+// walks the item's points and events, takes the FP32 path's decision again (the
+// same arithmetic on the same inputs gives the same events) and adds the FP64
+// weights of the left-out events to the same exact accumulators, so the bins
+// do not depend on which kernel added which event.  Its last warp converts the
+// bins when the histogram kernel left its fused finalize to it, and resets the
+// counters.  The FP64 arithmetic sits here, out of the FP32 kernels' main loops.
+template <int PREC>
+__global__ void __launch_bounds__(kNT) k_redo(const HistParams prm) {
+    grid_dependents_launch();  // a finalize kernel after this one may become resident early
+    grid_dependency_wait();
+    if (__ldcg(prm.counter + kRedoCount) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int n_warps = (int)(gridDim.x * (blockDim.x >> 5));
+    for (int it = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); it < prm.n_items; it += n_warps) {
+        if (!prm.redo[it]) continue;
+        const WorkItem wi = prm.items[it];
+        const SampleDev &sd = prm.samples[wi.sample];
+        if (debug_ok(wi.ev_begin >= 0 && wi.ev_count >= 0 && wi.ev_begin + wi.ev_count <= sd.n, prm.counter,
+                     kDbgItem)) {
+            const int sh = sd.frac_bits - 150;
+            for (int q = 0; q < wi.n_pts; ++q) {
+                const float *pc32 = prm.pc32 + (int64_t)(wi.point_base + q) * C32_STRIDE;
+                const double *pc64 = prm.pc64 + (int64_t)(wi.point_base + q) * C64_STRIDE;
+                Pt32 c;
+                load_pt32(pc32, c);
+                Pt64 c64;
+                if (PREC == kMix) load_pt64(pc64, c64);
+                const float sf = pc32[C32_ESCALE];
+                unsigned long long *accp = prm.acc + kDigits * (wi.acc_base + q) * (int64_t)prm.nbins;
+                RunAcc r{0ull, 0ull, -1};
+                Ch32 h;
+                int cur_ch = -1;
+                for (int e = lane; e < wi.ev_count; e += 32) {
+                    const float4 rec = sd.ev[wi.ev_begin + e];
+                    const int ch = __float_as_int(rec.w);
+                    if (ch != cur_ch) {
+                        cur_ch = ch;
+                        load_ch32(pc32, ch, h);
+                    }
+                    float A, th, tl;
+                    event_terms32(sd, rec.x, ch, A, th, tl);
+                    bool x;
+                    if (PREC == kFP32) {
+                        prob_fp32(c, h, A, th, tl, x);
+                    } else {
+                        const double Ad = sd.kA_rhoye * (double)rec.x;
+                        prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl, x);
+                    }
+                    if (x) {
+                        const float P = (float)prob_redo64(pc64, ch, rec.x, sd.kA_rhoye, sd.cLL);
+                        acc_event_f32(r, accp, prm, sf, rec.y, P * rec.z, sh, true);
+                    }
+                }
+                acc_finish(r, accp);
+            }
+        }
+        if (lane == 0) prm.redo[it] = 0;  // cleared for the next launch
+    }
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = (atomicAdd(prm.counter + kRedoTicket, 1) == n_warps - 1);
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    if (prm.fuse_final) convert_bins_warp(prm);  // also resets the work and completion counters
+    if (lane == 0) {
+        prm.counter[kRedoCount] = 0;
+        prm.counter[kRedoTicket] = 0;
     }
 }
 
@@ -989,7 +1183,9 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
             }
             float A, th, tl;
             event_terms32(sd, E, ch, A, th, tl);
-            const float P = prob_fp32(c, h, A, th, tl);
+            bool x;
+            float P = prob_fp32(c, h, A, th, tl, x);
+            if (x) P = (float)prob_redo64(r.pc64 + (int64_t)r.point * C64_STRIDE, ch, E, sd.kA_rhoye, sd.cLL);
             const float w = P * q.z;
             const int32_t o = sd.perm[i];
             if (r.out_prob) r.out_prob[o] = (double)P;
@@ -1014,7 +1210,9 @@ __global__ void __launch_bounds__(256) k_reweight(const ReweightParams r) {
             float A, th, tl;
             event_terms32(sd, E, ch, A, th, tl);
             const double Ad = sd.kA_rhoye * (double)E;
-            const float P = prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl);
+            bool x;
+            float P = prob_mix(c, h, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl, x);
+            if (x) P = (float)prob_redo64(r.pc64 + (int64_t)r.point * C64_STRIDE, ch, E, sd.kA_rhoye, sd.cLL);
             const float w = P * q.z;
             const int32_t o = sd.perm[i];
             if (r.out_prob) r.out_prob[o] = (double)P;

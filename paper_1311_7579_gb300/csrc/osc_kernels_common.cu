@@ -37,28 +37,38 @@ __global__ void __launch_bounds__(256) k_final(const FinalParams f) {
     const int64_t n = f.n_hist * (int64_t)f.nbins;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += stride * kFinPerThread) {
-        unsigned long long d[kFinPerThread][3];
+        Digits d[kFinPerThread];
 #pragma unroll
         for (int k = 0; k < kFinPerThread; ++k) {
             const int64_t i = i0 + k * stride;
-            if (i < n) {
-                d[k][0] = __ldcg(f.acc + 3 * i);
-                d[k][1] = __ldcg(f.acc + 3 * i + 1);
-                d[k][2] = __ldcg(f.acc + 3 * i + 2);
-            }
+            if (i < n) d[k] = load_digits(f.acc, i);
         }
 #pragma unroll
         for (int k = 0; k < kFinPerThread; ++k) {
             const int64_t i = i0 + k * stride;
             if (i < n) {
-                f.acc[3 * i] = 0ull;
-                f.acc[3 * i + 1] = 0ull;
-                f.acc[3 * i + 2] = 0ull;
-                f.out[i] = final_bin(d[k][0], d[k][1], d[k][2], f.hmeta + 4 * (i / f.nbins), f.pc64);
+                clear_digits(f.acc, i);
+                f.out[i] = final_bin(d[k], f.hmeta + 4 * (i / f.nbins), f.pc64);
             }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
+}
+
+const void *redo_kernel_fn_fp32();
+const void *redo_kernel_fn_mix();
+
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    static int cached[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
 }
 
 const void *hist_kernel_fn_fp32(int pt);
@@ -138,11 +148,9 @@ __global__ void __launch_bounds__(256) k_final_flag(const FinalFlag p) {
     const int64_t n = f.n_hist * (int64_t)f.nbins;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long d0 = __ldcg(f.acc + 3 * i), d1 = __ldcg(f.acc + 3 * i + 1), d2 = __ldcg(f.acc + 3 * i + 2);
-        f.acc[3 * i] = 0ull;
-        f.acc[3 * i + 1] = 0ull;
-        f.acc[3 * i + 2] = 0ull;
-        f.out[i] = final_bin(d0, d1, d2, f.hmeta + 4 * (i / f.nbins), f.pc64);
+        const Digits g = load_digits(f.acc, i);
+        clear_digits(f.acc, i);
+        f.out[i] = final_bin(g, f.hmeta + 4 * (i / f.nbins), f.pc64);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
     __threadfence_system();
@@ -171,7 +179,7 @@ cudaError_t launch_final_flag(const FinalFlag &p, cudaStream_t st) {
 }
 
 int final_blocks(int64_t n_bins) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n_bins + 255) / 256, 152 * 8));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n_bins + 255) / 256, (int64_t)device_sms() * 8));
 }
 
 cudaError_t launch_final(const FinalParams &p, cudaStream_t st) {
@@ -193,6 +201,82 @@ cudaError_t launch_final_programmatic(const FinalParams &p, cudaStream_t st) {
     FinalParams q = p;
     void *args[] = {&q};
     return cudaLaunchKernelExC(&cfg, (const void *)k_final, args);
+}
+
+// Exact sharded histograms: the accumulators' digit columns copied out (and
+// cleared) instead of converted, launched programmatically after the histogram
+// kernel (or its FP64 recomputation pass); the caller sums such columns over
+// ranks exactly and converts them with k_from_digits.
+__global__ void __launch_bounds__(256) k_digits_out(const FinalParams f, unsigned long long *out) {
+    grid_dependency_wait();
+    const int64_t n = f.n_hist * (int64_t)f.nbins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const Digits g = load_digits(f.acc, i);
+        clear_digits(f.acc, i);
+#pragma unroll
+        for (int q = 0; q < kDigits; ++q) out[kDigits * i + q] = g.d[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *f.counter = 0;
+}
+
+// Bins from digit columns (summed over ranks): the same conversion as every
+// finalize (final_bin), so the bins equal those of one launch over all events.
+__global__ void __launch_bounds__(256) k_from_digits(const unsigned long long *digits, const double *hmeta,
+                                                    const double *pc64, double *out, int64_t n, int32_t nbins) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        Digits g;
+#pragma unroll
+        for (int q = 0; q < kDigits; ++q) g.d[q] = digits[kDigits * i + q];
+        out[i] = final_bin(g, hmeta + 4 * (i / nbins), pc64);
+    }
+}
+
+cudaError_t launch_digits_out_programmatic(const FinalParams &p, unsigned long long *out, cudaStream_t st) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(final_blocks(p.n_hist * (int64_t)p.nbins));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FinalParams q = p;
+    void *args[] = {&q, &out};
+    return cudaLaunchKernelExC(&cfg, (const void *)k_digits_out, args);
+}
+
+cudaError_t launch_from_digits(const unsigned long long *digits, const double *hmeta, const double *pc64, double *out,
+                               int64_t n, int32_t nbins, cudaStream_t st) {
+    k_from_digits<<<final_blocks(n), 256, 0, st>>>(digits, hmeta, pc64, out, n, nbins);
+    return cudaGetLastError();
+}
+
+const void *redo_kernel_fn(int prec) {
+    return prec == kFP32 ? redo_kernel_fn_fp32() : prec == kMix ? redo_kernel_fn_mix() : nullptr;
+}
+
+// Two blocks of eight warps per SM: the pass has work only where events were
+// left out, and one warp takes one marked item.
+int redo_grid() { return 2 * device_sms(); }
+
+cudaError_t launch_redo_programmatic(int prec, const HistParams &p, cudaStream_t st) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(redo_grid());
+    cfg.blockDim = dim3(kNT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HistParams q = p;
+    void *args[] = {&q};
+    return cudaLaunchKernelExC(&cfg, redo_kernel_fn(prec), args);
 }
 
 cudaError_t launch_reweight(int prec, const ReweightParams &p, cudaStream_t st) {

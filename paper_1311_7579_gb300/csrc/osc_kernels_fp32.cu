@@ -1,5 +1,6 @@
 // Histogram and reweight kernel instantiations for one precision (fp32).
 #include "osc_kernels.cuh"
+#include "osc_launch.h"
 
 namespace osc {
 
@@ -28,9 +29,11 @@ cudaError_t launch_hist_fp32(int pt, const HistParams &p, int grid, cudaStream_t
 
 cudaError_t launch_reweight_fp32(const ReweightParams &p, cudaStream_t st) {
     int64_t blocks = (p.s.n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sms() * 16) blocks = device_sms() * 16;
     k_reweight<kFP32><<<(int)blocks, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
+
+const void *redo_kernel_fn_fp32() { return (const void *)k_redo<kFP32>; }
 
 }  // namespace osc

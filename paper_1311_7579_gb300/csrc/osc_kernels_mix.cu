@@ -1,5 +1,6 @@
 // Histogram and reweight kernel instantiations for one precision (FP64 eigen-solve, FP32 amplitude).
 #include "osc_kernels.cuh"
+#include "osc_launch.h"
 
 namespace osc {
 
@@ -28,9 +29,11 @@ cudaError_t launch_hist_mix(int pt, const HistParams &p, int grid, cudaStream_t 
 
 cudaError_t launch_reweight_mix(const ReweightParams &p, cudaStream_t st) {
     int64_t blocks = (p.s.n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sms() * 16) blocks = device_sms() * 16;
     k_reweight<kMix><<<(int)blocks, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
+
+const void *redo_kernel_fn_mix() { return (const void *)k_redo<kMix>; }
 
 }  // namespace osc

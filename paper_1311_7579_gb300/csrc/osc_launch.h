@@ -36,5 +36,18 @@ cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream
 cudaError_t launch_hist_layers(int prec, const HistParams &p, int grid, cudaStream_t st);
 const void *final_kernel_fn();
 int hist_threads();
+// FP32 precisions: the FP64 recomputation pass after a histogram kernel (k_redo),
+// launched with programmatic stream serialization; its kernel function.
+cudaError_t launch_redo_programmatic(int prec, const HistParams &p, cudaStream_t st);
+const void *redo_kernel_fn(int prec);
+int redo_grid();
+// Exact sharded histograms: digit columns out (programmatic, after the
+// histogram kernel or its FP64 recomputation pass; clears the accumulators),
+// and bins from digit columns.
+cudaError_t launch_digits_out_programmatic(const FinalParams &p, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_from_digits(const unsigned long long *digits, const double *hmeta, const double *pc64, double *out,
+                               int64_t n, int32_t nbins, cudaStream_t st);
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sms();
 
 }  // namespace osc

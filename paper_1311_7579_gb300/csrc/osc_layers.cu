@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kNT) k_hist_layers(const HistParams prm) {
             load_lay_point<PREC>(lp, prm.pc32 + (int64_t)cur_point * C32_STRIDE,
                                  prm.pc64 + (int64_t)cur_point * C64_STRIDE);
         }
-        unsigned long long *accp = prm.acc + 3 * wi.acc_base * (int64_t)prm.nbins;
+        unsigned long long *accp = prm.acc + kDigits * wi.acc_base * (int64_t)prm.nbins;
         const int sh = sd.frac_bits - 150;
         const double hs = sd.hscale_d;
         RunAcc r{0ull, 0ull, -1};
@@ -141,7 +141,7 @@ cudaError_t launch_hist_layers(int prec, const HistParams &p, int grid, cudaStre
 }
 
 cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream_t st) {
-    const int blocks = (int)std::min<int64_t>((p.s.n + 255) / 256, 152 * 8);
+    const int blocks = (int)std::min<int64_t>((p.s.n + 255) / 256, (int64_t)device_sms() * 8);
     if (prec == kFP32)
         k_reweight_layers<kFP32><<<blocks, 256, 0, st>>>(p);
     else if (prec == kMix)

@@ -25,9 +25,13 @@
 // whose coefficients carry only FP32 rounding relative to delta itself, so one
 // FP32 Newton step from a trigonometric FP32 seed gives delta to FP32 relative
 // accuracy.  tau delta_l <= tau |A| = c_L L k_A rho Y_e is energy independent
-// (<= 0.72 rad for the workloads here), so those parts of the phases are
+// (<= 0.72 rad for the beam workloads here), so those parts of the phases are
 // accurate in FP32; the large vacuum parts tau (d_l - d_0) are formed in
-// float-float and reduced exactly in revolutions.
+// float-float and reduced exactly in revolutions.  The FP32 amplitude takes the
+// Sylvester numerators in the vacuum mass basis (amplitude_mass32), where every
+// factor is a vacuum gap minus a matter shift, and bounds its own rounding error
+// per event; an event whose bound exceeds the tolerance is recomputed in FP64
+// (prob_redo64, osc_kernels.cuh).
 #pragma once
 
 #include <stdint.h>
@@ -71,11 +75,16 @@ struct Pt32 {
     float d0, d1, d2, g01, g02, g12;
     float v1h, v1l, v2h, v2l;
     float S0, PI0, W0, E0, S1, PI1, W1, E1;
+    float sd02, sd01;                        // d0 + d2, d0 + d1
 };
+// One channel (alpha -> beta, nu or nubar) in the vacuum mass basis.
 struct Ch32 {
-    float Xr, Xi, Yr, Yi, Zr, Zi;
+    float X0r, X0i, X1r, X1i, X2r, X2i;  // X_m = U_bm conj(U_am), m a sorted vacuum state
+    float Zr, Zi;                        // [alpha = e] H0_be + [beta = e] H0_ea
     float ee;    // 1 for the e -> e channel, else 0
     float diag;  // 1 for alpha == beta, else 0
+    float zm;    // |Zr| + |Zi|
+    bool real;   // mu -> mu or tau -> tau: X_m real, Z = 0
 };
 
 // Approximate reciprocal square root (PTX rsqrt.approx); only seeds use it.
@@ -175,62 +184,108 @@ __device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, 
     t3 = (c.T0 + A) * (1.0f / 3.0f);
 }
 
-// |S_ba|^2 from the eigenvalues L1, L2 (FP32), the gaps g_ij = L_i - L_j and the
-// half phases h_l = (phi_l - phi_0) / 2 relative to root 0 [rad].  Sylvester
-// coefficients C_l = N_l / D_l; the projectors sum to the identity, so
+// |S_ba|^2 from the matter shifts delta_l = lambda_l - d_l, the gaps
+// g_ij = lambda_i - lambda_j and the half phases h_l = (phi_l - phi_0) / 2
+// relative to root 0 [rad].  The projectors sum to the identity, so
 // S = delta_ba + sum_{l=1,2} C_l (e^{-i phi_l} - 1) needs no C_0, and
 // e^{-i phi} - 1 = -2 sin(phi/2) (sin(phi/2) + i cos(phi/2)) keeps small phase
-// differences accurate.  The factor -2 sin(phi_l / 2) is folded into 1/D_l:
+// differences accurate; the factor -2 sin(phi_l / 2) is folded into 1/D_l:
 // D_1 = (L1 - L0)(L1 - L2) = -g01 g12, D_2 = (L2 - L0)(L2 - L1) = g02 g12, so
 // w_l = -2 sin(phi_l / 2) / D_l and S = delta_ba + sum_l N_l w_l (sin + i cos)(phi_l / 2).
-__device__ __forceinline__ float amplitude2_32(const Pt32 &c, const Ch32 &h, float A, float L1, float L2, float g01,
-                                              float g02, float g12, float h1, float h2) {
+//
+// Sylvester numerators N_l = [(M - lambda_j)(M - lambda_k)]_ba in the vacuum mass
+// basis: M = U (D + A u u^dagger) U^dagger with u = U^dagger e, and U unitary, give
+//   N_l = sum_m (d_m - lambda_j)(d_m - lambda_k) X_m + A (Z + [ab = ee] (lambda_l - T0)),
+// X_m = U_bm conj(U_am), Z = [a = e] H0_be + [b = e] H0_ea, lambda_l - T0 =
+// delta_l - (the other two d's).  Each factor d_m - lambda_j is a vacuum gap
+// minus a matter shift, so no term carries the cancellation by dm31 / dm21 of
+// the flavour-basis form (M^2)_ba - sigma_l M_ba + pi_l delta_ba.
+//
+// est: the amplitude's rounding error bound in units of 2^-24, the magnitudes of
+// the summed terms of each N_l (and the operands of the A term) times |w_l|.
+// REAL: the mu -> mu and tau -> tau channels (X_m real, Z = 0).
+template <bool REAL>
+__device__ __forceinline__ float amplitude_mass32(const Pt32 &c, const Ch32 &h, float A, float dl0, float dl1,
+                                                  float dl2, float g01, float g02, float g12, float h1, float h2,
+                                                  float &est) {
     float s1, k1, s2, k2;
     __sincosf(h1, &s1, &k1);
     __sincosf(h2, &s2, &k2);
     const float inv2 = 2.0f * rcp_approx(g01 * g02 * g12);
     const float w1 = (g02 * s1) * inv2, w2 = (g01 * s2) * -inv2;
-    const float TA = c.T0 + A;
-    const float c1 = fmaf(A, c.smt, c.c10);
-    const float Kr = fmaf(A, fmaf(A, h.ee, h.Zr), h.Yr), Ki = fmaf(A, h.Zi, h.Yi);
-    const float Gr = fmaf(A, h.ee, h.Xr), Gi = h.Xi;
-    float sg, pp;
-    sg = TA - L1; pp = fmaf(-L1, sg, c1);
-    const float u1 = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * w1, v1 = fmaf(-sg, Gi, Ki) * w1;
-    sg = TA - L2; pp = fmaf(-L2, sg, c1);
-    const float u2 = fmaf(-sg, Gr, fmaf(pp, h.diag, Kr)) * w2, v2 = fmaf(-sg, Gi, Ki) * w2;
-    // S = delta_ba + sum_l (u_l + i v_l)(s_l + i k_l)
-    const float Sr = fmaf(u1, s1, fmaf(-v1, k1, fmaf(u2, s2, fmaf(-v2, k2, h.diag))));
-    const float Si = fmaf(u1, k1, fmaf(v1, s1, fmaf(u2, k2, v2 * s2)));
-    return fmaf(Sr, Sr, Si * Si);
+    // a_m = d_m - lambda_0, b_m = d_m - lambda_2, e_m = d_m - lambda_1 (a_0 = -dl0, b_2 = -dl2, e_1 = -dl1)
+    const float a1 = c.v1h - dl0, a2 = c.v2h - dl0;
+    const float b0 = c.g02 - dl2, b1 = c.g12 - dl2;
+    const float e0 = c.g01 - dl1, e2n = c.g12 + dl1;  // e_2 = -e2n
+    // root 1 (j, k = 0, 2): p_m = a_m b_m;  root 2 (j, k = 0, 1): q_m = a_m e_m
+    const float p0 = -dl0 * b0, p1 = a1 * b1, p2 = -a2 * dl2;
+    const float q0 = -dl0 * e0, q1 = -a1 * dl1, q2 = -a2 * e2n;
+    const float T1 = fabsf(p0) + fabsf(p1) + fabsf(p2), T2 = fabsf(q0) + fabsf(q1) + fabsf(q2);
+    if (REAL) {
+        const float u1 = fmaf(p0, h.X0r, fmaf(p1, h.X1r, p2 * h.X2r)) * w1;
+        const float u2 = fmaf(q0, h.X0r, fmaf(q1, h.X1r, q2 * h.X2r)) * w2;
+        est = fmaf(T1, fabsf(w1), T2 * fabsf(w2));
+        // S = 1 + sum_l u_l (s_l + i k_l)
+        const float Sr = fmaf(u1, s1, fmaf(u2, s2, 1.0f));
+        const float Si = fmaf(u1, k1, u2 * k2);
+        return fmaf(Sr, Sr, Si * Si);
+    } else {
+        const float AZi = A * h.Zi;
+        const float t1 = A * fmaf(h.ee, dl1 - c.sd02, h.Zr), t2 = A * fmaf(h.ee, dl2 - c.sd01, h.Zr);
+        const float n1r = fmaf(p0, h.X0r, fmaf(p1, h.X1r, fmaf(p2, h.X2r, t1)));
+        const float n1i = fmaf(p0, h.X0i, fmaf(p1, h.X1i, fmaf(p2, h.X2i, AZi)));
+        const float n2r = fmaf(q0, h.X0r, fmaf(q1, h.X1r, fmaf(q2, h.X2r, t2)));
+        const float n2i = fmaf(q0, h.X0i, fmaf(q1, h.X1i, fmaf(q2, h.X2i, AZi)));
+        const float u1 = n1r * w1, v1 = n1i * w1, u2 = n2r * w2, v2 = n2i * w2;
+        const float aA = fabsf(A);
+        const float T1a = fmaf(aA, fmaf(h.ee, fabsf(dl1) + fabsf(c.sd02), h.zm), T1);
+        const float T2a = fmaf(aA, fmaf(h.ee, fabsf(dl2) + fabsf(c.sd01), h.zm), T2);
+        est = fmaf(T1a, fabsf(w1), T2a * fabsf(w2));
+        // S = delta_ba + sum_l (u_l + i v_l)(s_l + i k_l)
+        const float Sr = fmaf(u1, s1, fmaf(-v1, k1, fmaf(u2, s2, fmaf(-v2, k2, h.diag))));
+        const float Si = fmaf(u1, k1, fmaf(v1, s1, fmaf(u2, k2, v2 * s2)));
+        return fmaf(Sr, Sr, Si * Si);
+    }
 }
 
 // Matter shifts delta_l = lambda_l - d_l of the three sorted eigenvalues (FP32):
 // trigonometric seed, then one Newton step on each lower root's shifted cubic;
 // the top shift follows from the trace (sum of shifts = A).
-__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
+__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2, float &cth) {
     float m0, m1;
-    seed_scaled32(c, A, m0, m1);
+    seed_scaled32(c, A, m0, m1, cth);
     // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) + m_l
     dl0 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td0) + m0, A, c.S0, c.PI0, c.W0, c.E0);
     dl1 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td1) + m1, A, c.S1, c.PI1, c.W1, c.E1);
     dl2 = A - dl0 - dl1;
 }
+__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
+    float cth;
+    shifts32(c, A, dl0, dl1, dl2, cth);
+}
 
 // P(alpha -> beta) for one event and one point, FP32 bulk.  A: signed matter
-// term [eV^2]; (th, tl): c_L L / (2 pi E_true) as float-float.
-__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl) {
-    float dl0, dl1, dl2;
-    shifts32(c, A, dl0, dl1, dl2);
-    const float L1 = c.d1 + dl1, L2 = c.d2 + dl2;
+// term [eV^2]; (th, tl): c_L L / (2 pi E_true) as float-float.  redo is set
+// when the result may miss the FP32 tolerance: the amplitude's error estimate
+// exceeds kFp32EstMax, or the seed's |cos theta| exceeds kFp32SeedCos.
+template <bool REAL>
+__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl, bool &redo) {
+    float dl0, dl1, dl2, cth;
+    shifts32(c, A, dl0, dl1, dl2, cth);
     // shift differences relative to root 0, shared by the gaps and the phases
     const float dd1 = dl1 - dl0, dd2 = dl2 - dl0;
     const float g01 = c.g01 - dd1, g02 = c.g02 - dd2, g12 = c.g12 + (dd1 - dd2);
     // half phases relative to root 0: pi * revolutions
     const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dd1);
     const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dd2);
-    return amplitude2_32(c, h, A, L1, L2, g01, g02, g12, 3.14159265358979323846f * f1,
-                         3.14159265358979323846f * f2);
+    float est;
+    const float P = amplitude_mass32<REAL>(c, h, A, dl0, dl1, dl2, g01, g02, g12, 3.14159265358979323846f * f1,
+                                           3.14159265358979323846f * f2, est);
+    redo = !(est <= kFp32EstMax) || fabsf(cth) > kFp32SeedCos;
+    return P;
+}
+__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl, bool &redo) {
+    return h.real ? prob_fp32<true>(c, h, A, th, tl, redo) : prob_fp32<false>(c, h, A, th, tl, redo);
 }
 
 // ------------------------------------------------------------------ FP64 path
@@ -383,19 +438,21 @@ __device__ __forceinline__ double prob_fp64(const Pt64 &c, const Ch64 &h, double
     const double c1 = fma(A, c.smt, c.c10);
     const double Kr = fma(A, fma(A, h.ee, h.Zr), h.Yr), Ki = fma(A, h.Zi, h.Yi);
     const double Gr = fma(A, h.ee, h.Xr), Gi = h.Xi;
+    // every multiply-add is an explicit fma, so the rounding sequence (and the
+    // result, bit for bit) is the same in every kernel that inlines this function
     double sg, pp;
-    sg = TA - L1; pp = c1 - L1 * sg;
-    const double C1r = (Kr - sg * Gr + pp * h.diag) * iD1, C1i = (Ki - sg * Gi) * iD1;
-    sg = TA - L2; pp = c1 - L2 * sg;
-    const double C2r = (Kr - sg * Gr + pp * h.diag) * iD2, C2i = (Ki - sg * Gi) * iD2;
+    sg = TA - L1; pp = fma(-L1, sg, c1);
+    const double C1r = fma(pp, h.diag, fma(-sg, Gr, Kr)) * iD1, C1i = fma(-sg, Gi, Ki) * iD1;
+    sg = TA - L2; pp = fma(-L2, sg, c1);
+    const double C2r = fma(pp, h.diag, fma(-sg, Gr, Kr)) * iD2, C2i = fma(-sg, Gi, Ki) * iD2;
     double s1, k1, s2, k2;
     sincos_gap64(tau, c.V1, dl1 - dl0, &s1, &k1);
     sincos_gap64(tau, c.V2, dl2 - dl0, &s2, &k2);
     // e^{-i phi} - 1 = (k - 1) - i s
     const double a1 = k1 - 1.0, a2 = k2 - 1.0;
-    const double Sr = h.diag + C1r * a1 + C1i * s1 + C2r * a2 + C2i * s2;
-    const double Si = C1i * a1 - C1r * s1 + C2i * a2 - C2r * s2;
-    return Sr * Sr + Si * Si;
+    const double Sr = fma(C2i, s2, fma(C2r, a2, fma(C1i, s1, fma(C1r, a1, h.diag))));
+    const double Si = fma(-C2r, s2, fma(C2i, a2, fma(-C1r, s1, C1i * a1)));
+    return fma(Sr, Sr, Si * Si);
 }
 
 // The FP64-eigenvalue variant (FP64 for the cubic eigen-solve and the phases,
@@ -425,17 +482,27 @@ __device__ __forceinline__ void roots_mix(const Pt32 &c, const Pt64 &c64, double
     t3 = (c64.T0 + Ad) * (1.0 / 3.0);
 }
 
-__device__ __forceinline__ float prob_mix(const Pt32 &c, const Ch32 &h, const Pt64 &c64, double Ad, double trev) {
+template <bool REAL>
+__device__ __forceinline__ float prob_mix(const Pt32 &c, const Ch32 &h, const Pt64 &c64, double Ad, double trev,
+                                          bool &redo) {
     const float A = (float)Ad;
     double m0, m1, m2, t3;
     roots_mix(c, c64, Ad, m0, m1, m2, t3);
-    const float L1 = (float)(m1 + t3), L2 = (float)(m2 + t3);
+    // shifts from the FP64 eigenvalues (exact relative to the shift), gaps of the FP64 roots
+    const float dl0 = (float)((m0 + t3) - c64.d0), dl1 = (float)((m1 + t3) - c64.d1), dl2 = (float)((m2 + t3) - c64.d2);
     const float g01 = (float)(m0 - m1), g02 = (float)(m0 - m2), g12 = (float)(m1 - m2);
     // phase differences in revolutions, reduced in FP64, then half angles [rad]
     const double r1 = trev * (m1 - m0), r2 = trev * (m2 - m0);
     const float f1 = (float)(r1 - rint(r1)), f2 = (float)(r2 - rint(r2));
-    return amplitude2_32(c, h, A, L1, L2, g01, g02, g12, 3.14159265358979323846f * f1,
-                         3.14159265358979323846f * f2);
+    float est;
+    const float P = amplitude_mass32<REAL>(c, h, A, dl0, dl1, dl2, g01, g02, g12, 3.14159265358979323846f * f1,
+                                           3.14159265358979323846f * f2, est);
+    redo = !(est <= kFp32EstMax);
+    return P;
+}
+__device__ __forceinline__ float prob_mix(const Pt32 &c, const Ch32 &h, const Pt64 &c64, double Ad, double trev,
+                                          bool &redo) {
+    return h.real ? prob_mix<true>(c, h, c64, Ad, trev, redo) : prob_mix<false>(c, h, c64, Ad, trev, redo);
 }
 
 }  // namespace osc

@@ -25,12 +25,12 @@ constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocScratch {
     double pc64[C64_STRIDE];
     float pc32[C32_STRIDE];
-    unsigned long long acc[3 * kNoAllocMaxBins];  // bin digit columns, as in the main path
-    int counter;                                  // work-item counter
-    int error;                                    // bit 0: an invalid event; bit 1: FP32 outside its domain
+    unsigned long long acc[kDigits * kNoAllocMaxBins];  // bin digit columns, as in the main path
+    int counter;                                        // work-item counter
+    int error;  // bit 0: an invalid event; bit 1: an event outside the pass's precision domain
 };
 
-// The scratch array (about 97 KB).  Host code must not use this name as an
+// The scratch array (about 130 KB).  Host code must not use this name as an
 // address: it is resolved per device with cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
@@ -41,7 +41,7 @@ struct NoAllocParams {
     int32_t chunk, n_items;
     SampleDev sd;        // only the scalar fields are used
     float lo_f, inv_f, nb_f, w_abs_max;
-    float a_lim;         // FP32 domain: |A| <= kFp32MatterRatio |dm31|
+    float a_lim;         // this pass's precision domain: |A| <= a_lim (FP32 bulk: 10 |dm31|, F64EIG: 1000 |dm31|)
     int32_t nbins;
     NoAllocScratch *s;
 };
@@ -52,7 +52,11 @@ __global__ void __launch_bounds__(kConstThreads) k_noalloc_consts(osc_point P, N
 
 // Same per-warp scheme as the one-point histogram path, over events in the
 // caller's order (any order gives the same exact bin sums; events sorted by
-// channel and E_reco flush least often).  Invalid events set the error flag.
+// channel and E_reco flush least often).  Invalid events set the error flag; so
+// do events outside the pass's precision domain, and the host then runs the call
+// again in the next precision (FP32 bulk -> FP32_F64EIG -> FP64).  Unsorted
+// events may flush once per event: the 32-bit digit columns absorb 2^32 flushes
+// a bin, more than the 2^31 - 1 events a call may hold.
 template <int PREC>
 __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) {
     const int lane = threadIdx.x & 31;
@@ -74,7 +78,8 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
         Ch32 h32;
         Pt64 c64;
         Ch64 h64;
-        if (PREC == kFP32) load_pt32(s->pc32, c32); else load_pt64(s->pc64, c64);
+        if (PREC != kFP64) load_pt32(s->pc32, c32);
+        if (PREC != kFP32) load_pt64(s->pc64, c64);
         for (int64_t e = beg + lane; e < end; e += 32) {
             const float E = p.e_true[e], er = p.e_reco[e], w = p.w_mc[e];
             const int a = p.flav_in[e], b = p.flav_out[e], nb = p.is_nubar[e];
@@ -84,15 +89,23 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
                 continue;
             }
             const int ch = chan_id(a, b, nb);
-            if (PREC == kFP32) {
+            if (PREC != kFP64) {
                 if (ch != cur_ch) {
                     cur_ch = ch;
                     load_ch32(s->pc32, ch, h32);
                 }
                 float A, th, tl;
                 event_terms32(p.sd, E, ch, A, th, tl);
-                if (fabsf(A) > p.a_lim) atomicOr(&s->error, 2);  // the host re-runs the call in FP64
-                const float P = prob_fp32(c32, h32, A, th, tl);
+                if (fabsf(A) > p.a_lim) atomicOr(&s->error, 2);  // the host re-runs the call in the next precision
+                bool x;
+                float P;
+                if (PREC == kFP32) {
+                    P = prob_fp32(c32, h32, A, th, tl, x);
+                } else {
+                    const double Ad = p.sd.kA_rhoye * (double)E;
+                    P = prob_mix(c32, h32, c64, (ch >= 9) ? -Ad : Ad, (double)th + (double)tl, x);
+                }
+                if (x) P = (float)prob_redo64(s->pc64, ch, E, p.sd.kA_rhoye, p.sd.cLL);
                 acc_event_f32(r, s->acc, hp, s->pc32[C32_ESCALE], er, P * w, p.sd.frac_bits - 150, true);
             } else {
                 if (ch != cur_ch) {
@@ -111,12 +124,7 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
 __global__ void k_noalloc_final(double *out, int nbins, double s_hi, double s_lo, NoAllocScratch *s) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbins || s->error) return;
-    const unsigned long long d0 = s->acc[3 * b], d1 = s->acc[3 * b + 1], d2 = s->acc[3 * b + 2];
-    const unsigned __int128 v = (unsigned __int128)d0 + ((unsigned __int128)d1 << 40) +
-                                ((unsigned __int128)(__int128)(long long)d2 << 80);
-    const long long hi = (long long)(unsigned long long)(v >> 64);
-    const unsigned long long lo = (unsigned long long)v;
-    out[b] = ((double)hi * s_hi + (double)lo * s_lo) * s->pc64[C64_NORM];
+    out[b] = bin_value(load_digits(s->acc, b), s_hi, s_lo, s->pc64[C64_NORM]);
 }
 
 static void put_err(char *err, size_t len, const char *msg) {
@@ -142,7 +150,7 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
         put_err(err, err_len, "null pointer argument");
         return OSC_E_ARG;
     }
-    if (prec != OSC_FP64 && prec != OSC_FP32_BULK) {
+    if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG) {
         put_err(err, err_len, "bad precision");
         return OSC_E_ARG;
     }
@@ -218,17 +226,25 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
     p.inv_f = (float)((double)nbins / (hi - lo));
     p.nb_f = (float)nbins;
     p.w_abs_max = (float)w_abs_max;
-    p.a_lim = (float)(kFp32MatterRatio * std::fabs(P.dm32 + P.dm21));
     p.nbins = nbins;
     p.s = s;
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    // The FP32 kernel flags events outside its domain; the call then runs again in FP64.
-    bool fp32 = prec == OSC_FP32_BULK;
+    // The precision of the first pass: FP32 bulk needs the sample's matter phase
+    // c_L L k_A rho Y_e within kFp32BulkMatterPhase (else its shifts and phases
+    // go to FP64: F64EIG).  A pass whose kernel flags an event outside its
+    // domain (FP32 bulk: |A| > kFp32BulkMatterRatio |dm31|; F64EIG: |A| >
+    // kFp32MatterRatio |dm31|) is followed by a pass in the next precision.
+    const double adm31 = std::fabs(P.dm32 + P.dm21);
+    int kind = prec == OSC_FP64 ? kFP64 : prec == OSC_FP32_F64EIG ? kMix : kFP32;
+    if (kind == kFP32 && !(kCL * baseline_km * p.sd.kA_rhoye <= kFp32BulkMatterPhase)) kind = kMix;
     int flag = 0;
     for (;;) {
+        p.a_lim = (float)((kind == kFP32 ? kFp32BulkMatterRatio : kFp32MatterRatio) * adm31);
         int per_sm = 1;
-        const void *fn = fp32 ? (const void *)k_noalloc_hist<kFP32> : (const void *)k_noalloc_hist<kFP64>;
+        const void *fn = kind == kFP32 ? (const void *)k_noalloc_hist<kFP32>
+                         : kind == kMix ? (const void *)k_noalloc_hist<kMix>
+                                        : (const void *)k_noalloc_hist<kFP64>;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNT, 0);
         per_sm = std::max(per_sm, 1);
         const int64_t warps = (int64_t)std::max(n_sm, 1) * per_sm * (kNT / 32);
@@ -239,15 +255,17 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)n_sm * per_sm, (p.n_items + 7) / 8));
         // Calls share the scratch and it keeps the previous call's contents: clear
         // the accumulators, the counter and the error flag first.
-        cudaError_t e = cudaMemsetAsync(s->acc, 0, sizeof(unsigned long long) * 3 * (size_t)nbins, st);
+        cudaError_t e = cudaMemsetAsync(s->acc, 0, sizeof(unsigned long long) * kDigits * (size_t)nbins, st);
         if (!e) e = cudaMemsetAsync(&s->counter, 0, 2 * sizeof(int), st);
         if (e) {
             put_err(err, err_len, "cudaMemsetAsync on the scratch array failed");
             return OSC_E_CUDA;
         }
         k_noalloc_consts<<<1, kConstThreads, 0, st>>>(P, s);
-        if (fp32)
+        if (kind == kFP32)
             k_noalloc_hist<kFP32><<<grid, kNT, 0, st>>>(p);
+        else if (kind == kMix)
+            k_noalloc_hist<kMix><<<grid, kNT, 0, st>>>(p);
         else
             k_noalloc_hist<kFP64><<<grid, kNT, 0, st>>>(p);
         k_noalloc_final<<<(nbins + 255) / 256, 256, 0, st>>>(d_out, nbins, std::ldexp(1.0, 64 - F),
@@ -262,8 +280,8 @@ extern "C" osc_status osc_histogram_noalloc(const float *d_e_true, const float *
             put_err(err, err_len, buf);
             return OSC_E_CUDA;
         }
-        if (fp32 && flag == 2) {
-            fp32 = false;
+        if (kind != kFP64 && flag == 2) {
+            kind = kind == kFP32 ? kMix : kFP64;
             continue;
         }
         break;

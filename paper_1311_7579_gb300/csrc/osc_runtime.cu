@@ -97,36 +97,32 @@ osc_status debug_word_check(osc_ctx *c) {
 
 int prec_kind(osc_precision p) { return p == OSC_FP32_BULK ? kFP32 : p == OSC_FP32_F64EIG ? kMix : kFP64; }
 
-bool fp32_in_domain(const osc_point &p, const Sample *s, int prec) {
+// Precisions ordered from the fastest to the most precise.
+static int prec_rank(int k) { return k == kFP32 ? 0 : k == kMix ? 1 : 2; }
+
+int pair_prec(const osc_point &p, const Sample *s, int prec) {
+    if (prec == kFP64) return kFP64;
     const double dm31 = std::fabs(p.dm32 + p.dm21);
     const double a_max = s->ka_max * (double)s->e_max;
-    if (!(a_max <= kFp32MatterRatio * dm31)) return false;
-    if (prec != kFP32 || s->dev.n_layers <= 1) return true;
-    return p.dm21 >= kFp32LayerSolarRatio * dm31 && a_max <= kFp32LayerMatterRatio * dm31;
+    if (!(a_max <= kFp32MatterRatio * dm31)) return kFP64;
+    if (prec == kFP32 && s->dev.n_layers > 1 &&
+        !(p.dm21 >= kFp32LayerSolarRatio * dm31 && a_max <= kFp32LayerMatterRatio * dm31))
+        return kFP64;
+    if (prec == kFP32 && !(s->matter_phase <= kFp32BulkMatterPhase && a_max <= kFp32BulkMatterRatio * dm31))
+        return kMix;
+    return prec;
 }
 
 int call_prec(osc_ctx *c, osc_precision prec, const int32_t *ids, int32_t n_ids, int32_t point_begin,
               int32_t n_points) {
-    const int pr = prec_kind(prec);
-    if (pr == kFP64) return pr;
-    double a_max = 0.0, a_max_layered = 0.0;
-    bool layered = false;
-    for (int32_t i = 0; i < n_ids; ++i) {
+    int pr = prec_kind(prec);
+    for (int32_t i = 0; i < n_ids && pr != kFP64; ++i) {
         const Sample *s = c->samples[ids[i]];
-        const double a = s->ka_max * (double)s->e_max;
-        a_max = std::max(a_max, a);
-        if (s->dev.n_layers > 1) {
-            layered = true;
-            a_max_layered = std::max(a_max_layered, a);
+        for (int32_t k = point_begin; k < point_begin + n_points; ++k) {
+            const int q = pair_prec(c->pts[k], s, pr);
+            if (prec_rank(q) > prec_rank(pr)) pr = q;
+            if (pr == kFP64) break;
         }
-    }
-    for (int32_t k = point_begin; k < point_begin + n_points; ++k) {
-        const osc_point &p = c->pts[k];
-        const double dm31 = std::fabs(p.dm32 + p.dm21);
-        if (!(a_max <= kFp32MatterRatio * dm31)) return kFP64;
-        if (pr == kFP32 && layered &&
-            !(p.dm21 >= kFp32LayerSolarRatio * dm31 && a_max_layered <= kFp32LayerMatterRatio * dm31))
-            return kFP64;
     }
     return pr;
 }
@@ -154,9 +150,9 @@ osc_status ensure_acc(osc_ctx *c, int64_t bins) {
     if (bins <= c->acc_cap_bins) return OSC_OK;
     int64_t want = std::max<int64_t>(bins, 1024);
     void *p;
-    osc_status s = dalloc(c, &p, (size_t)want * 24);
+    osc_status s = dalloc(c, &p, (size_t)want * kDigits * sizeof(unsigned long long));
     if (s) return s;
-    cudaError_t e = cudaMemsetAsync(p, 0, (size_t)want * 24, c->stream);
+    cudaError_t e = cudaMemsetAsync(p, 0, (size_t)want * kDigits * sizeof(unsigned long long), c->stream);
     if (e) return fail_cuda(c, e, "cudaMemsetAsync(acc)");
     if (c->d_acc) {
         cudaStreamSynchronize(c->stream);
@@ -240,6 +236,7 @@ static void fill_hist_params(HistParams &hp, const WorkItem *d_items, int32_t n_
     hp.lo_f = (float)lo;
     hp.inv_f = (float)((double)nbins / (hi - lo));
     hp.nb_f = (float)nbins;
+    hp.redo = nullptr;
     hp.fuse_final = 0;
     hp.fin_n_hist = 0;
     hp.fin_hmeta = nullptr;
@@ -362,6 +359,7 @@ static void free_plan(osc_ctx *c, Plan *p) {
     dfree(c, p->d_items);
     dfree(c, p->d_samples);
     dfree(c, p->d_hmeta);
+    dfree(c, p->d_redo);
     dfree(c, p->d_rows);
     dfree(c, p->d_rowmap);
     dfree(c, p->d_tab);
@@ -477,6 +475,7 @@ void osc_destroy(osc_ctx *ctx) {
     dfree(ctx, ctx->d_counter);
     dfree(ctx, ctx->d_out);
     dfree(ctx, ctx->d_rw);
+    dfree(ctx, ctx->d_aux);
     for (auto &p : ctx->ev_pending) {
         cudaEventDestroy(p.second.first);
         cudaEventDestroy(p.second.second);
@@ -552,7 +551,9 @@ osc_status osc_load_sample(osc_ctx *ctx, const osc_sample_desc *d, int32_t *samp
     s->frac_bits = F;
     s->chan_mask = mask;
     s->e_max = e_max;
+    s->w_abs = wmax;
     s->ka_max = matter_k_A() * d->density_gcc * d->ye;
+    s->matter_phase = kCL * d->baseline_km * s->ka_max;
     osc_status st = OSC_OK;
     void *p;
     if ((st = dalloc(ctx, &p, n_pad * sizeof(float4))) == OSC_OK) s->ev = (float4 *)p;
@@ -616,8 +617,11 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
     if (ctx->serve) return fail(ctx, OSC_E_STATE, "cannot change a sample's path while serving runs");
     Sample *s = it->second;
     void *lay = nullptr;
-    double ka_max = 0.0;
-    for (int k = 0; k < n_layers; ++k) ka_max = std::max(ka_max, matter_k_A() * density_gcc[k] * ye[k]);
+    double ka_max = 0.0, matter_phase = 0.0;
+    for (int k = 0; k < n_layers; ++k) {
+        ka_max = std::max(ka_max, matter_k_A() * density_gcc[k] * ye[k]);
+        matter_phase += kCL * length_km[k] * matter_k_A() * density_gcc[k] * ye[k];
+    }
     if (n_layers > 1) {
         std::vector<float4> l32(n_layers);
         std::vector<double2> l64(n_layers);
@@ -643,6 +647,7 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
     dfree(ctx, s->lay);
     s->lay = lay;
     s->ka_max = ka_max;
+    s->matter_phase = matter_phase;
     SampleDev &sd = s->dev;
     if (n_layers == 1) {
         s->L = length_km[0];
@@ -934,6 +939,9 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     if ((st = dalloc(ctx, &a, items.size() * sizeof(WorkItem))) == OSC_OK) p->d_items = (WorkItem *)a;
     if (!st && (st = dalloc(ctx, &a, sdev.size() * sizeof(SampleDev))) == OSC_OK) p->d_samples = (SampleDev *)a;
     if (!st && (st = dalloc(ctx, &a, hmeta.size() * sizeof(double))) == OSC_OK) p->d_hmeta = (double *)a;
+    // FP32 precisions: one flag per work item for the FP64 recomputation pass (zero between launches)
+    const bool redo = kind == kEventByEvent && prec != kFP64;
+    if (!st && redo && (st = dalloc(ctx, &a, items.size())) == OSC_OK) p->d_redo = (uint8_t *)a;
     if (st) {
         free_plan(ctx, p);
         return st;
@@ -941,6 +949,7 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
     cudaError_t e = cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(p->d_samples, sdev.data(), sdev.size() * sizeof(SampleDev), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(p->d_hmeta, hmeta.data(), hmeta.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (!e && redo) e = cudaMemset(p->d_redo, 0, items.size());
     if (e) {
         free_plan(ctx, p);
         return fail_cuda(ctx, e, "cudaMemcpy(plan)");
@@ -954,13 +963,24 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
 // Histogram kernel, then (outputs of more than one conversion round) the
 // finalize kernel.  Timing mode runs them as a CUDA graph with event-record
 // nodes around each kernel, parameters refreshed per call.
-static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *d_out) {
+// d_digits (exact sharded histograms): the digit columns go there instead of
+// being converted, by direct launches in every mode.
+static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *d_out,
+                           unsigned long long *d_digits = nullptr) {
     HistParams hp;
     fill_hist_params(hp, p->d_items, p->n_items, p->d_samples, ctx->d_pc32, ctx->d_pc64, ctx->d_acc, ctx->d_counter,
                      p->nbins, lo, hi);
+    hp.redo = p->d_redo;
     FinalParams fp{ctx->d_acc, p->d_hmeta, ctx->d_pc64, d_out, p->n_hist, p->nbins, ctx->d_counter};
     void *hargs[] = {&hp};
     void *fargs[] = {&fp};
+    cudaKernelNodeParams kr{};
+    if (p->d_redo) {
+        kr.func = (void *)redo_kernel_fn(p->prec);
+        kr.gridDim = dim3(redo_grid());
+        kr.blockDim = dim3(hist_threads());
+        kr.kernelParams = hargs;
+    }
     cudaKernelNodeParams kh{};
     kh.func = (void *)plan_kernel(p);
     kh.gridDim = dim3(p->grid);
@@ -973,14 +993,14 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     kf.gridDim = dim3((unsigned)fb);
     kf.blockDim = dim3(256);
     kf.kernelParams = fargs;
-    const bool fused = fuse_finalize(p->n_hist, p->nbins, p->pt);
+    const bool fused = !d_digits && fuse_finalize(p->n_hist, p->nbins, p->pt);
     if (fused) {
         hp.fuse_final = 1;
         hp.fin_n_hist = p->n_hist;
         hp.fin_hmeta = p->d_hmeta;
         hp.fin_out = d_out;
     }
-    if (!ctx->timing) {
+    if (!ctx->timing || d_digits) {
         // Direct launches.  The event-by-event histogram kernel goes with
         // programmatic stream serialization: it starts (and fetches its first
         // work) while the constants kernel before it is still running, and waits
@@ -998,7 +1018,12 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
         cfg.attrs = at;
         cfg.numAttrs = p->kind == kEventByEvent ? 1 : 0;
         CK(cudaLaunchKernelExC(&cfg, kh.func, hargs));
-        if (!fused) CK(launch_final_programmatic(fp, ctx->stream));
+        // FP32 precisions: the FP64 recomputation pass (returns at once when no event was left out)
+        if (p->d_redo) CK(launch_redo_programmatic(p->prec, hp, ctx->stream));
+        if (d_digits)
+            CK(launch_digits_out_programmatic(fp, d_digits, ctx->stream));
+        else if (!fused)
+            CK(launch_final_programmatic(fp, ctx->stream));
     } else {
         // timing mode: the same graph with event-record nodes around each kernel,
         // fresh events swapped in per launch (read later without blocking the stream)
@@ -1012,14 +1037,20 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
             CK(cudaGraphAddEventRecordNode(&p->t_ev[0], p->graph_t, nullptr, 0, ev[0]));
             CK(cudaGraphAddKernelNode(&p->t_hist_node, p->graph_t, &p->t_ev[0], 1, &kh));
             CK(cudaGraphAddEventRecordNode(&p->t_ev[1], p->graph_t, &p->t_hist_node, 1, ev[1]));
+            cudaGraphNode_t tail = p->t_ev[1];
+            if (p->d_redo) {
+                CK(cudaGraphAddKernelNode(&p->t_redo_node, p->graph_t, &p->t_ev[1], 1, &kr));
+                tail = p->t_redo_node;
+            }
             if (!fused) {
-                CK(cudaGraphAddEventRecordNode(&p->t_ev[2], p->graph_t, &p->t_ev[1], 1, ev[2]));
+                CK(cudaGraphAddEventRecordNode(&p->t_ev[2], p->graph_t, &tail, 1, ev[2]));
                 CK(cudaGraphAddKernelNode(&p->t_final_node, p->graph_t, &p->t_ev[2], 1, &kf));
                 CK(cudaGraphAddEventRecordNode(&p->t_ev[3], p->graph_t, &p->t_final_node, 1, ev[3]));
             }
             CK(cudaGraphInstantiate(&p->exec_t, p->graph_t, 0));
         } else {
             CK(cudaGraphExecKernelNodeSetParams(p->exec_t, p->t_hist_node, &kh));
+            if (p->d_redo) CK(cudaGraphExecKernelNodeSetParams(p->exec_t, p->t_redo_node, &kr));
             if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->exec_t, p->t_final_node, &kf));
             for (int k = 0; k < (fused ? 2 : 4); ++k) CK(cudaGraphExecEventRecordNodeSetEvent(p->exec_t, p->t_ev[k], ev[k]));
         }
@@ -1027,7 +1058,7 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
         ctx->ev_pending.push_back({1, {ev[0], ev[1]}});
         if (!fused) ctx->ev_pending.push_back({2, {ev[2], ev[3]}});
     }
-    ctx->launches += fused ? 1 : 2;
+    ctx->launches += (fused ? 1 : 2) + (p->d_redo ? 1 : 0);
     return OSC_OK;
 }
 
@@ -1055,12 +1086,13 @@ static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     return st;
 }
 
-extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
-                                    int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
-                                    double *out, int out_on_device) {
-    NvtxRange nvtx_range("osc_histogram");
+// osc_histogram, and (digits != null) osc_histogram_digits: the same call with
+// the bins' digit columns as its output instead of doubles.
+static osc_status histogram_impl(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
+                                 int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
+                                 double *out, uint64_t *digits, int out_on_device) {
     CHECK_CTX(ctx);
-    if (!sample_ids || !out) return fail(ctx, OSC_E_ARG, "null argument");
+    if (!sample_ids || !(out || digits)) return fail(ctx, OSC_E_ARG, "null argument");
     if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
         return fail(ctx, OSC_E_ARG, "bad precision");
     if (n_samples < 1 || n_samples > 4096) return fail(ctx, OSC_E_ARG, "n_samples must be in [1, 4096]");
@@ -1123,21 +1155,107 @@ extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int
     Plan *p = nullptr;
     st = get_plan(ctx, ids, point_begin, n_points, pr, nbins, pt, chunk, &p, layered ? kLayered : kEventByEvent);
     if (st) return st;
-    double *d_out = out;
+    // output: doubles, or kDigits words a bin (the same byte count per word)
+    const int64_t words = digits ? bins * kDigits : bins;
+    double *host = digits ? (double *)digits : out;
+    double *d_out = host;
     bool staged = false;
-    if (!out_on_device && !(d_out = pinned_device_ptr(out))) {
-        st = ensure_buf(ctx, &ctx->d_out, &ctx->out_cap, bins);
+    if (!out_on_device && !(d_out = pinned_device_ptr(host))) {
+        st = ensure_buf(ctx, &ctx->d_out, &ctx->out_cap, words);
         if (st) return st;
         d_out = ctx->d_out;
         staged = true;
     }
-    st = run_plan(ctx, p, lo, hi, d_out);
+    st = digits ? run_plan(ctx, p, lo, hi, nullptr, (unsigned long long *)d_out) : run_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
-    if (staged) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (staged) CK(cudaMemcpyAsync(host, d_out, words * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (!out_on_device) {
         CK(cudaStreamSynchronize(ctx->stream));
         return debug_word_check(ctx);
     }
+    return OSC_OK;
+}
+
+extern "C" osc_status osc_histogram(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
+                                    int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
+                                    double *out, int out_on_device) {
+    NvtxRange nvtx_range("osc_histogram");
+    if (!out) return ctx ? fail(ctx, OSC_E_ARG, "null argument") : OSC_E_ARG;
+    return histogram_impl(ctx, sample_ids, n_samples, point_begin, n_points, prec, lo, hi, nbins, out, nullptr,
+                          out_on_device);
+}
+
+// ------------------------------------------------- exact sharded histograms
+extern "C" osc_status osc_histogram_digits(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                                           int32_t point_begin, int32_t n_points, osc_precision prec, double lo,
+                                           double hi, int32_t nbins, uint64_t *digits, int out_on_device) {
+    NvtxRange nvtx_range("osc_histogram_digits");
+    if (!digits) return ctx ? fail(ctx, OSC_E_ARG, "null argument") : OSC_E_ARG;
+    return histogram_impl(ctx, sample_ids, n_samples, point_begin, n_points, prec, lo, hi, nbins, nullptr, digits,
+                          out_on_device);
+}
+
+extern "C" osc_status osc_histogram_from_digits(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples,
+                                                int32_t point_begin, int32_t n_points, int32_t nbins,
+                                                const uint64_t *digits, double *out, int on_device) {
+    NvtxRange nvtx_range("osc_histogram_from_digits");
+    CHECK_CTX(ctx);
+    if (!sample_ids || !digits || !out) return fail(ctx, OSC_E_ARG, "null argument");
+    if (n_samples < 1 || n_samples > 4096) return fail(ctx, OSC_E_ARG, "n_samples must be in [1, 4096]");
+    if (nbins < 1 || nbins > (1 << 20)) return fail(ctx, OSC_E_ARG, "nbins must be in [1, 2^20]");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if (n_points < 1 || point_begin < 0 || (int64_t)point_begin + n_points > (int64_t)ctx->pts.size())
+        return fail(ctx, OSC_E_ARG, "point range outside the parameter table");
+    std::vector<const Sample *> ss;
+    for (int32_t i = 0; i < n_samples; ++i) {
+        auto it = ctx->samples.find(sample_ids[i]);
+        if (it == ctx->samples.end()) return fail(ctx, OSC_E_ARG, "unknown sample id");
+        ss.push_back(it->second);
+    }
+    const int64_t bins = (int64_t)n_samples * n_points * nbins;
+    const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
+    // staging: the histograms' metadata, then (host input) the digit columns, then (pageable output) the bins
+    const int64_t n_meta = (int64_t)hmeta.size();
+    const int64_t n_dig = on_device ? 0 : bins * kDigits;
+    double *d_host_out = on_device ? out : pinned_device_ptr(out);
+    const int64_t n_stage_out = d_host_out ? 0 : bins;
+    osc_status st = ensure_buf(ctx, &ctx->d_aux, &ctx->aux_cap, n_meta + n_dig + n_stage_out);
+    if (st) return st;
+    double *d_meta = ctx->d_aux;
+    const unsigned long long *d_dig = on_device ? (const unsigned long long *)digits
+                                                : (const unsigned long long *)(ctx->d_aux + n_meta);
+    double *d_out = d_host_out ? d_host_out : ctx->d_aux + n_meta + n_dig;
+    CK(cudaMemcpyAsync(d_meta, hmeta.data(), n_meta * 8, cudaMemcpyHostToDevice, ctx->stream));
+    if (!on_device) CK(cudaMemcpyAsync((void *)d_dig, digits, n_dig * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_from_digits(d_dig, d_meta, ctx->d_pc64, d_out, bins, nbins, ctx->stream));
+    ctx->launches += 1;
+    if (!d_host_out) CK(cudaMemcpyAsync(out, d_out, bins * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return OSC_OK;
+}
+
+extern "C" osc_status osc_sample_set_bounds(osc_ctx *ctx, int32_t sample_id, double w_abs_max, double e_true_max) {
+    NvtxRange nvtx_range("osc_sample_set_bounds");
+    CHECK_CTX(ctx);
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    auto it = ctx->samples.find(sample_id);
+    if (it == ctx->samples.end()) return fail(ctx, OSC_E_ARG, "unknown sample id");
+    if (ctx->serve) return fail(ctx, OSC_E_STATE, "cannot change a sample's bounds while serving runs");
+    Sample *s = it->second;
+    if (!(std::isfinite(w_abs_max) && w_abs_max >= s->w_abs && w_abs_max > 0 && w_abs_max < 3.0e38))
+        return fail(ctx, OSC_E_RANGE, "w_abs_max must be finite, > 0 and at least the sample's own largest |w_mc|");
+    if (!(std::isfinite(e_true_max) && e_true_max >= (double)s->e_max && e_true_max < 3.0e38))
+        return fail(ctx, OSC_E_RANGE, "e_true_max must be finite and at least the sample's own largest E_true");
+    int F = 62 - (int)std::ceil(std::log2(w_abs_max));
+    F = std::max(8, std::min(F, 190));
+    float e = (float)e_true_max;
+    if ((double)e < e_true_max) e = std::nextafter(e, INFINITY);
+    drop_plans(ctx);  // plans hold copies of the sample's scale
+    s->frac_bits = F;
+    s->e_max = e;
+    s->dev.frac_bits = F;
+    s->dev.hscale_d = std::ldexp(1.0, F - 64);
+    s->dev.hscale_f = (float)s->dev.hscale_d;
     return OSC_OK;
 }
 

@@ -77,6 +77,7 @@ struct Batch {
     double *d_pc64 = nullptr;
     unsigned long long *d_acc = nullptr;
     int32_t *d_counter = nullptr;
+    uint8_t *d_redo = nullptr;  // FP32 precisions: per work item, marked for the FP64 recomputation pass
     // pinned host memory: staging block (same layout) and the results, which the
     // finalize writes directly (d_out is h_out's device address)
     char *h_stage = nullptr;
@@ -211,6 +212,7 @@ osc_status launch_batch(osc_serve *sv, Batch &b) {
     hp.lo_f = (float)sv->lo;
     hp.inv_f = (float)((double)sv->nbins / (sv->hi - sv->lo));
     hp.nb_f = (float)sv->nbins;
+    hp.redo = nullptr;
     hp.fuse_final = 0;  // the flag-writing finalize kernel below converts the bins
     hp.fin_n_hist = 0;
     hp.fin_hmeta = nullptr;
@@ -233,8 +235,14 @@ osc_status launch_batch(osc_serve *sv, Batch &b) {
         hs.items = b.d_items + n_lay;
         hs.n_items = n_items - n_lay;
         // programmatic launch after the kernel before it (constants or layered histogram)
+        if (prec != kFP64) hs.redo = b.d_redo;
         e = launch_hist_programmatic(prec, 1, hs, hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + 7) / 8), st);
         ++kernels;
+        // FP32 precisions: the FP64 recomputation pass (returns at once when no event was left out)
+        if (!e && prec != kFP64) {
+            e = launch_redo_programmatic(prec, hs, st);
+            ++kernels;
+        }
     }
     FinalFlag ff{{b.d_acc, b.d_hmeta, b.d_pc64, b.d_out, (int64_t)n, sv->nbins, b.d_counter}, b.d_flag, b.seq + 1,
                  b.d_counter + kFlagTicket};
@@ -366,6 +374,7 @@ void free_serve(osc_ctx *ctx, osc_serve *sv) {
         dfree(ctx, b.d_pc32);
         dfree(ctx, b.d_pc64);
         dfree(ctx, b.d_acc);
+        dfree(ctx, b.d_redo);
         dfree(ctx, b.d_counter);
         cudaFreeHost(b.h_stage);
         cudaFreeHost(b.h_out);
@@ -402,15 +411,17 @@ osc_status osc_serve_start(osc_ctx *ctx, int32_t max_slots, double lo, double hi
         if (!st && !(st = dalloc(ctx, &p, b.lay.bytes))) b.d_stage = (char *)p;
         if (!st && !(st = dalloc(ctx, &p, S * C32_STRIDE * 4))) b.d_pc32 = (float *)p;
         if (!st && !(st = dalloc(ctx, &p, S * C64_STRIDE * 8))) b.d_pc64 = (double *)p;
-        if (!st && !(st = dalloc(ctx, &p, S * B * 24))) b.d_acc = (unsigned long long *)p;
+        if (!st && !(st = dalloc(ctx, &p, S * B * kDigits * sizeof(unsigned long long)))) b.d_acc = (unsigned long long *)p;
         if (!st && !(st = dalloc(ctx, &p, 64))) b.d_counter = (int32_t *)p;
+        if (!st && !(st = dalloc(ctx, &p, kMaxItems))) b.d_redo = (uint8_t *)p;
         if (!st) {
             b.d_pts = (osc_point *)(b.d_stage + b.lay.pts);
             b.d_hmeta = (double *)(b.d_stage + b.lay.hmeta);
             b.d_samples = (SampleDev *)(b.d_stage + b.lay.samples);
             b.d_items = (WorkItem *)(b.d_stage + b.lay.items);
-            e = cudaMemsetAsync(b.d_acc, 0, S * B * 24, b.stream);
+            e = cudaMemsetAsync(b.d_acc, 0, S * B * kDigits * sizeof(unsigned long long), b.stream);
             if (!e) e = cudaMemsetAsync(b.d_counter, 0, 64, b.stream);
+            if (!e) e = cudaMemsetAsync(b.d_redo, 0, kMaxItems, b.stream);
             if (!e) e = cudaHostAlloc((void **)&b.h_stage, b.lay.bytes, 0);
             if (!e) e = cudaHostAlloc((void **)&b.h_out, S * B * 8, cudaHostAllocMapped);
             if (!e) e = cudaHostGetDevicePointer((void **)&b.d_out, b.h_out, 0);
@@ -452,7 +463,7 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
         if (it == ctx->samples.end()) return OSC_E_ARG;
         r.sd = it->second->dev;
         r.frac_bits = it->second->frac_bits;
-        r.prec = fp32_in_domain(*pt, it->second, prec_kind(prec)) ? prec_kind(prec) : kFP64;
+        r.prec = pair_prec(*pt, it->second, prec_kind(prec));
     }
     r.pt = *pt;
     {

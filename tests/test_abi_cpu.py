@@ -108,3 +108,37 @@ def test_oracle_library_builds():
     import oracle
     oracle.build()
     assert oracle.num_threads() >= 1
+
+
+def test_noalloc_wrapper_rejects_bad_tensors_before_any_call():
+    """osc_histogram_noalloc's binding checks the caller's tensors (the library
+    only sees pointers): CPU tensors, wrong dtypes, unequal lengths and a short
+    or non-float64 output are each rejected with OSC_E_ARG before the library
+    is called."""
+    torch = pytest.importorskip("torch")
+    from paper_1311_7579_gb300 import synth
+
+    n = 64
+    f = torch.zeros(n, dtype=torch.float32)
+    u = torch.zeros(n, dtype=torch.uint8)
+    out = torch.zeros(100, dtype=torch.float64)
+    pt = synth.table1_point()
+
+    def call(*arrs, out=out, nbins=100):
+        api.osc_histogram_noalloc(*arrs, 295.0, 2.6, 0.5, 1.5, pt, "fp32", 0.0, 5.0, nbins, out)
+
+    cases = [(f, f, f, u, u, u)]  # CPU tensors
+    if torch.cuda.is_available():
+        fc, uc = f.cuda(), u.cuda()
+        cases = [(f, fc, fc, uc, uc, uc), (fc, fc, fc.double(), uc, uc, uc), (fc, fc, fc, uc.int(), uc, uc),
+                 (fc, fc[:10], fc, uc, uc, uc), (fc, fc, fc, uc, uc, uc[:-1])]
+    for arrs in cases:
+        with pytest.raises(api.OscError) as e:
+            call(*arrs)
+        assert e.value.status == api.OSC_E_ARG
+    if torch.cuda.is_available():
+        fc, uc = f.cuda(), u.cuda()
+        for bad_out in (out, out.cuda().float(), out.cuda()[:50]):
+            with pytest.raises(api.OscError) as e:
+                call(fc, fc, fc, uc, uc, uc, out=bad_out)
+            assert e.value.status == api.OSC_E_ARG

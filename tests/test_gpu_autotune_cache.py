@@ -30,7 +30,8 @@ def test_tuned_shapes_persist_across_contexts(tmp_path, monkeypatch):
     assert int(pt) in (1, 4, 16, 64, 256) and int(chunk) % 64 == 0
     h2, launches2 = _run(s, pts)
     assert launches1 > 4 * launches2  # the first call timed several candidate shapes
-    assert launches2 <= 2  # histogram kernel (+ finalize kernel for this output size)
+    # histogram kernel, the FP64 recomputation pass of the FP32 precisions (+ finalize kernel for this output size)
+    assert launches2 <= 3
     assert np.array_equal(h1, h2)
     # a corrupt cache is ignored, not fatal
     cache.write_text("garbage line\nanother\n")

@@ -6,13 +6,22 @@ the C ABI), single layer and through random layer profiles:
     either ordering, any delta; baselines 1-13000 km, densities 0-13 g/cm^3,
     E_true log-uniform in [0.05, 50] GeV, every channel, nu and nubar.
 
-This is where the eigenvalue cubic has near-double roots: tiny splittings under
-large matter terms, and tiny solar splittings in vacuum-like conditions.  The
-FP64 path must stay at its rounding floor (|dP| <= 1e-10; phases reach ~1e6 rad,
-so the floor here is ~1e-11).  The FP32 precisions must never return nonsense: a
-call outside their domain runs in FP64 (include/osc.h, osc_precision), and
-inside it their error stays below 1e-2 (measured: 2.3e-3 single layer at extreme
-mixing angles, 4.2e-3 through layers; workload parameters stay below 1e-4).
+This is where the eigenvalue cubic has near-double roots and the resonances are
+narrow.  Both FP32 precisions must hold the FP32 tolerance |dP| <= 1e-5 for every
+event: what FP32 arithmetic cannot resolve runs with FP64 shifts and phases
+(FP32_F64EIG) or in FP64, per call or per event (include/osc.h, osc_precision).
+
+FP64: the phases reach ~1e6 rad here, and an FP64 evaluation of the definition
+(the GPU's or the oracle's) carries a phase error of order 2^-53 times the
+phase.  Each event's bound is therefore 1e-12 + 4 * 2^-52 * Phi, with Phi =
+c_L L (|dm31| + dm21 + |A|) / E_true an upper bound of its largest phase (the
+reading of Sec. 2.2's 1e-12 over this domain); events with Phi <= 1e3 rad, the
+scale of the paper's validation at 295 km, are held to 1e-12 itself.  Through
+layers (a generalisation the paper does not have) the FP64 layer update, whose
+eigenvector weights divide by the distance of an eigenvalue in matter from a
+vacuum eigenvalue, is less well conditioned than the single-layer form, and
+its bound is TOL64_LAYERS = 5e-11 (measured 1.55e-11 at worst, at phases
+below 1e3 rad).
 """
 import numpy as np
 import pytest
@@ -24,8 +33,11 @@ pytestmark = pytest.mark.gpu
 
 N = 5000
 TRIALS = 40
-TOL64 = 1e-10
-TOL32_GROSS = 1e-2
+TOL64 = 1e-12
+TOL64_LAYERS = 5e-11
+TOL32 = 1e-5
+C_L = 2.533865  # rad per (eV^2 km / GeV)
+K_A = 1.526493e-4  # eV^2 per GeV per g/cm^3
 
 
 def _point(rng):
@@ -47,6 +59,8 @@ def _sample(rng):
 def test_random_points_over_the_accepted_domain(layered):
     rng = np.random.default_rng(20261204 + int(layered))
     worst = {"fp64": 0.0, "fp32": 0.0, "fp32_f64eig": 0.0}
+    worst64_ratio = 0.0   # FP64 |dP| over its phase-conditioned bound
+    worst64_small = 0.0   # FP64 |dP| over events with Phi <= 1e3 rad
     with api.Context(0) as c:
         for _ in range(TRIALS):
             pt = _point(rng)
@@ -57,15 +71,31 @@ def test_random_points_over_the_accepted_domain(layered):
                           for _ in range(int(rng.integers(2, 6)))]
                 api.osc_set_layers(c.ptr, sid, layers)
                 ref, _ = oracle.reweight_layers(s, oracle.point_from_row(pt), layers)
+                L_tot = sum(x[0] for x in layers)
+                ka = max(K_A * x[1] * x[2] for x in layers)
             else:
                 ref, _ = oracle.reweight(s, oracle.point_from_row(pt))
+                L_tot = s["baseline_km"]
+                ka = K_A * s["density_gcc"] * s["ye"]
+            E = s["e_true"].astype(np.float64)
+            phi = C_L * L_tot * (abs(pt[4] + pt[3]) + pt[3] + ka * E) / E
+            bound64 = TOL64 + 4 * 2.0 ** -52 * phi
             api.osc_set_params(c.ptr, pt[None, :])
             for prec in worst:
                 p = np.zeros(N)
                 api.osc_reweight(c.ptr, sid, 0, prec, out_prob=p)
                 assert np.all(np.isfinite(p)), prec
-                worst[prec] = max(worst[prec], float(np.max(np.abs(p - ref))))
+                d = np.abs(p - ref)
+                worst[prec] = max(worst[prec], float(np.max(d)))
+                if prec == "fp64":
+                    worst64_ratio = max(worst64_ratio, float(np.max(d / bound64)))
+                    small = phi <= 1e3
+                    if small.any():
+                        worst64_small = max(worst64_small, float(np.max(d[small])))
             api.osc_unload_sample(c.ptr, sid)
-    print("worst |dP|", worst)
-    assert worst["fp64"] <= TOL64, worst
-    assert worst["fp32"] <= TOL32_GROSS and worst["fp32_f64eig"] <= TOL32_GROSS, worst
+    print("worst |dP|", worst, "fp64 / bound", worst64_ratio, "fp64 at Phi <= 1e3", worst64_small)
+    if layered:
+        assert worst["fp64"] <= TOL64_LAYERS, worst
+    else:
+        assert worst64_ratio <= 1.0 and worst64_small <= TOL64, (worst, worst64_ratio, worst64_small)
+    assert worst["fp32"] <= TOL32 and worst["fp32_f64eig"] <= TOL32, worst
