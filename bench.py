@@ -4,11 +4,12 @@ Workload (one step = one pass of the whole hot path over one batch): the
 precision-study configuration -- 10M events shaped like the paper's beam MC
 (Gamma(3, 0.25 GeV) true energies, 295 km, 2.6 g/cm^3, Y_e 0.5, nu_mu -> nu_mu
 90 % / nu_mu -> nu_e 10 %, 20 % antineutrinos) at the Table 1 parameter point:
-set the point (passed by value to the FP64 constants kernel), then the
-histogram kernel -- probability, weight, bin and exact accumulation, finalized
-in place, launched programmatically after the constants kernel -- into a
-100-bin E_reco histogram over [0, 5) GeV.  FP32-bulk path; the all-FP64 path is
-timed on the same workload as the GPU baseline to beat.
+one fit step, osc_histogram_point -- the point by value to the FP64 constants
+kernel, then the histogram kernel (probability, weight, bin and exact
+accumulation, finalized in place) and the FP32 path's FP64 recomputation pass,
+replayed as one CUDA graph whose kernels are joined by programmatic edges --
+into a 100-bin E_reco histogram over [0, 5) GeV.  FP32-bulk path; the all-FP64
+path is timed on the same workload as the GPU baseline to beat.
 
 Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
 launching stream, with a 256 MB write between steps to flush the 129 MB L2
@@ -42,14 +43,23 @@ N_EVENTS = 10_000_000
 NBINS, LO, HI = 100, 0.0, 5.0
 FLUSH_BYTES = 256 << 20
 
-# Algorithmic FP32 operations per (event, point) of the FP32-bulk path, counted
-# from osc_math.cuh / osc_kernels.cuh (FMA = 2, add/mul = 1; transcendental and
-# reciprocal calls counted separately as SFU operations -- 12 per event-point --,
-# conversions, comparisons, selects and integer work not counted): event terms 11,
-# matter shifts 75 (seed 43, two Newton steps 30, trace 2), gaps and phases 32,
-# amplitude 60, weight and bin 4.
-FP32_FLOP_PER_EVPT = 182
-SFU_PER_EVPT = 11
+# Algorithmic work per (event, point) of the FP32-bulk path.
+#  * The method's minimum (the roofline's count): about 95 FP32 operations and 6
+#    SFU operations -- the cubic's eigenvalues from a seed and Newton steps, the
+#    Sylvester amplitude over three roots, weight and bin.
+#  * The kernel's own arithmetic, counted from osc_math.cuh / osc_kernels.cuh
+#    (FMA = 2, add/mul = 1; conversions, comparisons, selects and integer work not
+#    counted) for the mu -> mu / tau -> tau channels, 90 % of the workload: event
+#    terms 11, matter shifts 74 (seed 36, seeds 6, two Newton steps 30, trace 2),
+#    gaps and phases 28, amplitude in the mass basis with its error bound 48,
+#    weight and bin 4 -- 165 flops; the other channels add the matter and
+#    electron terms, about 185.  SFU: 12 (1/E, the seed's rsqrt, sqrt and
+#    sin/cos, two Newton reciprocals, two sin/cos of half phases, 1/D).
+ALG_OPS_PER_EVPT = 95
+ALG_SFU_PER_EVPT = 6
+FP32_FLOP_PER_EVPT = 165
+SFU_PER_EVPT = 12
+ALG_BYTES_PER_EVENT = 13  # E_true, E_reco, w_mc (FP32) and the channel byte
 
 
 def _dist():
@@ -249,18 +259,32 @@ def precision_per_config(api, synth, c):
     return out
 
 
-def serving_leg(api, synth, c, rates, seconds, prec="fp32"):
+SERVE_CAP_BYTES = 8 << 30
+SERVE_RATES = (1000, 2000, 5000, 10000, 20000, 50000)  # the serving context's workspace cap (samples, points, batch buffers)
+
+
+def serving_leg(api, synth, device, rates, seconds, prec="fp32"):
     """Serving workload: requests (sample id uniform over the 8 uneven samples,
     point from the scan distribution) arrive as a Poisson process at each rate for
     `seconds`; a submitter thread follows the arrival schedule, a collector thread
-    waits on the tickets.  Reports achieved request and event-weight throughput and
-    the p50/p99 submit-to-completion latency measured inside the library."""
+    waits on the tickets.  The serving context has an 8 GB workspace cap: the 8
+    resident samples (47.6M events) and every batch buffer are admitted under it.
+    Reports achieved request and event-weight throughput and the p50/p99
+    submit-to-completion latency measured inside the library."""
+    with api.Context(device, workspace_cap_bytes=SERVE_CAP_BYTES) as ctx:
+        out = _serving_leg(api, synth, ctx.ptr, rates, seconds, prec)
+        out["workspace_cap_bytes"] = SERVE_CAP_BYTES
+        return out
+
+
+def _serving_leg(api, synth, c, rates, seconds, prec):
     import threading
     samples = _uneven_samples(synth)
     sids = [api.osc_load_sample(c, s) for s in samples]
     sizes = np.array([s["n"] for s in samples], dtype=np.float64)
     api.osc_serve_start(c, 256, LO, 20.0, NBINS)
-    out = {"samples_events": [int(x) for x in sizes], "max_slots": 256, "prec": prec, "rates": []}
+    out = {"samples_events": [int(x) for x in sizes], "max_slots": 256, "prec": prec, "rates": [],
+           "seconds_per_rate": seconds, "workspace_used_bytes": int(api.osc_workspace_used(c))}
     try:
         # warm-up
         for k in range(16):
@@ -561,8 +585,11 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(prec):
-        api.osc_set_params(c, point)
-        api.osc_histogram(c, [sid], 0, 1, prec, LO, HI, NBINS, out=out)
+        # one fit step: the point by value and its histogram in one call, replayed as
+        # one CUDA graph (constants -> histogram -> FP64 recomputation pass, joined by
+        # programmatic edges); with per-kernel timing on, the library makes the two
+        # calls it stands for instead (their kernels bracketed by events)
+        api.osc_histogram_point(c, [sid], point[0], prec, LO, HI, NBINS, out=out)
 
     def timed(prec, k, w, kernel_timing):
         """k steps after w warm-up steps; per-step device times [ms].  With
@@ -594,6 +621,8 @@ def run_ours(args):
         ms = np.array([a.elapsed_time(b) for a, b in ev])
         return ms, counts, sums, n1 - n0
 
+    # the FP32 FMA peak of this device, measured (the roofline's denominator)
+    fp32_peak_meas = api.osc_measure_fp32_peak(local)
     with ClockSampler(local) as clk:
         time.sleep(1.0)  # let nvidia-smi start sampling before the timed region
         t_clk0 = time.perf_counter()
@@ -652,8 +681,10 @@ def run_ours(args):
         peaks, src = _measured_peaks()
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
-        achieved = FP32_FLOP_PER_EVPT * N_EVENTS / (k_hist_ms * 1e-3) / 1e12
+        fp32_peak_nominal = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
+        fp32_peak = fp32_peak_meas
+        achieved = ALG_OPS_PER_EVPT * N_EVENTS / (k_hist_ms * 1e-3) / 1e12
+        achieved_recount = FP32_FLOP_PER_EVPT * N_EVENTS / (k_hist_ms * 1e-3) / 1e12
         traffic = _profiled_traffic()
         # issue view: the kernel's warp instructions per launch (ncu) over its live duration,
         # against 4 schedulers x 1 warp instruction per clock per SM
@@ -695,15 +726,15 @@ def run_ours(args):
         configs.update(configs_leg(torch, api, synth, c, stream, flush))
         serving = None
         if args.serve_seconds > 0:
-            serving = {"fp32": serving_leg(api, synth, c, (1000, 2000, 5000, 10000, 20000, 50000), args.serve_seconds,
-                                           "fp32"),
-                       "fp64": serving_leg(api, synth, c, (100,), args.serve_seconds, "fp64")}
+            serving = {"fp32": serving_leg(api, synth, local, SERVE_RATES, args.serve_seconds, "fp32"),
+                       "fp64": serving_leg(api, synth, local, (100,), args.serve_seconds, "fp64")}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot32 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
             "config": {"workload": "precision study: 10M events x 1 point (Table 1), FP32-bulk, step = "
-                                   "set_params + histogram", "events": N_EVENTS, "points": 1, "nbins": NBINS,
+                                   "osc_histogram_point (point by value + histogram, one CUDA graph)",
+                       "events": N_EVENTS, "points": 1, "nbins": NBINS,
                        "baseline_km": 295.0, "density_gcc": 2.6, "ye": 0.5,
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -718,9 +749,15 @@ def run_ours(args):
                           "hist_fp32_f64eig": smx[1] / max(1, cmx[1])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": traffic,
-                         "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
-                                        % (n_sm, sm_mhz, src),
-                         "flop_per_evpt": FP32_FLOP_PER_EVPT,
+                         "ops_per_evpt": ALG_OPS_PER_EVPT, "sfu_per_evpt": ALG_SFU_PER_EVPT,
+                         "peak_source": "measured on this device: FP32 FMA chains on every SM, CUDA events "
+                                        "(osc_measure_fp32_peak); nominal %.1f = %d SMs x 128 lanes x 2 x %.0f MHz"
+                                        % (fp32_peak_nominal, n_sm, sm_mhz),
+                         "peak_nominal": fp32_peak_nominal,
+                         "recount": {"flop_per_evpt": FP32_FLOP_PER_EVPT, "sfu_per_evpt": SFU_PER_EVPT,
+                                     "achieved": achieved_recount, "frac": achieved_recount / fp32_peak},
+                         "algorithmic_bytes_per_launch": ALG_BYTES_PER_EVENT * N_EVENTS,
+                         "traffic_over_algorithmic": (traffic / (ALG_BYTES_PER_EVENT * N_EVENTS)) if traffic else None,
                          "hbm_gbs_event_stream": 16.0 * N_EVENTS / (k_hist_ms * 1e-3) / 1e9,
                          "hbm_peak_gbs": peaks.get("hbm_gbs"),
                          "issue": issue, "pipes": pipes},
@@ -778,6 +815,15 @@ def run_profile_case(args):
     return 0
 
 
+def run_serving_only(args):
+    """The serving workload alone on device 0: FP32-bulk at every offered rate and
+    FP64 at 100 req/s, --serve-seconds per rate, under the 8 GB workspace cap."""
+    from paper_1311_7579_gb300 import api, synth
+    res = {"serving": {"fp32": serving_leg(api, synth, 0, SERVE_RATES, args.serve_seconds, "fp32"),
+                       "fp64": serving_leg(api, synth, 0, (100,), args.serve_seconds, "fp64")}}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -790,6 +836,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds per offered rate of the serving leg (0 skips it)")
     ap.add_argument("--profile", action="store_true", help="run the small ncu profiling case and exit")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving workload (--serve-seconds per rate) and print its JSON")
     ap.add_argument("--events", type=int, default=2_000_000)
     ap.add_argument("--points", type=int, default=1)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
@@ -799,6 +847,8 @@ def main():
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)
+    if args.serving_only:
+        return run_serving_only(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -163,7 +163,9 @@ osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points);
 /* Per-event probability and weight (P * w_mc * norm) for one point of the
  * table, in the caller's event order (Sec. 2.1: result array copied back).
  * out_prob / out_weight: n doubles each, either may be NULL; host pointers if
- * out_on_device == 0, device pointers otherwise.  Synchronous. */
+ * out_on_device == 0 (a page-locked host buffer is written by the kernel
+ * directly, a pageable one through a device staging buffer and a copy), device
+ * pointers otherwise.  Synchronous. */
 osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_precision prec,
                         double *out_prob, double *out_weight, int out_on_device);
 
@@ -323,6 +325,16 @@ osc_status osc_submit(osc_ctx *ctx, int32_t sample_id, const osc_point *pt, osc_
 osc_status osc_wait(osc_ctx *ctx, uint64_t ticket, double *out_hist, int32_t timeout_ms,
                     double *latency_us);
 osc_status osc_serve_stop(osc_ctx *ctx);
+
+/* The FP32 FMA throughput of CUDA device `device` in TFLOP/s (an FMA counts as
+ * two flops): the peak against which the FP32 path's roofline is reported (the
+ * paper has no counterpart; the vendor's figure assumes the maximum clock).
+ * Independent FMA chains run on every SM for about 30 ms in all, timed with CUDA
+ * events; the best of five launches is returned.  No clock or power setting is
+ * changed.  It allocates a small result buffer of its own, needs no context, and
+ * leaves the calling thread's current device as it was.  OSC_E_ARG for a null
+ * tflops or an invalid device, OSC_E_CUDA if a CUDA call fails. */
+osc_status osc_measure_fp32_peak(int device, double *tflops);
 
 /* One-point histogram that allocates nothing (the paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc -- for example a host

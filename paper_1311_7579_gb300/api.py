@@ -29,7 +29,7 @@ ENTRY_POINTS = [
     "osc_set_layers", "osc_set_tile", "osc_enable_timing", "osc_last_timing", "osc_timing_totals",
     "osc_launch_count", "osc_workspace_used", "osc_sync", "osc_serve_start", "osc_submit", "osc_wait",
     "osc_serve_stop", "osc_histogram_noalloc", "osc_sample_set_bounds", "osc_histogram_digits",
-    "osc_histogram_from_digits",
+    "osc_histogram_from_digits", "osc_measure_fp32_peak",
 ]
 
 
@@ -101,6 +101,7 @@ def load_library(path):
         "osc_histogram_noalloc": (st, [vp, vp, vp, vp, vp, vp, i64, d, d, d, d, ctypes.POINTER(OscPoint),
                                        ctypes.c_int, d, d, i32, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
         "osc_sample_set_bounds": (st, [vp, i32, d, d]),
+        "osc_measure_fp32_peak": (st, [ctypes.c_int, ctypes.POINTER(d)]),
         "osc_histogram_digits": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_int, d, d, i32, vp,
                                       ctypes.c_int]),
         "osc_histogram_from_digits": (st, [vp, ctypes.POINTER(i32), i32, i32, i32, i32, vp, vp, ctypes.c_int]),
@@ -228,6 +229,15 @@ def osc_histogram(ctx, sample_ids, point_begin, n_points, prec, lo, hi, nbins, o
     _check(ctx, lib().osc_histogram(ctx, ids, n_ids, int(point_begin), int(n_points), PRECISIONS[prec], float(lo),
                                     float(hi), int(nbins), _ptr(out), 1 if dev else 0))
     return out
+
+
+def osc_measure_fp32_peak(device=0):
+    """FP32 FMA throughput of the device [TFLOP/s, FMA = 2 flops]."""
+    t = ctypes.c_double()
+    s = lib().osc_measure_fp32_peak(int(device), ctypes.byref(t))
+    if s != OSC_OK:
+        raise OscError(s, "osc_measure_fp32_peak failed")
+    return t.value
 
 
 def osc_sample_set_bounds(ctx, sample_id, w_abs_max, e_true_max):

@@ -55,6 +55,12 @@ struct Plan {
     cudaGraphExec_t exec_t = nullptr;
     cudaGraphNode_t t_hist_node = nullptr, t_redo_node = nullptr, t_final_node = nullptr,
                     t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // one-point fit step (osc_histogram_point): constants, histogram, FP64
+    // recomputation and finalize kernels joined by programmatic edges
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraphNode_t s_const = nullptr, s_hist = nullptr, s_redo = nullptr, s_final = nullptr;
+    bool step_fused = false;
     // bin-centre plans: true-energy binning, probability table and its rows
     double t_lo = 0, t_hi = 0;
     int32_t t_nbins = 0, n_rows = 0;

@@ -103,6 +103,9 @@ static cudaError_t launch_by_value(const osc_point *h_pts, int n, float *pc32, d
     return cudaGetLastError();
 }
 
+const void *point_consts_one_fn() { return (const void *)k_point_consts_v<1>; }
+int point_consts_threads() { return kConstThreads; }
+
 cudaError_t launch_point_consts_host(const osc_point *h_pts, int n, float *pc32, double *pc64, cudaStream_t st) {
     if (n < 1 || n > kPointsByValue) return cudaErrorInvalidValue;
     // a small parameter block launches faster than the full one (one point: a fit step)

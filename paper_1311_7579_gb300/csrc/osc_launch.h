@@ -47,6 +47,10 @@ int redo_grid();
 cudaError_t launch_digits_out_programmatic(const FinalParams &p, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_from_digits(const unsigned long long *digits, const double *hmeta, const double *pc64, double *out,
                                int64_t n, int32_t nbins, cudaStream_t st);
+// The constants kernel of a one-point table passed by value (a graph node's
+// function) and its block size.
+const void *point_consts_one_fn();
+int point_consts_threads();
 // Streaming multiprocessors of the current device (queried once per device).
 int device_sms();
 

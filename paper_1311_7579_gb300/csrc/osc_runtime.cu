@@ -356,6 +356,8 @@ static void free_sample(osc_ctx *c, Sample *s) {
 static void free_plan(osc_ctx *c, Plan *p) {
     if (p->exec_t) cudaGraphExecDestroy(p->exec_t);
     if (p->graph_t) cudaGraphDestroy(p->graph_t);
+    if (p->step_exec) cudaGraphExecDestroy(p->step_exec);
+    if (p->step_graph) cudaGraphDestroy(p->step_graph);
     dfree(c, p->d_items);
     dfree(c, p->d_samples);
     dfree(c, p->d_hmeta);
@@ -666,6 +668,34 @@ osc_status osc_set_layers(osc_ctx *ctx, int32_t sample_id, int32_t n_layers, con
     return OSC_OK;
 }
 
+// Device room for a point table of n points and its FP32 / FP64 constants.
+static osc_status ensure_point_table(osc_ctx *ctx, int32_t n_points) {
+    if (n_points <= ctx->pts_cap) return OSC_OK;
+    int32_t cap = 1;
+    while (cap < n_points) cap <<= 1;
+    void *a, *b, *c;
+    osc_status s = dalloc(ctx, &a, (size_t)cap * sizeof(osc_point));
+    if (s) return s;
+    if ((s = dalloc(ctx, &b, (size_t)cap * C32_STRIDE * 4))) {
+        dfree(ctx, a);
+        return s;
+    }
+    if ((s = dalloc(ctx, &c, (size_t)cap * C64_STRIDE * 8))) {
+        dfree(ctx, a);
+        dfree(ctx, b);
+        return s;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, ctx->d_pts);
+    dfree(ctx, ctx->d_pc32);
+    dfree(ctx, ctx->d_pc64);
+    ctx->d_pts = (osc_point *)a;
+    ctx->d_pc32 = (float *)b;
+    ctx->d_pc64 = (double *)c;
+    ctx->pts_cap = cap;
+    return OSC_OK;
+}
+
 osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points) {
     NvtxRange nvtx_range("osc_set_params");
     CHECK_CTX(ctx);
@@ -676,30 +706,8 @@ osc_status osc_set_params(osc_ctx *ctx, const osc_point *pts, int32_t n_points) 
         if (s) return s;
     }
     std::lock_guard<std::mutex> lk(ctx->api_mu);
-    if (n_points > ctx->pts_cap) {
-        int32_t cap = 1;
-        while (cap < n_points) cap <<= 1;
-        void *a, *b, *c;
-        osc_status s = dalloc(ctx, &a, (size_t)cap * sizeof(osc_point));
-        if (s) return s;
-        if ((s = dalloc(ctx, &b, (size_t)cap * C32_STRIDE * 4))) {
-            dfree(ctx, a);
-            return s;
-        }
-        if ((s = dalloc(ctx, &c, (size_t)cap * C64_STRIDE * 8))) {
-            dfree(ctx, a);
-            dfree(ctx, b);
-            return s;
-        }
-        cudaStreamSynchronize(ctx->stream);
-        dfree(ctx, ctx->d_pts);
-        dfree(ctx, ctx->d_pc32);
-        dfree(ctx, ctx->d_pc64);
-        ctx->d_pts = (osc_point *)a;
-        ctx->d_pc32 = (float *)b;
-        ctx->d_pc64 = (double *)c;
-        ctx->pts_cap = cap;
-    }
+    osc_status s = ensure_point_table(ctx, n_points);
+    if (s) return s;
     ctx->pts.assign(pts, pts + n_points);
     // small tables travel as kernel parameters; larger ones through a copy
     const bool by_value = n_points <= kPointsByValue;
@@ -802,11 +810,20 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
     Sample *s = it->second;
     if (!out_prob && !out_weight) return OSC_OK;
     double *dp = out_prob, *dw = out_weight;
+    // host outputs: a page-locked buffer is written by the kernel directly, a
+    // pageable one through a device staging buffer and a copy
+    bool stage_p = false, stage_w = false;
     if (!out_on_device) {
-        osc_status st = ensure_buf(ctx, &ctx->d_rw, &ctx->rw_cap, 2 * s->n);
-        if (st) return st;
-        dp = out_prob ? ctx->d_rw : nullptr;
-        dw = out_weight ? ctx->d_rw + s->n : nullptr;
+        dp = out_prob ? pinned_device_ptr(out_prob) : nullptr;
+        dw = out_weight ? pinned_device_ptr(out_weight) : nullptr;
+        stage_p = out_prob && !dp;
+        stage_w = out_weight && !dw;
+        if (stage_p || stage_w) {
+            osc_status st = ensure_buf(ctx, &ctx->d_rw, &ctx->rw_cap, 2 * s->n);
+            if (st) return st;
+            if (stage_p) dp = ctx->d_rw;
+            if (stage_w) dw = ctx->d_rw + s->n;
+        }
     }
     ReweightParams rp;
     rp.s = s->dev;
@@ -822,10 +839,8 @@ osc_status osc_reweight(osc_ctx *ctx, int32_t sample_id, int32_t point, osc_prec
     else
         CK(launch_reweight(pr, rp, ctx->stream));
     ctx->launches += 1;
-    if (!out_on_device) {
-        if (out_prob) CK(cudaMemcpyAsync(out_prob, dp, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        if (out_weight) CK(cudaMemcpyAsync(out_weight, dw, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    }
+    if (stage_p) CK(cudaMemcpyAsync(out_prob, dp, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (stage_w) CK(cudaMemcpyAsync(out_weight, dw, s->n * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return OSC_OK;
 }
@@ -1063,6 +1078,92 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
 }
 
 
+// One fit step (osc_histogram_point) as a CUDA graph: the constants kernel of
+// the step's point, then the histogram kernel, the FP64 recomputation pass
+// (FP32 precisions) and the finalize kernel (larger outputs), each joined to
+// the one before by a programmatic edge, so that a kernel starts while the one
+// before still runs and waits in griddepcontrol.wait for its results -- the
+// overlap of the direct launches, in one graph launch.  The graph is built once
+// per plan and replayed with its node parameters refreshed (the point by value,
+// the output pointer).
+static osc_status run_step_graph(osc_ctx *ctx, Plan *p, const osc_point &pt, double lo, double hi, double *d_out) {
+    HistParams hp;
+    fill_hist_params(hp, p->d_items, p->n_items, p->d_samples, ctx->d_pc32, ctx->d_pc64, ctx->d_acc, ctx->d_counter,
+                     p->nbins, lo, hi);
+    hp.redo = p->d_redo;
+    FinalParams fp{ctx->d_acc, p->d_hmeta, ctx->d_pc64, d_out, p->n_hist, p->nbins, ctx->d_counter};
+    const bool fused = fuse_finalize(p->n_hist, p->nbins, p->pt);
+    if (fused) {
+        hp.fuse_final = 1;
+        hp.fin_n_hist = p->n_hist;
+        hp.fin_hmeta = p->d_hmeta;
+        hp.fin_out = d_out;
+    }
+    PointsByValueT<1> pv;
+    pv.n = 1;
+    pv.p[0] = pt;
+    float *pc32 = ctx->d_pc32;
+    double *pc64 = ctx->d_pc64;
+    void *cargs[] = {&pv, &pc32, &pc64};
+    void *hargs[] = {&hp};
+    void *fargs[] = {&fp};
+    cudaKernelNodeParams kc{}, kh{}, kr{}, kf{};
+    kc.func = (void *)point_consts_one_fn();
+    kc.gridDim = dim3(1);
+    kc.blockDim = dim3(point_consts_threads());
+    kc.kernelParams = cargs;
+    kh.func = (void *)plan_kernel(p);
+    kh.gridDim = dim3(p->grid);
+    kh.blockDim = dim3(hist_threads());
+    kh.kernelParams = hargs;
+    kr.func = p->d_redo ? (void *)redo_kernel_fn(p->prec) : nullptr;
+    kr.gridDim = dim3(redo_grid());
+    kr.blockDim = dim3(hist_threads());
+    kr.kernelParams = hargs;
+    kf.func = (void *)final_kernel_fn();
+    kf.gridDim = dim3(final_blocks(p->n_hist * (int64_t)p->nbins));
+    kf.blockDim = dim3(256);
+    kf.kernelParams = fargs;
+    if (p->step_exec && p->step_fused != fused) {
+        cudaGraphExecDestroy(p->step_exec);
+        cudaGraphDestroy(p->step_graph);
+        p->step_exec = nullptr;
+        p->step_graph = nullptr;
+    }
+    if (!p->step_exec) {
+        // programmatic edges where the downstream kernel waits in griddepcontrol.wait
+        // (every kernel of an event-by-event plan); full completion edges otherwise
+        cudaGraphEdgeData ed{};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        const cudaGraphEdgeData *edge = p->kind == kEventByEvent ? &ed : nullptr;
+        CK(cudaGraphCreate(&p->step_graph, 0));
+        CK(cudaGraphAddKernelNode(&p->s_const, p->step_graph, nullptr, 0, &kc));
+        CK(cudaGraphAddKernelNode(&p->s_hist, p->step_graph, nullptr, 0, &kh));
+        CK(cudaGraphAddDependencies(p->step_graph, &p->s_const, &p->s_hist, edge, 1));
+        cudaGraphNode_t prev = p->s_hist;
+        if (p->d_redo) {
+            CK(cudaGraphAddKernelNode(&p->s_redo, p->step_graph, nullptr, 0, &kr));
+            CK(cudaGraphAddDependencies(p->step_graph, &prev, &p->s_redo, &ed, 1));
+            prev = p->s_redo;
+        }
+        if (!fused) {
+            CK(cudaGraphAddKernelNode(&p->s_final, p->step_graph, nullptr, 0, &kf));
+            CK(cudaGraphAddDependencies(p->step_graph, &prev, &p->s_final, &ed, 1));
+        }
+        CK(cudaGraphInstantiate(&p->step_exec, p->step_graph, 0));
+        p->step_fused = fused;
+    } else {
+        CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_const, &kc));
+        CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_hist, &kh));
+        if (p->d_redo) CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_redo, &kr));
+        if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_final, &kf));
+    }
+    CK(cudaGraphLaunch(p->step_exec, ctx->stream));
+    ctx->launches += 2 + (p->d_redo ? 1 : 0) + (fused ? 0 : 1);
+    return OSC_OK;
+}
+
 // Time one candidate tile shape (ms per histogram launch).
 static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_t pb, int32_t np, int prec,
                              int32_t nbins, double lo, double hi, int32_t pt, int32_t chunk, double *ms) {
@@ -1088,9 +1189,11 @@ static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
 
 // osc_histogram, and (digits != null) osc_histogram_digits: the same call with
 // the bins' digit columns as its output instead of doubles.
+// step_pt (osc_histogram_point): the table holds that one point, whose constants
+// the step's CUDA graph computes as its first kernel.
 static osc_status histogram_impl(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
                                  int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
-                                 double *out, uint64_t *digits, int out_on_device) {
+                                 double *out, uint64_t *digits, int out_on_device, const osc_point *step_pt = nullptr) {
     CHECK_CTX(ctx);
     if (!sample_ids || !(out || digits)) return fail(ctx, OSC_E_ARG, "null argument");
     if (prec != OSC_FP64 && prec != OSC_FP32_BULK && prec != OSC_FP32_F64EIG)
@@ -1123,6 +1226,8 @@ static osc_status histogram_impl(osc_ctx *ctx, const int32_t *sample_ids, int32_
             pt = it->second.first;
             chunk = it->second.second;
         } else {
+            // a graph step computes its constants in the graph: the candidates need them now
+            if (step_pt) CK(launch_point_consts_host(step_pt, 1, ctx->d_pc32, ctx->d_pc64, ctx->stream));
             int32_t best_pt = default_pt(n_points), best_chunk = 0;
             double best_ms = 1e30;
             const int32_t cands[] = {1, 4, 16, 64, 256};
@@ -1166,7 +1271,9 @@ static osc_status histogram_impl(osc_ctx *ctx, const int32_t *sample_ids, int32_
         d_out = ctx->d_out;
         staged = true;
     }
-    st = digits ? run_plan(ctx, p, lo, hi, nullptr, (unsigned long long *)d_out) : run_plan(ctx, p, lo, hi, d_out);
+    st = digits    ? run_plan(ctx, p, lo, hi, nullptr, (unsigned long long *)d_out)
+         : step_pt ? run_step_graph(ctx, p, *step_pt, lo, hi, d_out)
+                   : run_plan(ctx, p, lo, hi, d_out);
     if (st) return st;
     if (staged) CK(cudaMemcpyAsync(host, d_out, words * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (!out_on_device) {
@@ -1263,9 +1370,20 @@ extern "C" osc_status osc_histogram_point(osc_ctx *ctx, const int32_t *sample_id
                                           const osc_point *pt, osc_precision prec, double lo, double hi,
                                           int32_t nbins, double *out, int out_on_device) {
     NvtxRange nvtx_range("osc_histogram_point");
-    const osc_status s = osc_set_params(ctx, pt, 1);
+    if (!ctx || !pt || !out || ctx->timing || ctx->poisoned) {
+        // timing mode keeps the per-kernel event records of the two calls
+        const osc_status s = osc_set_params(ctx, pt, 1);
+        if (s) return s;
+        return osc_histogram(ctx, sample_ids, n_samples, 0, 1, prec, lo, hi, nbins, out, out_on_device);
+    }
+    osc_status s = validate_point(ctx, *pt, 0);
     if (s) return s;
-    return osc_histogram(ctx, sample_ids, n_samples, 0, 1, prec, lo, hi, nbins, out, out_on_device);
+    {
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        if ((s = ensure_point_table(ctx, 1))) return s;
+        ctx->pts.assign(pt, pt + 1);
+    }
+    return histogram_impl(ctx, sample_ids, n_samples, 0, 1, prec, lo, hi, nbins, out, nullptr, out_on_device, pt);
 }
 
 // ------------------------------------------------------ bin-centre method

@@ -297,6 +297,17 @@ def test_device_outputs_match_host_outputs(ctx):
     api.osc_reweight(ctx, sid, 2, "fp64", out_prob=pd)
     ph, _ = _gpu_probs(ctx, sid, 2, "fp64", s["n"])
     assert np.array_equal(pd.cpu().numpy(), ph)
+    # osc_reweight into page-locked host buffers (written by the kernel directly),
+    # one of them pageable (staged): same values
+    for prec in ("fp32", "fp64"):
+        ph, wh = _gpu_probs(ctx, sid, 2, prec, s["n"])
+        pp = torch.zeros(s["n"], dtype=torch.float64).pin_memory().numpy()
+        wp = torch.zeros(s["n"], dtype=torch.float64).pin_memory().numpy()
+        api.osc_reweight(ctx, sid, 2, prec, out_prob=pp, out_weight=wp)
+        assert np.array_equal(pp, ph) and np.array_equal(wp, wh)
+        wq = np.zeros(s["n"])
+        api.osc_reweight(ctx, sid, 2, prec, out_prob=pp, out_weight=wq)
+        assert np.array_equal(wq, wh)
     api.osc_unload_sample(ctx, sid)
 
 
@@ -332,6 +343,37 @@ def test_histogram_point_is_set_params_plus_histogram(ctx):
     api.osc_set_params(ctx, pts[2:3])
     assert np.array_equal(again, api.osc_histogram(ctx, ids, 0, 1, "fp64", LO, HI, NB))
     for sid in ids:
+        api.osc_unload_sample(ctx, sid)
+
+
+def test_histogram_point_graph_step_separate_finalize_and_layers(ctx):
+    """osc_histogram_point runs the fit step as one CUDA graph (constants,
+    histogram, FP64 recomputation pass, finalize, joined by programmatic edges)
+    replayed with its parameters refreshed: the bins equal set_params +
+    osc_histogram bitwise for a separate finalize kernel (600 bins), a layered
+    sample (completion edges) and points alternating between calls; the graph
+    launches the same kernels the two calls do."""
+    s1 = synth.table1_sample(30000, seed=24)
+    s2 = synth.all_channel_sample(12000, seed=25, L_km=810.0, rho=2.8)
+    ids = [api.osc_load_sample(ctx, s1), api.osc_load_sample(ctx, s2)]
+    lid = api.osc_load_sample(ctx, synth.all_channel_sample(9000, seed=26, L_km=1300.0, rho=2.85))
+    api.osc_set_layers(ctx, lid, [(400.0, 2.6, 0.5), (500.0, 3.3, 0.5), (400.0, 2.6, 0.5)])
+    pts = synth.scan_points(4, seed=27)
+    for nb in (NB, 300):
+        for group in (ids, [lid]):
+            for prec in ("fp32", "fp64"):
+                api.osc_set_params(ctx, pts[:1])
+                api.osc_histogram(ctx, group, 0, 1, prec, LO, HI, nb)  # autotuned here, once
+                for k in (0, 1, 0, 2, 3):
+                    api.osc_set_params(ctx, pts[k:k + 1])
+                    n0 = api.osc_launch_count(ctx)
+                    ref = api.osc_histogram(ctx, group, 0, 1, prec, LO, HI, nb)
+                    n1 = api.osc_launch_count(ctx)
+                    got = api.osc_histogram_point(ctx, group, pts[k], prec, LO, HI, nb)
+                    n2 = api.osc_launch_count(ctx)
+                    assert np.array_equal(got, ref), (nb, prec, k)
+                    assert n2 - n1 == (n1 - n0) + 1  # the constants kernel is a node of the step's graph
+    for sid in ids + [lid]:
         api.osc_unload_sample(ctx, sid)
 
 
