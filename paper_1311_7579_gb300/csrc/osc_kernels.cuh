@@ -621,6 +621,9 @@ __device__ __forceinline__ void acc_finish_warp(RunAcc &r, unsigned long long *a
     if (has && lane == first && (lo | hi)) fx_flush(accp + kDigits * r.cur_b, lo, hi);
 }
 
+// Counts a work item marked for the FP64 recomputation pass.
+__device__ __forceinline__ void mark_redo(const HistParams &prm) { atomicAdd(prm.counter + kRedoCount, 1); }
+
 // FP32 matter term and c_L L / (2 pi E) float-float of one event.
 __device__ __forceinline__ void event_terms32(const SampleDev &sd, float E, int ch, float &A, float &th, float &tl) {
     A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
@@ -903,7 +906,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             const bool any = __any_sync(0xffffffffu, redo);
             if (any && lane == 0) {
                 prm.redo[it] = 1;
-                atomicAdd(prm.counter + kRedoCount, 1);
+                mark_redo(prm);
             }
         }
         // move to the ticket held ahead and fetch the one after it, or (few
@@ -1076,7 +1079,7 @@ __global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(con
                 // mark the item for the FP64 recomputation of its left-out events
                 if (__syncthreads_or(redo) && tid == 0) {
                     prm.redo[it] = 1;
-                    atomicAdd(prm.counter + kRedoCount, 1);
+                    mark_redo(prm);
                 }
             }
             acc_finish(r, accp);

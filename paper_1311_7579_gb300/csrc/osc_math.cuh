@@ -69,6 +69,26 @@ __device__ __forceinline__ float acos_third(float x) {
     return x < 0.0f ? 3.14159265358979323846f * k - r : r;
 }
 
+// arccos(x) / 3 from Abramowitz & Stegun formula 4.4.45: acos(x) = sqrt(1 - x)
+// (a0 + a1 x + a2 x^2 + a3 x^3) for 0 <= x <= 1 with |error| <= 7e-5 rad.  It
+// seeds the FP32-bulk shifts only: their Newton step squares the seed's error,
+// and its per-event error bound, together with the seed's |cos theta| check,
+// sends every event the step would not settle to the FP64 recomputation.  The
+// FP64 and FP64-eigen paths, whose Newton polish must reach FP64 accuracy, take
+// the seven-term form above.
+__device__ __forceinline__ float acos_third_short(float x) {
+    constexpr float k = 1.0f / 3.0f;
+    const float ax = fabsf(x);
+    float p = -0.0187293f * k;
+    p = fmaf(p, ax, 0.0742610f * k);
+    p = fmaf(p, ax, -0.2121144f * k);
+    p = fmaf(p, ax, 1.5707288f * k);
+    float sq;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(1.0f - ax));
+    const float r = sq * p;
+    return x < 0.0f ? 3.14159265358979323846f * k - r : r;
+}
+
 struct Pt32 {
     float p0, p1, q0, q1, q2, T0, c10, smt;  // p*: -p/3, q*: -q/2 of the depressed cubic, in powers of A
     float td0, td1;                          // T0 / 3 - d0, T0 / 3 - d1
@@ -121,6 +141,8 @@ __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float v
 // from mp3 = -p/3 and qh = -q/2: mu = 2 r cos(theta/3 + 2 pi k/3) with
 // r = sqrt(mp3) and cos(theta) = qh / r^3.
 // Also returns cos(theta): near +-1 the angle is ill-conditioned (see near_double_pair64).
+// SHORT: the four-term arccos (FP32-bulk shifts), else the eight-term one.
+template <bool SHORT = false>
 __device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, float &m1, float &cth_out) {
     mp3 = fmaxf(mp3, 1e-30f);
     const float ir = rsqrt_approx(mp3);
@@ -128,7 +150,7 @@ __device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, floa
     float cth = qh * ir * ir * ir;
     cth = fminf(fmaxf(cth, -1.0f), 1.0f);
     cth_out = cth;
-    const float th3 = acos_third(cth);
+    const float th3 = SHORT ? acos_third_short(cth) : acos_third(cth);
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;
@@ -169,10 +191,11 @@ static __device__ __noinline__ double2 near_double_pair64(double p, double q, fl
 
 // The same seed for the characteristic cubic of one event, from the point's
 // pre-scaled coefficients: -p/3 = P0 + P1 A + A^2/9, -q/2 = Q0 + Q1 A + Q2 A^2 + A^3/27.
+template <bool SHORT = false>
 __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1, float &cth) {
     const float mp3 = fmaf(fmaf(A, 1.0f / 9.0f, c.p1), A, c.p0);
     const float qh = fmaf(fmaf(fmaf(A, 1.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
-    seed_core32(mp3, qh, m0, m1, cth);
+    seed_core32<SHORT>(mp3, qh, m0, m1, cth);
 }
 __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1) {
     float cth;
@@ -251,9 +274,12 @@ __device__ __forceinline__ float amplitude_mass32(const Pt32 &c, const Ch32 &h, 
 // Matter shifts delta_l = lambda_l - d_l of the three sorted eigenvalues (FP32):
 // trigonometric seed, then one Newton step on each lower root's shifted cubic;
 // the top shift follows from the trace (sum of shifts = A).
+// SHORT: the four-term arccos seed (the single-layer FP32-bulk path, whose
+// per-event error bound guards it); the layered path keeps the eight-term one.
+template <bool SHORT = true>
 __device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2, float &cth) {
     float m0, m1;
-    seed_scaled32(c, A, m0, m1, cth);
+    seed_scaled32<SHORT>(c, A, m0, m1, cth);
     // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) + m_l
     dl0 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td0) + m0, A, c.S0, c.PI0, c.W0, c.E0);
     dl1 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td1) + m1, A, c.S1, c.PI1, c.W1, c.E1);
@@ -261,7 +287,7 @@ __device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, flo
 }
 __device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
     float cth;
-    shifts32(c, A, dl0, dl1, dl2, cth);
+    shifts32<false>(c, A, dl0, dl1, dl2, cth);
 }
 
 // P(alpha -> beta) for one event and one point, FP32 bulk.  A: signed matter

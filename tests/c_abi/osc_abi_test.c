@@ -9,6 +9,11 @@
  *       histograms of every point, the FP64 probabilities of point 0 and the
  *       FP32 histograms to <output>; also checks the error paths of a live
  *       context.  The calling test compares the numbers with the oracle.
+ *   osc_abi_test time <input> <k>
+ *       loads the sample of <input>, then makes k fit steps (osc_histogram_point
+ *       of its first point, FP32-bulk, into a pageable host buffer) after three
+ *       untimed ones, and prints the wall time per step [us] (clock_gettime): the
+ *       end-to-end cost of the C ABI without any Python in between.
  *
  * Input layout (little endian): int64 n, int32 n_points, int32 nbins,
  * double lo, hi, baseline_km, density_gcc, ye; float e_true[n], e_reco[n],
@@ -16,9 +21,11 @@
  * Output: double hist64[n_points][nbins], prob64[n], hist32[n_points][nbins].
  * Exit status 0 on success; a message on stderr otherwise.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #include "osc.h"
 
@@ -135,9 +142,65 @@ static int gpu(const char *in_path, const char *out_path) {
     return 0;
 }
 
+static double now_s(void) {
+    struct timespec t;
+    clock_gettime(CLOCK_MONOTONIC, &t);
+    return (double)t.tv_sec + 1e-9 * (double)t.tv_nsec;
+}
+
+static int timing(const char *in_path, int k) {
+    void *buf = NULL;
+    size_t len = 0;
+    CHECK(k > 0, "k must be positive");
+    CHECK(read_all(in_path, &buf, &len) == 0, "cannot read the input file");
+    const char *p = (const char *)buf;
+    int64_t n;
+    int32_t n_points, nbins;
+    double hdr[5];
+    memcpy(&n, p, 8);
+    memcpy(&n_points, p + 8, 4);
+    memcpy(&nbins, p + 12, 4);
+    memcpy(hdr, p + 16, sizeof(hdr));
+    p += 16 + sizeof(hdr);
+    osc_sample_desc d;
+    d.n = n;
+    d.e_true = (const float *)p;
+    d.e_reco = d.e_true + n;
+    d.w_mc = d.e_reco + n;
+    d.flav_in = (const uint8_t *)(d.w_mc + n);
+    d.flav_out = d.flav_in + n;
+    d.is_nubar = d.flav_out + n;
+    d.baseline_km = hdr[2];
+    d.density_gcc = hdr[3];
+    d.ye = hdr[4];
+    osc_point pt;
+    memcpy(&pt, d.is_nubar + n, sizeof(osc_point));
+    osc_ctx *ctx = NULL;
+    CHECK(osc_create(0, 0, NULL, &ctx) == OSC_OK, "create");
+    int32_t sid = -1;
+    CHECK(osc_load_sample(ctx, &d, &sid) == OSC_OK, osc_last_error(ctx));
+    double *out = (double *)calloc((size_t)nbins, sizeof(double));
+    CHECK(out != NULL, "alloc");
+    for (int i = 0; i < 3; ++i)
+        CHECK(osc_histogram_point(ctx, &sid, 1, &pt, OSC_FP32_BULK, hdr[0], hdr[1], nbins, out, 0) == OSC_OK,
+              osc_last_error(ctx));
+    const double t0 = now_s();
+    for (int i = 0; i < k; ++i)
+        CHECK(osc_histogram_point(ctx, &sid, 1, &pt, OSC_FP32_BULK, hdr[0], hdr[1], nbins, out, 0) == OSC_OK,
+              osc_last_error(ctx));
+    const double dt = now_s() - t0;
+    CHECK(out[0] >= 0.0, "histogram");
+    printf("{\"steps\": %d, \"us_per_step\": %.3f, \"events\": %lld}\n", k, 1e6 * dt / k, (long long)n);
+    free(out);
+    osc_destroy(ctx);
+    free(buf);
+    return 0;
+}
+
 int main(int argc, char **argv) {
     if (argc >= 2 && strcmp(argv[1], "nogpu") == 0) return no_gpu();
     if (argc >= 4 && strcmp(argv[1], "gpu") == 0) return gpu(argv[2], argv[3]);
-    fprintf(stderr, "usage: osc_abi_test nogpu | gpu <input> <output>\n");
+    if (argc >= 4 && strcmp(argv[1], "time") == 0) return timing(argv[2], atoi(argv[3]));
+    fprintf(stderr, "usage: osc_abi_test nogpu | gpu <input> <output> | time <input> <k>\n");
     return 2;
 }

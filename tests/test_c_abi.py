@@ -63,3 +63,29 @@ def test_c_program_on_gpu(exe, tmp_path):
     for k in range(pts.shape[0]):
         wsum = oracle.hist_from_weights(s["e_reco"], np.abs(s["w_mc"]).astype(np.float64), pts[k][6], lo, hi, nbins)
         assert np.all(np.abs(h32[k] - ho[k]) <= 1e-5 * wsum + 1e-12)
+
+
+def _write_input(path, s, pts, nbins, lo, hi):
+    with open(path, "wb") as f:
+        f.write(np.array([s["n"]], np.int64).tobytes())
+        f.write(np.array([pts.shape[0], nbins], np.int32).tobytes())
+        f.write(np.array([lo, hi, s["baseline_km"], s["density_gcc"], s["ye"]], np.float64).tobytes())
+        for k in ("e_true", "e_reco", "w_mc"):
+            f.write(np.ascontiguousarray(s[k], np.float32).tobytes())
+        for k in ("flav_in", "flav_out", "is_nubar"):
+            f.write(np.ascontiguousarray(s[k], np.uint8).tobytes())
+        f.write(np.ascontiguousarray(pts, np.float64).tobytes())
+
+
+@pytest.mark.gpu
+def test_c_program_times_fit_steps(exe, tmp_path):
+    """The plain C program's timing mode: k fit steps (osc_histogram_point into a
+    host buffer) without any Python, reported per step."""
+    import json
+    s = synth.table1_sample(200_000, seed=62)
+    inp = tmp_path / "in.bin"
+    _write_input(inp, s, synth.table1_point()[None, :], 100, 0.0, 5.0)
+    r = subprocess.run([exe, "time", str(inp), "20"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert res["steps"] == 20 and res["events"] == s["n"] and res["us_per_step"] > 0

@@ -372,9 +372,32 @@ def test_histogram_point_graph_step_separate_finalize_and_layers(ctx):
                     got = api.osc_histogram_point(ctx, group, pts[k], prec, LO, HI, nb)
                     n2 = api.osc_launch_count(ctx)
                     assert np.array_equal(got, ref), (nb, prec, k)
-                    assert n2 - n1 == (n1 - n0) + 1  # the constants kernel is a node of the step's graph
+                    assert n2 - n1 == (n1 - n0) + 1, (nb, prec, k)  # the constants kernel is a node of the graph
     for sid in ids + [lid]:
         api.osc_unload_sample(ctx, sid)
+
+
+def test_histogram_point_graph_step_runs_the_recomputation_pass(ctx):
+    """At extreme mixing angles the FP32 kernels leave events to the FP64
+    recomputation pass: the graph step's conditional node then runs it, and the
+    bins equal the direct launches' (which always launch the pass) bitwise, for
+    the fused (100 bins) and separate (600 bins) finalize; the per-event
+    probabilities of those points stay within the FP32 tolerance."""
+    s = synth.all_channel_sample(20000, seed=28, L_km=295.0, rho=2.6, e_lo=0.05, e_hi=3.0)
+    sid = api.osc_load_sample(ctx, s)
+    pts = np.array([[0.01, 0.0251, 0.99, 7.6e-5, -2.4e-3, 3.1, 1.0, 1.0],
+                    [0.99, 0.0251, 0.01, 7.6e-5, 2.4e-3, -0.7, 1.0, 1.0]])
+    for k in range(2):
+        api.osc_set_params(ctx, pts[k:k + 1])
+        po, _ = oracle.reweight(s, oracle.point_from_row(pts[k]))
+        p32, _ = _gpu_probs(ctx, sid, 0, "fp32", s["n"])
+        assert np.max(np.abs(p32 - po)) <= 1e-5
+        for nb in (NB, 600):
+            ref = api.osc_histogram(ctx, [sid], 0, 1, "fp32", LO, HI, nb)
+            for _ in range(2):
+                got = api.osc_histogram_point(ctx, [sid], pts[k], "fp32", LO, HI, nb)
+                assert np.array_equal(got, ref), (k, nb)
+    api.osc_unload_sample(ctx, sid)
 
 
 def test_prepared_point_histogram_matches_the_plain_call(ctx):
