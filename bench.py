@@ -302,6 +302,8 @@ def _serving_leg(api, synth, c, rates, seconds, prec):
                 for i in range(n):
                     while tickets[i] is None:
                         time.sleep(0)
+                    if tickets[i] < 0:  # rejected at submission: the queue was full
+                        continue
                     _, lat[i] = api.osc_wait(c, tickets[i], NBINS, out=buf)
                     done[0] += 1
 
@@ -311,13 +313,25 @@ def _serving_leg(api, synth, c, rates, seconds, prec):
             for i in range(n):
                 while time.perf_counter() - t0 < t_arr[i]:
                     pass
-                tickets[i] = api.osc_submit(c, sids[sid_idx[i]], pts[i], prec)
+                try:
+                    tickets[i] = api.osc_submit(c, sids[sid_idx[i]], pts[i], prec)
+                except api.OscError as err:
+                    # above saturation the queue (2^20 requests) fills: the request is
+                    # shed, as a server under overload would, and counted
+                    if err.status != api.OSC_E_BUSY:
+                        for k in range(i, n):
+                            tickets[k] = -1
+                        th.join()
+                        raise
+                    tickets[i] = -1
             th.join()
             wall = time.perf_counter() - t0
-            evpt = float(sizes[sid_idx].sum())
-            out["rates"].append({"offered_req_s": rate, "requests": n, "achieved_req_s": n / wall,
-                                 "event_weights_s": evpt / wall, "p50_us": float(np.percentile(lat, 50)),
-                                 "p99_us": float(np.percentile(lat, 99))})
+            ok = np.array([t is not None and t >= 0 for t in tickets])
+            evpt = float(sizes[sid_idx[ok]].sum())
+            out["rates"].append({"offered_req_s": rate, "requests": n, "rejected_queue_full": int(n - ok.sum()),
+                                 "achieved_req_s": float(ok.sum()) / wall, "event_weights_s": evpt / wall,
+                                 "p50_us": float(np.percentile(lat[ok], 50)) if ok.any() else None,
+                                 "p99_us": float(np.percentile(lat[ok], 99)) if ok.any() else None})
         # saturation: everything queued at once
         nsat = 2000 if prec == "fp32" else 100
         rng = np.random.default_rng(5005)

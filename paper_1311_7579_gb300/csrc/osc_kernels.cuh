@@ -388,23 +388,21 @@ __device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long lon
                                        unsigned long long h) {
     asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
 }
-// Adds w * 2^F, truncated to an integer, using integer operations only (a
-// 64-bit float-to-integer conversion is an FP64-pipe instruction on this GPU).
-// F = 62 - ceil(log2 max|w_mc|) per sample, so |w| * 2^F < 2^63 and the
-// addend is the FP32 mantissa m shifted to bit s = e + sh (sh = F - 150) of a
-// 64-bit word; bits below the fixed-point LSB (2^-F) are dropped.
+// Adds w * 2^F, truncated to an integer (bits below the fixed-point LSB 2^-F
+// dropped).  F = 62 - ceil(log2 max|w_mc|) per sample, so x = |w| 2^F < 2^63.
+// x is formed by two exact power-of-two scalings (2^(F-64), then 2^64; F - 64
+// is a normal exponent for every F in [8, 190], and subnormal w scale exactly)
+// and split into 32-bit halves with float operations, each exact: the high half
+// floor(x 2^-32) and the remainder x - 2^32 floor(x 2^-32) are floats with at
+// most 24 significant bits, and both 32-bit conversions truncate toward zero.
+// (A 64-bit float-to-integer conversion is an FP64-pipe instruction on this
+// GPU; the two 32-bit ones are not.)  sh = F - 150.
 __device__ __forceinline__ void fx_add_f32(unsigned long long &lo, unsigned long long &hi, float w, int sh) {
-    const uint32_t u = __float_as_uint(w);
-    const int e = (int)((u >> 23) & 0xFFu);
-    const int s = e + sh;
-    unsigned long long v;
-    if (s >= 0 && s <= 40) {
-        v = (unsigned long long)((u & 0x7FFFFFu) | 0x800000u) << s;  // every normal weight in range
-    } else {
-        const unsigned long long m = (unsigned long long)((u & 0x7FFFFFu) | (e ? 0x800000u : 0u));
-        v = (s > 40) ? (m << 40) : ((s > -24) ? (m >> (-s)) : 0ull);
-    }
-    if (u >> 31) {
+    const float x = __fmul_rn(__fmul_rn(fabsf(w), __int_as_float((sh + 213) << 23)), 18446744073709551616.0f);
+    const float hf = floorf(__fmul_rn(x, 2.3283064365386963e-10f));
+    const float lf = __fmaf_rn(-hf, 4294967296.0f, x);
+    const unsigned long long v = ((unsigned long long)__float2uint_rz(hf) << 32) | __float2uint_rz(lf);
+    if (__float_as_uint(w) >> 31) {
         asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
     } else {
         asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));

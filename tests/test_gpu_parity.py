@@ -150,6 +150,28 @@ def test_histograms_multi_point_both_paths(ctx):
     api.osc_unload_sample(ctx, sid)
 
 
+def test_histograms_of_subnormal_weights(ctx):
+    """Every weight below the smallest normal float (max |w_mc| ~ 2^-134, the
+    fixed-point scale at its cap F = 190): each FP32 event weight P w_mc is a
+    subnormal float, and its fixed-point addend must still be floor(|P w_mc| 2^F),
+    so the FP32 bins equal the exact sums of the weights the GPU returns, and the
+    FP64 bins the oracle's."""
+    s = dict(synth.table1_sample(60000, seed=17))
+    s["w_mc"] = (s["w_mc"].astype(np.float64) * 2.0 ** -135).astype(np.float32)
+    assert np.all(np.abs(s["w_mc"]) < np.finfo(np.float32).tiny) and np.all(s["w_mc"] > 0)
+    sid = api.osc_load_sample(ctx, s)
+    pt = synth.table1_point()
+    api.osc_set_params(ctx, pt[None, :])
+    h32 = api.osc_histogram(ctx, [sid], 0, 1, "fp32", LO, HI, NB)[0, 0]
+    _, w32 = _gpu_probs(ctx, sid, 0, "fp32", s["n"])
+    assert h32.sum() > 0 and np.all(np.abs(w32) < np.finfo(np.float32).tiny)
+    _check_fp64_hist(h32, oracle.hist_from_weights(s["e_reco"], w32, pt[6], LO, HI, NB, compensated=True))
+    h64 = api.osc_histogram(ctx, [sid], 0, 1, "fp64", LO, HI, NB)[0, 0]
+    _, wo = oracle.reweight(s, oracle.point_from_row(pt))
+    _check_fp64_hist(h64, oracle.hist_from_weights(s["e_reco"], wo, pt[6], LO, HI, NB, compensated=True))
+    api.osc_unload_sample(ctx, sid)
+
+
 def test_histogram_bitwise_independent_of_tile_shape(ctx):
     s = synth.table1_sample(50000, seed=12)
     sid = api.osc_load_sample(ctx, s)
