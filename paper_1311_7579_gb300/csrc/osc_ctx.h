@@ -147,7 +147,7 @@ osc_status validate_point(osc_ctx *c, const osc_point &p, int index);
 osc_status debug_word_check(osc_ctx *c);
 osc_status ensure_acc(osc_ctx *c, int64_t bins);
 // grid of the persistent histogram kernel; finalize fusion rule
-int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items);
+int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items, int threads);
 bool fuse_finalize(int64_t n_hist, int32_t nbins, int32_t pt);
 int prec_kind(osc_precision p);
 // FP32-bulk through layers also needs dm21 >= kFp32LayerSolarRatio |dm31|: with a

@@ -930,14 +930,22 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
 // accumulator suffices.  Two events are computed per iteration.
 // Resident blocks per SM: the 256-point tile fits three blocks (80 registers,
 // no spills) and gains from the extra warps; the one-point path needs more
-// registers for its two events in flight, and FP64 more still.
+// registers for its two events in flight, and FP64 more still.  The FP32-bulk
+// one-point kernel, whose work items are per warp, runs 128-thread blocks, five
+// per SM: at 96 registers (a few bytes of spills outside the event loop) they
+// hold 20 warps per SM, where two 256-thread blocks of 125 registers hold 16.
+template <int PREC, int PT>
+constexpr int hist_block_threads() {
+    return (PREC == kFP32 && PT == 1) ? 128 : kNT;
+}
 template <int PREC, int PT>
 constexpr int hist_min_blocks() {
-    return PREC == kFP64 ? 1 : (PT == 256 ? 3 : 2);
+    return PREC == kFP64 ? 1 : (PT == 256 ? 3 : ((PREC == kFP32 && PT == 1) ? 5 : 2));
 }
 
 template <int PREC, int PT>
-__global__ void __launch_bounds__(kNT, (hist_min_blocks<PREC, PT>())) k_hist(const HistParams prm) {
+__global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_blocks<PREC, PT>()))
+    k_hist(const HistParams prm) {
     // a finalize kernel after this one (programmatic launch) may become resident
     // as blocks of this grid retire; it waits for the whole grid
     grid_dependents_launch();

@@ -82,6 +82,7 @@ cudaError_t launch_reweight_fp32(const ReweightParams &p, cudaStream_t st);
 cudaError_t launch_reweight_fp64(const ReweightParams &p, cudaStream_t st);
 
 int hist_threads() { return kNT; }
+int hist_threads_for(int prec, int pt) { return (prec == kFP32 && pt == 1) ? hist_block_threads<kFP32, 1>() : kNT; }
 
 const void *hist_kernel_fn(int prec, int pt) {
     return prec == kFP32 ? hist_kernel_fn_fp32(pt) : prec == kMix ? hist_kernel_fn_mix(pt) : hist_kernel_fn_fp64(pt);
@@ -129,7 +130,7 @@ cudaError_t launch_hist_programmatic(int prec, int pt, const HistParams &p, int 
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kNT);
+    cfg.blockDim = dim3(hist_threads_for(prec, pt));
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cfg.attrs = at;

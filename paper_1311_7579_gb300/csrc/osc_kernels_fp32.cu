@@ -17,7 +17,7 @@ const void *hist_kernel_fn_fp32(int pt) {
 
 cudaError_t launch_hist_fp32(int pt, const HistParams &p, int grid, cudaStream_t st) {
     switch (pt) {
-        case 1: k_hist<kFP32, 1><<<grid, kNT, 0, st>>>(p); break;
+        case 1: k_hist<kFP32, 1><<<grid, hist_block_threads<kFP32, 1>(), 0, st>>>(p); break;
         case 4: k_hist<kFP32, 4><<<grid, kNT, 0, st>>>(p); break;
         case 16: k_hist<kFP32, 16><<<grid, kNT, 0, st>>>(p); break;
         case 64: k_hist<kFP32, 64><<<grid, kNT, 0, st>>>(p); break;

@@ -36,6 +36,9 @@ cudaError_t launch_reweight_layers(int prec, const ReweightParams &p, cudaStream
 cudaError_t launch_hist_layers(int prec, const HistParams &p, int grid, cudaStream_t st);
 const void *final_kernel_fn();
 int hist_threads();
+// Threads per block of the event-by-event histogram kernel of a precision and
+// points-per-block (128 for the FP32-bulk one-point kernel, else hist_threads()).
+int hist_threads_for(int prec, int pt);
 // FP32 precisions: the FP64 recomputation pass after a histogram kernel (k_redo),
 // launched with programmatic stream serialization; its kernel function.
 cudaError_t launch_redo_programmatic(int prec, const HistParams &p, cudaStream_t st);

@@ -177,9 +177,9 @@ static osc_status ensure_buf(osc_ctx *c, double **buf, int64_t *cap, int64_t n) 
     return OSC_OK;
 }
 
-int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items) {
+int hist_grid(osc_ctx *c, const void *kernel, int32_t n_items, int threads) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, hist_threads(), 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
     if (per_sm < 1) per_sm = 1;
     int g = c->n_sm * per_sm;
     return std::max(1, std::min(g, n_items));
@@ -871,10 +871,11 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
     for (int32_t id : ids) ev += ctx->samples[id]->n;
     const int64_t tiles = (n_points + pt - 1) / pt;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_kernel_fn(prec, pt), hist_threads(), 0);
+    const int threads = hist_threads_for(prec, pt);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hist_kernel_fn(prec, pt), threads, 0);
     per_sm = std::max(per_sm, 1);
     // one point per item: items are taken per warp; otherwise per block
-    const int64_t slots = (int64_t)ctx->n_sm * per_sm * (pt == 1 ? hist_threads() / 32 : 1);
+    const int64_t slots = (int64_t)ctx->n_sm * per_sm * (pt == 1 ? threads / 32 : 1);
     const int64_t quantum = (pt == 1) ? 64 : 1024;
     // about 4 items per resident worker
     int64_t c = (ev * tiles + 4 * slots - 1) / (4 * slots);
@@ -886,6 +887,9 @@ static int32_t default_chunk(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
 // Histogram kernel of an event-by-event or layered plan.
 static const void *plan_kernel(const Plan *p) {
     return p->kind == kLayered ? layers_hist_kernel_fn(p->prec) : hist_kernel_fn(p->prec, p->pt);
+}
+static int plan_threads(const Plan *p) {
+    return p->kind == kLayered ? hist_threads() : hist_threads_for(p->prec, p->pt);
 }
 
 // Keep at most 16 cached plans: evict the least recently used one.
@@ -942,12 +946,12 @@ static osc_status get_plan(osc_ctx *ctx, const std::vector<int32_t> &ids, int32_
         sdev.push_back(ctx->samples[id]->dev);
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel(p), hist_threads(), 0);
-    const int64_t slots = (int64_t)ctx->n_sm * std::max(per_sm, 1) * (pt == 1 ? hist_threads() / 32 : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel(p), plan_threads(p), 0);
+    const int64_t slots = (int64_t)ctx->n_sm * std::max(per_sm, 1) * (pt == 1 ? plan_threads(p) / 32 : 1);
     std::vector<WorkItem> items;
     build_items(ss, point_begin, n_points, pt, chunk, slots, 0, items);
     p->n_items = (int32_t)items.size();
-    p->grid = hist_grid(ctx, plan_kernel(p), p->n_items);
+    p->grid = hist_grid(ctx, plan_kernel(p), p->n_items, plan_threads(p));
     const std::vector<double> hmeta = hist_meta(ss, point_begin, n_points);
     void *a;
     osc_status st = OSC_OK;
@@ -999,7 +1003,7 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
     cudaKernelNodeParams kh{};
     kh.func = (void *)plan_kernel(p);
     kh.gridDim = dim3(p->grid);
-    kh.blockDim = dim3(hist_threads());
+    kh.blockDim = dim3(plan_threads(p));
     kh.kernelParams = hargs;
     cudaKernelNodeParams kf{};
     kf.func = (void *)final_kernel_fn();
@@ -1027,7 +1031,7 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(p->grid);
-        cfg.blockDim = dim3(hist_threads());
+        cfg.blockDim = dim3(plan_threads(p));
         cfg.dynamicSmemBytes = 0;
         cfg.stream = ctx->stream;
         cfg.attrs = at;
@@ -1116,7 +1120,7 @@ static osc_status run_step_graph(osc_ctx *ctx, Plan *p, const osc_point &pt, dou
     kc.kernelParams = cargs;
     kh.func = (void *)plan_kernel(p);
     kh.gridDim = dim3(p->grid);
-    kh.blockDim = dim3(hist_threads());
+    kh.blockDim = dim3(plan_threads(p));
     kh.kernelParams = hargs;
     if (p->step_exec && p->step_fused != fused) {
         cudaGraphExecDestroy(p->step_exec);

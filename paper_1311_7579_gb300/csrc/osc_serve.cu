@@ -227,7 +227,8 @@ osc_status launch_batch(osc_serve *sv, Batch &b) {
             hl.fuse_final = 0;
             e = cudaMemsetAsync(hl.counter, 0, 2 * sizeof(int32_t), st);
         }
-        if (!e) e = launch_hist_layers(prec, hl, hist_grid(ctx, layers_hist_kernel_fn(prec), (n_lay + 7) / 8), st);
+        if (!e) e = launch_hist_layers(prec, hl, hist_grid(ctx, layers_hist_kernel_fn(prec), (n_lay + 7) / 8, hist_threads()),
+                                            st);
         ++kernels;
     }
     if (!e && n_lay < n_items) {
@@ -236,7 +237,9 @@ osc_status launch_batch(osc_serve *sv, Batch &b) {
         hs.n_items = n_items - n_lay;
         // programmatic launch after the kernel before it (constants or layered histogram)
         if (prec != kFP64) hs.redo = b.d_redo;
-        e = launch_hist_programmatic(prec, 1, hs, hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + 7) / 8), st);
+        const int thr = hist_threads_for(prec, 1), wpb = thr / 32;
+        e = launch_hist_programmatic(prec, 1, hs,
+                                     hist_grid(ctx, hist_kernel_fn(prec, 1), (hs.n_items + wpb - 1) / wpb, thr), st);
         ++kernels;
         // FP32 precisions: the FP64 recomputation pass (returns at once when no event was left out)
         if (!e && prec != kFP64) {
