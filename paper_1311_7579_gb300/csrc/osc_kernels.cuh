@@ -629,7 +629,7 @@ __device__ __forceinline__ void event_terms32(const SampleDev &sd, float E, int 
     const float r0 = rcp_approx(E);
     const float rl = r0 * fmaf(-E, r0, 1.0f);
     th = sd.rev_hi * r0;  // |tl| stays below ulp(th): no renormalisation needed
-    tl = fmaf(sd.rev_hi, r0, -th) + fmaf(sd.rev_hi, rl, sd.rev_lo * r0);
+    tl = fmaf(sd.rev_lo, r0, fmaf(sd.rev_hi, rl, fmaf(sd.rev_hi, r0, -th)));
 }
 
 // ------------------------------------------------------------ event staging

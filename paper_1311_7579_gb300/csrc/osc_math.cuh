@@ -78,7 +78,7 @@ __device__ __forceinline__ float acos_third(float x) {
 // the seven-term form above.
 __device__ __forceinline__ float acos_third_short(float x) {
     constexpr float k = 1.0f / 3.0f;
-    const float ax = fabsf(x);
+    const float ax = fminf(fabsf(x), 1.0f);  // rounding can put |cos theta| just above 1
     float p = -0.0187293f * k;
     p = fmaf(p, ax, 0.0742610f * k);
     p = fmaf(p, ax, -0.2121144f * k);
@@ -130,10 +130,9 @@ __device__ __forceinline__ float shifted_newton(float dl, float A, float S, floa
 // th + tl = c_L L / (2 pi E) (float-float), vh + vl = d_l - d_0, dd = delta_l - delta_0.
 __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float vl, float dd) {
     const float ph = th * vh;
-    const float e1 = fmaf(th, vh, -ph);
-    const float e2 = fmaf(th, vl, tl * vh);
-    const float fr = ph - rintf(ph);  // exact
-    return fr + fmaf(th, dd, e1 + e2);
+    const float e1 = fmaf(th, vh, -ph);  // exact residual of the product
+    const float fr = ph - rintf(ph);     // exact
+    return fr + fmaf(th, dd, fmaf(th, vl, fmaf(tl, vh, e1)));
 }
 
 // Trigonometric FP32 seed of the two lower roots m0 <= m1 of the depressed
@@ -200,6 +199,23 @@ __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0,
 __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1) {
     float cth;
     seed_scaled32(c, A, m0, m1, cth);
+}
+// The same seed as (r, t0, t1) with m0 = -r t0 and m1 = -r t1, t0,1 = cos(theta/3)
+// +- sqrt(3) sin(theta/3), so that the caller folds the products into its own
+// sums.  cth is returned unclamped (the short arccos clamps |x| itself).
+template <bool SHORT>
+__device__ __forceinline__ void seed_scaled32_rt(const Pt32 &c, float A, float &r, float &t0, float &t1,
+                                                 float &cth) {
+    const float mp3 = fmaxf(fmaf(fmaf(A, 1.0f / 9.0f, c.p1), A, c.p0), 1e-30f);
+    const float qh = fmaf(fmaf(fmaf(A, 1.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
+    const float ir = rsqrt_approx(mp3);
+    r = mp3 * ir;
+    cth = qh * ir * ir * ir;
+    const float th3 = SHORT ? acos_third_short(cth) : acos_third(fminf(fmaxf(cth, -1.0f), 1.0f));
+    float sn, cs;
+    __sincosf(th3, &sn, &cs);
+    t0 = fmaf(1.7320508075688772f, sn, cs);
+    t1 = fmaf(-1.7320508075688772f, sn, cs);
 }
 // As roots mu of the depressed cubic (lambda = mu + (T0 + A) / 3).
 __device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, float &m1, float &t3, float &cth) {
@@ -278,11 +294,11 @@ __device__ __forceinline__ float amplitude_mass32(const Pt32 &c, const Ch32 &h, 
 // per-event error bound guards it); the layered path keeps the eight-term one.
 template <bool SHORT = true>
 __device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2, float &cth) {
-    float m0, m1;
-    seed_scaled32<SHORT>(c, A, m0, m1, cth);
-    // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) + m_l
-    dl0 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td0) + m0, A, c.S0, c.PI0, c.W0, c.E0);
-    dl1 = shifted_newton(fmaf(A, 1.0f / 3.0f, c.td1) + m1, A, c.S1, c.PI1, c.W1, c.E1);
+    float r, t0, t1;
+    seed_scaled32_rt<SHORT>(c, A, r, t0, t1, cth);
+    // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) - r t_l
+    dl0 = shifted_newton(fmaf(-r, t0, fmaf(A, 1.0f / 3.0f, c.td0)), A, c.S0, c.PI0, c.W0, c.E0);
+    dl1 = shifted_newton(fmaf(-r, t1, fmaf(A, 1.0f / 3.0f, c.td1)), A, c.S1, c.PI1, c.W1, c.E1);
     dl2 = A - dl0 - dl1;
 }
 __device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
