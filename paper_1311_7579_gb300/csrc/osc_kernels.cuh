@@ -466,7 +466,9 @@ __device__ __forceinline__ double final_bin(const Digits &g, const double *m, co
 // Small outputs (one conversion round: up to 256 bins for a block, 128 for a
 // warp; larger outputs go to the finalize kernel, launched programmatically):
 // the last block or warp of the histogram kernel to finish converts the bins
-// instead of a separate launch.  Every thread fences its own flushes before its
+// instead of a separate launch (or, for the FP32 precisions, the FP64
+// recomputation pass launched after it does, which waits for the whole grid
+// anyway).  Every thread fences its own flushes before its
 // block or warp takes its completion ticket.  The last one runs alone at the
 // end of the grid, so it issues the loads of all its bins (digit columns and
 // histogram scales, then the points' norms) before it converts any of them.
@@ -478,8 +480,6 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // events left to the FP64 recomputation: the redo kernel adds them, then converts
-    if (prm.redo && __ldcg(prm.counter + kRedoCount) > 0) return;
     const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const Digits g = load_digits(prm.acc, i);
@@ -507,8 +507,6 @@ __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
-    // events left to the FP64 recomputation: the redo kernel adds them, then converts
-    if (prm.redo && __ldcg(prm.counter + kRedoCount) > 0) return;
     convert_bins_warp(prm);
 }
 // The last warp's conversion of the fused finalize (four bins per lane per round,
@@ -951,7 +949,8 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
     grid_dependents_launch();
     if constexpr (PT == 1) {
         hist_items_per_warp<PREC>(prm);
-        if (prm.fuse_final) fused_final_warp(prm);
+        // with an FP64 recomputation pass after it (prm.redo), that kernel converts the bins
+        if (prm.fuse_final && !prm.redo) fused_final_warp(prm);
         return;
     } else {
         constexpr int S = kNT / PT;
@@ -1090,7 +1089,7 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
             }
             acc_finish(r, accp);
         }
-        if (prm.fuse_final) fused_final(prm);
+        if (prm.fuse_final && !prm.redo) fused_final(prm);
     }
 }
 
@@ -1109,7 +1108,12 @@ template <int PREC>
 __global__ void __launch_bounds__(kNT) k_redo(const HistParams prm) {
     grid_dependents_launch();  // a finalize kernel after this one may become resident early
     grid_dependency_wait();
-    if (__ldcg(prm.counter + kRedoCount) == 0) return;
+    if (__ldcg(prm.counter + kRedoCount) == 0) {
+        // nothing to recompute: one warp does the fused finalize the histogram
+        // kernel left to this kernel (and resets the work counters)
+        if (prm.fuse_final && blockIdx.x == 0 && threadIdx.x < 32) convert_bins_warp(prm);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int n_warps = (int)(gridDim.x * (blockDim.x >> 5));
     for (int it = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); it < prm.n_items; it += n_warps) {
