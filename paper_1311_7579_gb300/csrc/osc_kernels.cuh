@@ -556,11 +556,9 @@ struct RunAcc {
     unsigned long long lo, hi;
     int cur_b;
 };
-__device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
-                                              float er, float wt, int sh, bool active) {
-    const float x = __fmul_rn(sf, er);
-    const float tb = __fsub_rn(x, prm.lo_f);
-    const float u = __fmul_rn(tb, prm.inv_f);
+// tb = sf E_reco - lo and u = tb / width (by the reciprocal width) decide the bin.
+__device__ __forceinline__ void acc_event_u(RunAcc &r, unsigned long long *accp, const HistParams &prm, float tb,
+                                            float u, float wt, int sh, bool active) {
     if (active && tb >= 0.0f && u < prm.nb_f) {
         const int b = __float2int_rz(u);
         if (!debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) return;
@@ -571,6 +569,20 @@ __device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *acc
         }
         fx_add_f32(r.lo, r.hi, wt, sh);
     }
+}
+__device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
+                                              float er, float wt, int sh, bool active) {
+    const float tb = vsub(vmul(sf, er), prm.lo_f);
+    acc_event_u(r, accp, prm, tb, vmul(tb, prm.inv_f), wt, sh, active);
+}
+// Two events in order (a, then b), their bin arithmetic in one packed chain:
+// the same bins and sums as two acc_event_f32 calls.
+__device__ __forceinline__ void acc_pair_f32(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
+                                             float2 er, float2 wt, int sh, bool act_a, bool act_b) {
+    const float2 tb = vsub(vmul(vb<float2>(sf), er), vb<float2>(prm.lo_f));
+    const float2 u = vmul(tb, vb<float2>(prm.inv_f));
+    acc_event_u(r, accp, prm, tb.x, u.x, wt.x, sh, act_a);
+    acc_event_u(r, accp, prm, tb.y, u.y, wt.y, sh, act_b);
 }
 __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
                                               float er, double wt, double hs, bool active) {
@@ -620,21 +632,37 @@ __device__ __forceinline__ void acc_finish_warp(RunAcc &r, unsigned long long *a
 // Counts a work item marked for the FP64 recomputation pass.
 __device__ __forceinline__ void mark_redo(const HistParams &prm) { atomicAdd(prm.counter + kRedoCount, 1); }
 
-// FP32 matter term and c_L L / (2 pi E) float-float of one event.
+// FP32 matter term A = +-k_A rho Y_e E and c_L L / (2 pi E) as a float-float
+// th + tl, for one or two events (kA: +-k_A rho Y_e per lane), returned as
+// (A, th, -tl).  1/E = r0 + rl to ~1e-14: the residual 1 - E r0 of the
+// approximate reciprocal is exact in FP32; r0 enters negated (rcp(-E)), which
+// negates rl and the whole low part without a packed negation.
+template <class V>
+__device__ __forceinline__ void event_terms_bulk(const SampleDev &sd, V E, V kA, V &A, V &th, V &ntl) {
+    A = vmul(kA, E);
+    const V r0n = vmap(E, [](float v) { return rcp_approx(-v); });  // -r0
+    const V rln = vmul(r0n, vfma(E, r0n, vb<V>(1.0f)));               // -rl
+    th = vmul(vb<V>(-sd.rev_hi), r0n);  // |tl| stays below ulp(th): no renormalisation needed
+    ntl = vfma(vb<V>(sd.rev_lo), r0n, vfma(vb<V>(sd.rev_hi), rln, vfma(vb<V>(sd.rev_hi), r0n, th)));
+}
+__device__ __forceinline__ float kA_lane(const SampleDev &sd, int ch) {
+    return (ch >= 9) ? -sd.kA_rhoye_f : sd.kA_rhoye_f;
+}
+// One event, as (A, th, tl).
 __device__ __forceinline__ void event_terms32(const SampleDev &sd, float E, int ch, float &A, float &th, float &tl) {
-    A = (ch >= 9) ? -(sd.kA_rhoye_f * E) : sd.kA_rhoye_f * E;
-    // 1/E = r0 + rl to ~1e-14: the residual 1 - E r0 of the approximate reciprocal is exact in FP32
-    const float r0 = rcp_approx(E);
-    const float rl = r0 * fmaf(-E, r0, 1.0f);
-    th = sd.rev_hi * r0;  // |tl| stays below ulp(th): no renormalisation needed
-    tl = fmaf(sd.rev_lo, r0, fmaf(sd.rev_hi, rl, fmaf(sd.rev_hi, r0, -th)));
+    float ntl;
+    event_terms_bulk(sd, E, kA_lane(sd, ch), A, th, ntl);
+    tl = -ntl;
 }
 
 // ------------------------------------------------------------ event staging
-struct Stage32 {
-    float2 ae[kET];  // (A signed, e_reco)
-    float2 tt[kET];  // c_L L / (2 pi E) float-float
-    float2 wc[kET];  // (w_mc, channel bits)
+struct Stage32 {  // one array per field: a lane's two events (j, j + 1) load as packed pairs
+    float A[kET];    // signed matter term
+    float th[kET];   // c_L L / (2 pi E) float-float: th, -tl
+    float ntl[kET];
+    float er[kET];   // e_reco
+    float w[kET];    // w_mc
+    int ch[kET];     // channel
 };
 struct Stage64 {
     double a[kET];
@@ -645,11 +673,10 @@ struct Stage64 {
 };
 
 __device__ __forceinline__ void stage_one32(Stage32 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
-    float A, th, tl;
-    event_terms32(sd, E, ch, A, th, tl);
-    s.ae[j] = make_float2(A, er);
-    s.tt[j] = make_float2(th, tl);
-    s.wc[j] = make_float2(w, __int_as_float(ch));
+    event_terms_bulk(sd, E, kA_lane(sd, ch), s.A[j], s.th[j], s.ntl[j]);
+    s.er[j] = er;
+    s.w[j] = w;
+    s.ch[j] = ch;
 }
 __device__ __forceinline__ void stage_one64(Stage64 &s, int j, const SampleDev &sd, float E, float er, float w, int ch) {
     const double Ad = sd.kA_rhoye * (double)E;
@@ -796,22 +823,17 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                     Enb = q.x; rnb = q.y; wnb = q.z; cnb = __float_as_int(q.w);
                 }
                 if (ca == cur_ch && (!has_b || cb == cur_ch)) {
-                    float Aa, tha, tla, Ab, thb, tlb;
-                    event_terms32(sd, Ea, ca, Aa, tha, tla);
-                    event_terms32(sd, Eb, cb, Ab, thb, tlb);
-                    bool xa, xb;
-                    float Pa, Pb;
-                    if (h32.real) {
-                        Pa = prob_fp32<true>(c32, h32, Aa, tha, tla, xa);
-                        Pb = prob_fp32<true>(c32, h32, Ab, thb, tlb, xb);
-                    } else {
-                        Pa = prob_fp32<false>(c32, h32, Aa, tha, tla, xa);
-                        Pb = prob_fp32<false>(c32, h32, Ab, thb, tlb, xb);
-                    }
-                    xb = xb && has_b;
+                    // both events in one packed chain
+                    float2 A, th, ntl;
+                    event_terms_bulk(sd, make_float2(Ea, Eb), make_float2(kA_lane(sd, ca), kA_lane(sd, cb)), A, th,
+                                     ntl);
+                    unsigned x;
+                    const float2 P = h32.real ? prob_bulk<true>(c32, h32, A, th, ntl, x)
+                                              : prob_bulk<false>(c32, h32, A, th, ntl, x);
+                    const bool xa = x & 1u, xb = has_b && (x & 2u);
                     redo = redo || xa || xb;
-                    acc_event_f32(r, accp, prm, sf, ra, Pa * wa, sh, !xa);
-                    acc_event_f32(r, accp, prm, sf, rb, Pb * wb, sh, has_b && !xb);
+                    acc_pair_f32(r, accp, prm, sf, make_float2(ra, rb), vmul(P, make_float2(wa, wb)), sh, !xa,
+                                 has_b && !xb);
                 } else {
                     for (int k = 0; k < 2; ++k) {
                         const float E = k ? Eb : Ea, er = k ? rb : ra, w = k ? wb : wa;
@@ -938,7 +960,7 @@ constexpr int hist_block_threads() {
 }
 template <int PREC, int PT>
 constexpr int hist_min_blocks() {
-    return PREC == kFP64 ? 1 : (PT == 256 ? 3 : ((PREC == kFP32 && PT == 1) ? 5 : 2));
+    return PREC == kFP64 ? 1 : (PT == 256 ? 3 : ((PREC == kFP32 && PT == 1) ? 4 : 2));
 }
 
 template <int PREC, int PT>
@@ -990,39 +1012,38 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
                     stage_tile<PREC>(stg, sd, wi.ev_begin + t0, nt);
                     __syncthreads();
                     const Stage32 &s = reinterpret_cast<const Stage32 &>(stg);
-                    for (int j = sl; j < nt; j += 2 * S) {
-                        const int j2 = j + S;
-                        const bool has_b = j2 < nt;
-                        const float2 aea = s.ae[j], tta = s.tt[j], wca = s.wc[j];
-                        const float2 aeb = s.ae[has_b ? j2 : j], ttb = s.tt[has_b ? j2 : j], wcb = s.wc[has_b ? j2 : j];
-                        const int ca = __float_as_int(wca.y), cb = __float_as_int(wcb.y);
+                    // lane sl takes the event pairs (2 sl, 2 sl + 1), (2 (sl + S), ...): an
+                    // increasing sequence, so its bins are monotone within a channel
+                    for (int j = 2 * sl; j < nt; j += 2 * S) {
+                        const bool has_b = j + 1 < nt;  // j + 1 < kET: a stale value past nt is never used
+                        const int ca = s.ch[j], cb = has_b ? s.ch[j + 1] : ca;
                         if (ca == cur_ch && cb == cur_ch) {
-                            bool xa, xb;
-                            float Pa, Pb;
-                            if (h.real) {
-                                Pa = prob_fp32<true>(c, h, aea.x, tta.x, tta.y, xa);
-                                Pb = prob_fp32<true>(c, h, aeb.x, ttb.x, ttb.y, xb);
-                            } else {
-                                Pa = prob_fp32<false>(c, h, aea.x, tta.x, tta.y, xa);
-                                Pb = prob_fp32<false>(c, h, aeb.x, ttb.x, ttb.y, xb);
-                            }
-                            xb = xb && has_b;
+                            // both events in one packed chain
+                            const float2 A = *reinterpret_cast<const float2 *>(s.A + j);
+                            const float2 th = *reinterpret_cast<const float2 *>(s.th + j);
+                            const float2 ntl = *reinterpret_cast<const float2 *>(s.ntl + j);
+                            unsigned x;
+                            const float2 P = h.real ? prob_bulk<true>(c, h, A, th, ntl, x)
+                                                    : prob_bulk<false>(c, h, A, th, ntl, x);
+                            const bool xa = x & 1u, xb = has_b && (x & 2u);
                             redo = redo || (active && (xa || xb));
-                            acc_event_f32(r, accp, prm, sf, aea.y, Pa * wca.x, sh, active && !xa);
-                            acc_event_f32(r, accp, prm, sf, aeb.y, Pb * wcb.x, sh, active && has_b && !xb);
+                            acc_pair_f32(r, accp, prm, sf, *reinterpret_cast<const float2 *>(s.er + j),
+                                         vmul(P, *reinterpret_cast<const float2 *>(s.w + j)), sh, active && !xa,
+                                         active && has_b && !xb);
                         } else {
                             for (int k = 0; k < 2; ++k) {
                                 if (k && !has_b) break;
-                                const float2 ae = k ? aeb : aea, tt = k ? ttb : tta, wc = k ? wcb : wca;
+                                const int jj = j + k;
                                 const int ch = k ? cb : ca;
                                 if (ch != cur_ch) {
                                     cur_ch = ch;
                                     load_ch32(pc, ch, h);
                                 }
-                                bool x;
-                                const float P = prob_fp32(c, h, ae.x, tt.x, tt.y, x);
+                                unsigned x;
+                                const float P = h.real ? prob_bulk<true>(c, h, s.A[jj], s.th[jj], s.ntl[jj], x)
+                                                       : prob_bulk<false>(c, h, s.A[jj], s.th[jj], s.ntl[jj], x);
                                 redo = redo || (active && x);
-                                acc_event_f32(r, accp, prm, sf, ae.y, P * wc.x, sh, active && !x);
+                                acc_event_f32(r, accp, prm, sf, s.er[jj], vmul(P, s.w[jj]), sh, active && !x);
                             }
                         }
                     }

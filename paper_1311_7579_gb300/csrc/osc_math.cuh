@@ -47,6 +47,64 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// ------------------------------------------------- one or two events at once
+// The FP32-bulk chain (acos_third_short, shifts_bulk, phase_rev_bulk,
+// amplitude_bulk, prob_bulk) is written once over V = float (one event) or
+// V = float2 (two events, one in each half of this GPU's packed add / sub /
+// mul / fma.f32x2 instructions, which issue once for both).  Every operation
+// is explicitly rounded -- the compiler contracts nothing -- so both forms, and
+// every kernel that uses either, give the same bits for an event.  The packed
+// instructions take no negated operands, so the chain carries exactly negated
+// terms where a negation would otherwise be needed (-1/E, -tl, -(-p/3), -g01).
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as the fused b (-1) + a: one rounding, so the same bits as a subtraction
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// A scalar in every lane.
+template <class V>
+__device__ __forceinline__ V vb(float x);
+template <>
+__device__ __forceinline__ float vb<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float2 vb<float2>(float x) { return make_float2(x, x); }
+// Lane access, and lane-wise application of operations that have no packed form.
+template <class V>
+struct Lanes;
+template <>
+struct Lanes<float> {
+    static constexpr int n = 1;
+    static __device__ __forceinline__ float get(float a, int) { return a; }
+    static __device__ __forceinline__ void set(float &a, int, float v) { a = v; }
+};
+template <>
+struct Lanes<float2> {
+    static constexpr int n = 2;
+    static __device__ __forceinline__ float get(float2 a, int i) { return i ? a.y : a.x; }
+    static __device__ __forceinline__ void set(float2 &a, int i, float v) { (i ? a.y : a.x) = v; }
+};
+template <class V, class F>
+__device__ __forceinline__ V vmap(V a, F f) {
+    V r;
+#pragma unroll
+    for (int i = 0; i < Lanes<V>::n; ++i) Lanes<V>::set(r, i, f(Lanes<V>::get(a, i)));
+    return r;
+}
+template <class V>
+__device__ __forceinline__ void vsincos(V x, V &s, V &c) {
+#pragma unroll
+    for (int i = 0; i < Lanes<V>::n; ++i) {
+        float si, ci;
+        __sincosf(Lanes<V>::get(x, i), &si, &ci);
+        Lanes<V>::set(s, i, si);
+        Lanes<V>::set(c, i, ci);
+    }
+}
+
 // arccos(x) / 3 on [-1, 1] from Abramowitz & Stegun, Handbook of Mathematical
 // Functions, formula 4.4.46: acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7)
 // for 0 <= x <= 1 with |error| <= 2e-8, and acos(-x) = pi - acos(x); the
@@ -76,17 +134,26 @@ __device__ __forceinline__ float acos_third(float x) {
 // sends every event the step would not settle to the FP64 recomputation.  The
 // FP64 and FP64-eigen paths, whose Newton polish must reach FP64 accuracy, take
 // the seven-term form above.
-__device__ __forceinline__ float acos_third_short(float x) {
+template <class V>
+__device__ __forceinline__ V acos_third_short(V x) {
     constexpr float k = 1.0f / 3.0f;
-    const float ax = fminf(fabsf(x), 1.0f);  // rounding can put |cos theta| just above 1
-    float p = -0.0187293f * k;
-    p = fmaf(p, ax, 0.0742610f * k);
-    p = fmaf(p, ax, -0.2121144f * k);
-    p = fmaf(p, ax, 1.5707288f * k);
-    float sq;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(1.0f - ax));
-    const float r = sq * p;
-    return x < 0.0f ? 3.14159265358979323846f * k - r : r;
+    // rounding can put |cos theta| just above 1
+    const V ax = vmap(x, [](float v) { return fminf(fabsf(v), 1.0f); });
+    V p = vfma(vb<V>(-0.0187293f * k), ax, vb<V>(0.0742610f * k));
+    p = vfma(p, ax, vb<V>(-0.2121144f * k));
+    p = vfma(p, ax, vb<V>(1.5707288f * k));
+    const V sq = vmap(vsub(vb<V>(1.0f), ax), [](float v) {
+        float q;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(v));
+        return q;
+    });
+    const V r = vmul(sq, p);
+    const V rc = vsub(vb<V>(3.14159265358979323846f * k), r);
+    V out;
+#pragma unroll
+    for (int i = 0; i < Lanes<V>::n; ++i)
+        Lanes<V>::set(out, i, Lanes<V>::get(x, i) < 0.0f ? Lanes<V>::get(rc, i) : Lanes<V>::get(r, i));
+    return out;
 }
 
 struct Pt32 {
@@ -114,16 +181,18 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return r;
 }
 
-__device__ __forceinline__ float shifted_newton(float dl, float A, float S, float PI, float W, float E) {
+template <class V>
+__device__ __forceinline__ V shifted_newton(V dl, V A, float S, float PI, float W, float E) {
     // one Newton step on g(delta) = delta^3 + b delta^2 + c delta - e, with
-    // t = delta (delta + b) + c:  g = t delta - e,  g' = t + delta (2 delta + b)
-    const float b = S - A;
-    const float c = fmaf(-A, W, PI);
-    const float e = A * E;
-    const float t = fmaf(dl + b, dl, c);
-    const float g = fmaf(t, dl, -e);
-    const float gp = fmaf(dl, fmaf(2.0f, dl, b), t);
-    return fmaf(-g, rcp_approx(gp), dl);
+    // t = delta (delta + b) + c:  g = t delta - e,  g' = t + delta (2 delta + b);
+    // -e and -1/g' are formed directly (A (-E), rcp(-g'))
+    const V b = vsub(vb<V>(S), A);
+    const V c = vfma(A, vb<V>(-W), vb<V>(PI));
+    const V ne = vmul(A, vb<V>(-E));
+    const V t = vfma(vadd(dl, b), dl, c);
+    const V g = vfma(t, dl, ne);
+    const V gp = vfma(dl, vfma(vb<V>(2.0f), dl, b), t);
+    return vfma(g, vmap(gp, [](float v) { return rcp_approx(-v); }), dl);
 }
 
 // Phase of root l relative to root 0 in revolutions, reduced to about [-0.62, 0.62]:
@@ -140,8 +209,6 @@ __device__ __forceinline__ float phase_rev(float th, float tl, float vh, float v
 // from mp3 = -p/3 and qh = -q/2: mu = 2 r cos(theta/3 + 2 pi k/3) with
 // r = sqrt(mp3) and cos(theta) = qh / r^3.
 // Also returns cos(theta): near +-1 the angle is ill-conditioned (see near_double_pair64).
-// SHORT: the four-term arccos (FP32-bulk shifts), else the eight-term one.
-template <bool SHORT = false>
 __device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, float &m1, float &cth_out) {
     mp3 = fmaxf(mp3, 1e-30f);
     const float ir = rsqrt_approx(mp3);
@@ -149,7 +216,7 @@ __device__ __forceinline__ void seed_core32(float mp3, float qh, float &m0, floa
     float cth = qh * ir * ir * ir;
     cth = fminf(fmaxf(cth, -1.0f), 1.0f);
     cth_out = cth;
-    const float th3 = SHORT ? acos_third_short(cth) : acos_third(cth);
+    const float th3 = acos_third(cth);
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     const float rc = r * cs, rsn = r * sn * 1.7320508075688772f;
@@ -190,11 +257,10 @@ static __device__ __noinline__ double2 near_double_pair64(double p, double q, fl
 
 // The same seed for the characteristic cubic of one event, from the point's
 // pre-scaled coefficients: -p/3 = P0 + P1 A + A^2/9, -q/2 = Q0 + Q1 A + Q2 A^2 + A^3/27.
-template <bool SHORT = false>
 __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1, float &cth) {
     const float mp3 = fmaf(fmaf(A, 1.0f / 9.0f, c.p1), A, c.p0);
     const float qh = fmaf(fmaf(fmaf(A, 1.0f / 27.0f, c.q2), A, c.q1), A, c.q0);
-    seed_core32<SHORT>(mp3, qh, m0, m1, cth);
+    seed_core32(mp3, qh, m0, m1, cth);
 }
 __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0, float &m1) {
     float cth;
@@ -202,8 +268,8 @@ __device__ __forceinline__ void seed_scaled32(const Pt32 &c, float A, float &m0,
 }
 // The same seed as (r, t0, t1) with m0 = -r t0 and m1 = -r t1, t0,1 = cos(theta/3)
 // +- sqrt(3) sin(theta/3), so that the caller folds the products into its own
-// sums.  cth is returned unclamped (the short arccos clamps |x| itself).
-template <bool SHORT>
+// sums (the layered path's shifts; the single-layer FP32-bulk path forms the
+// same seed in shifts_bulk with the short arccos).
 __device__ __forceinline__ void seed_scaled32_rt(const Pt32 &c, float A, float &r, float &t0, float &t1,
                                                  float &cth) {
     const float mp3 = fmaxf(fmaf(fmaf(A, 1.0f / 9.0f, c.p1), A, c.p0), 1e-30f);
@@ -211,7 +277,7 @@ __device__ __forceinline__ void seed_scaled32_rt(const Pt32 &c, float A, float &
     const float ir = rsqrt_approx(mp3);
     r = mp3 * ir;
     cth = qh * ir * ir * ir;
-    const float th3 = SHORT ? acos_third_short(cth) : acos_third(fminf(fmaxf(cth, -1.0f), 1.0f));
+    const float th3 = acos_third(fminf(fmaxf(cth, -1.0f), 1.0f));
     float sn, cs;
     __sincosf(th3, &sn, &cs);
     t0 = fmaf(1.7320508075688772f, sn, cs);
@@ -243,91 +309,153 @@ __device__ __forceinline__ void seed_roots32(const Pt32 &c, float A, float &m0, 
 // est: the amplitude's rounding error bound in units of 2^-24, the magnitudes of
 // the summed terms of each N_l (and the operands of the A term) times |w_l|.
 // REAL: the mu -> mu and tau -> tau channels (X_m real, Z = 0).
+// ng01 = -g01 (the packed form has no negated operand; see the lane notes above).
+template <bool REAL, class V>
+__device__ __forceinline__ V amplitude_bulk(const Pt32 &c, const Ch32 &h, V A, V dl0, V dl1, V dl2, V ng01, V g02,
+                                            V g12, V h1, V h2, V &est) {
+    V s1, k1, s2, k2;
+    vsincos(h1, s1, k1);
+    vsincos(h2, s2, k2);
+    // 2 / (g01 g02 g12) = -2 / (ng01 g02 g12)
+    const V inv2 = vmul(vb<V>(-2.0f), vmap(vmul(vmul(ng01, g02), g12), [](float v) { return rcp_approx(v); }));
+    const V w1 = vmul(vmul(g02, s1), inv2), w2 = vmul(vmul(ng01, s2), inv2);
+    // a_m = d_m - lambda_0, b_m = d_m - lambda_2, e_m = d_m - lambda_1 (a_0 = -dl0,
+    // b_2 = -dl2, e_1 = -dl1), held as na_m = -a_m, nb_m = -b_m, ne0 = -e_0, e2n = -e_2
+    const V na1 = vsub(dl0, vb<V>(c.v1h)), na2 = vsub(dl0, vb<V>(c.v2h));
+    const V nb0 = vsub(dl2, vb<V>(c.g02)), nb1 = vsub(dl2, vb<V>(c.g12));
+    const V ne0 = vsub(dl1, vb<V>(c.g01)), e2n = vadd(vb<V>(c.g12), dl1);
+    // root 1 (j, k = 0, 2): p_m = a_m b_m;  root 2 (j, k = 0, 1): q_m = a_m e_m
+    const V p0 = vmul(dl0, nb0), p1 = vmul(na1, nb1), p2 = vmul(na2, dl2);
+    const V q0 = vmul(dl0, ne0), q1 = vmul(na1, dl1), q2 = vmul(na2, e2n);
+    V T1, T2;  // lane-wise: the absolute values fold into the scalar adds
+#pragma unroll
+    for (int i = 0; i < Lanes<V>::n; ++i) {
+        using L = Lanes<V>;
+        L::set(T1, i, __fadd_rn(__fadd_rn(fabsf(L::get(p0, i)), fabsf(L::get(p1, i))), fabsf(L::get(p2, i))));
+        L::set(T2, i, __fadd_rn(__fadd_rn(fabsf(L::get(q0, i)), fabsf(L::get(q1, i))), fabsf(L::get(q2, i))));
+    }
+    if (REAL) {
+        const V u1 = vmul(vfma(p0, vb<V>(h.X0r), vfma(p1, vb<V>(h.X1r), vmul(p2, vb<V>(h.X2r)))), w1);
+        const V u2 = vmul(vfma(q0, vb<V>(h.X0r), vfma(q1, vb<V>(h.X1r), vmul(q2, vb<V>(h.X2r)))), w2);
+#pragma unroll
+        for (int i = 0; i < Lanes<V>::n; ++i) {
+            using L = Lanes<V>;
+            L::set(est, i, __fmaf_rn(L::get(T1, i), fabsf(L::get(w1, i)),
+                                     __fmul_rn(L::get(T2, i), fabsf(L::get(w2, i)))));
+        }
+        // S = 1 + sum_l u_l (s_l + i k_l)
+        const V Sr = vfma(u1, s1, vfma(u2, s2, vb<V>(1.0f)));
+        const V Si = vfma(u1, k1, vmul(u2, k2));
+        return vfma(Sr, Sr, vmul(Si, Si));
+    } else {
+        const V AZi = vmul(A, vb<V>(h.Zi));
+        const V t1 = vmul(A, vfma(vb<V>(h.ee), vsub(dl1, vb<V>(c.sd02)), vb<V>(h.Zr)));
+        const V t2 = vmul(A, vfma(vb<V>(h.ee), vsub(dl2, vb<V>(c.sd01)), vb<V>(h.Zr)));
+        const V n1r = vfma(p0, vb<V>(h.X0r), vfma(p1, vb<V>(h.X1r), vfma(p2, vb<V>(h.X2r), t1)));
+        const V n1i = vfma(p0, vb<V>(h.X0i), vfma(p1, vb<V>(h.X1i), vfma(p2, vb<V>(h.X2i), AZi)));
+        const V n2r = vfma(q0, vb<V>(h.X0r), vfma(q1, vb<V>(h.X1r), vfma(q2, vb<V>(h.X2r), t2)));
+        const V n2i = vfma(q0, vb<V>(h.X0i), vfma(q1, vb<V>(h.X1i), vfma(q2, vb<V>(h.X2i), AZi)));
+        const V u1 = vmul(n1r, w1), v1 = vmul(n1i, w1), u2 = vmul(n2r, w2), v2 = vmul(n2i, w2);
+#pragma unroll
+        for (int i = 0; i < Lanes<V>::n; ++i) {
+            using L = Lanes<V>;
+            const float aA = fabsf(L::get(A, i));
+            const float T1a = __fmaf_rn(
+                aA, __fmaf_rn(h.ee, __fadd_rn(fabsf(L::get(dl1, i)), fabsf(c.sd02)), h.zm), L::get(T1, i));
+            const float T2a = __fmaf_rn(
+                aA, __fmaf_rn(h.ee, __fadd_rn(fabsf(L::get(dl2, i)), fabsf(c.sd01)), h.zm), L::get(T2, i));
+            L::set(est, i, __fmaf_rn(T1a, fabsf(L::get(w1, i)), __fmul_rn(T2a, fabsf(L::get(w2, i)))));
+        }
+        // S = delta_ba + sum_l (u_l + i v_l)(s_l + i k_l)
+        const V nv1 = vmul(v1, vb<V>(-1.0f)), nv2 = vmul(v2, vb<V>(-1.0f));
+        const V Sr = vfma(u1, s1, vfma(nv1, k1, vfma(u2, s2, vfma(nv2, k2, vb<V>(h.diag)))));
+        const V Si = vfma(u1, k1, vfma(v1, s1, vfma(u2, k2, vmul(v2, s2))));
+        return vfma(Sr, Sr, vmul(Si, Si));
+    }
+}
+// The same amplitude for one event from g01 (the FP64-eigenvalue variant's FP32 part).
 template <bool REAL>
 __device__ __forceinline__ float amplitude_mass32(const Pt32 &c, const Ch32 &h, float A, float dl0, float dl1,
                                                   float dl2, float g01, float g02, float g12, float h1, float h2,
                                                   float &est) {
-    float s1, k1, s2, k2;
-    __sincosf(h1, &s1, &k1);
-    __sincosf(h2, &s2, &k2);
-    const float inv2 = 2.0f * rcp_approx(g01 * g02 * g12);
-    const float w1 = (g02 * s1) * inv2, w2 = (g01 * s2) * -inv2;
-    // a_m = d_m - lambda_0, b_m = d_m - lambda_2, e_m = d_m - lambda_1 (a_0 = -dl0, b_2 = -dl2, e_1 = -dl1)
-    const float a1 = c.v1h - dl0, a2 = c.v2h - dl0;
-    const float b0 = c.g02 - dl2, b1 = c.g12 - dl2;
-    const float e0 = c.g01 - dl1, e2n = c.g12 + dl1;  // e_2 = -e2n
-    // root 1 (j, k = 0, 2): p_m = a_m b_m;  root 2 (j, k = 0, 1): q_m = a_m e_m
-    const float p0 = -dl0 * b0, p1 = a1 * b1, p2 = -a2 * dl2;
-    const float q0 = -dl0 * e0, q1 = -a1 * dl1, q2 = -a2 * e2n;
-    const float T1 = fabsf(p0) + fabsf(p1) + fabsf(p2), T2 = fabsf(q0) + fabsf(q1) + fabsf(q2);
-    if (REAL) {
-        const float u1 = fmaf(p0, h.X0r, fmaf(p1, h.X1r, p2 * h.X2r)) * w1;
-        const float u2 = fmaf(q0, h.X0r, fmaf(q1, h.X1r, q2 * h.X2r)) * w2;
-        est = fmaf(T1, fabsf(w1), T2 * fabsf(w2));
-        // S = 1 + sum_l u_l (s_l + i k_l)
-        const float Sr = fmaf(u1, s1, fmaf(u2, s2, 1.0f));
-        const float Si = fmaf(u1, k1, u2 * k2);
-        return fmaf(Sr, Sr, Si * Si);
-    } else {
-        const float AZi = A * h.Zi;
-        const float t1 = A * fmaf(h.ee, dl1 - c.sd02, h.Zr), t2 = A * fmaf(h.ee, dl2 - c.sd01, h.Zr);
-        const float n1r = fmaf(p0, h.X0r, fmaf(p1, h.X1r, fmaf(p2, h.X2r, t1)));
-        const float n1i = fmaf(p0, h.X0i, fmaf(p1, h.X1i, fmaf(p2, h.X2i, AZi)));
-        const float n2r = fmaf(q0, h.X0r, fmaf(q1, h.X1r, fmaf(q2, h.X2r, t2)));
-        const float n2i = fmaf(q0, h.X0i, fmaf(q1, h.X1i, fmaf(q2, h.X2i, AZi)));
-        const float u1 = n1r * w1, v1 = n1i * w1, u2 = n2r * w2, v2 = n2i * w2;
-        const float aA = fabsf(A);
-        const float T1a = fmaf(aA, fmaf(h.ee, fabsf(dl1) + fabsf(c.sd02), h.zm), T1);
-        const float T2a = fmaf(aA, fmaf(h.ee, fabsf(dl2) + fabsf(c.sd01), h.zm), T2);
-        est = fmaf(T1a, fabsf(w1), T2a * fabsf(w2));
-        // S = delta_ba + sum_l (u_l + i v_l)(s_l + i k_l)
-        const float Sr = fmaf(u1, s1, fmaf(-v1, k1, fmaf(u2, s2, fmaf(-v2, k2, h.diag))));
-        const float Si = fmaf(u1, k1, fmaf(v1, s1, fmaf(u2, k2, v2 * s2)));
-        return fmaf(Sr, Sr, Si * Si);
-    }
+    return amplitude_bulk<REAL, float>(c, h, A, dl0, dl1, dl2, -g01, g02, g12, h1, h2, est);
 }
 
-// Matter shifts delta_l = lambda_l - d_l of the three sorted eigenvalues (FP32):
-// trigonometric seed, then one Newton step on each lower root's shifted cubic;
-// the top shift follows from the trace (sum of shifts = A).
-// SHORT: the four-term arccos seed (the single-layer FP32-bulk path, whose
-// per-event error bound guards it); the layered path keeps the eight-term one.
-template <bool SHORT = true>
-__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2, float &cth) {
-    float r, t0, t1;
-    seed_scaled32_rt<SHORT>(c, A, r, t0, t1, cth);
+// Matter shifts delta_l = lambda_l - d_l of the three sorted eigenvalues (FP32),
+// layered path: trigonometric seed with the eight-term arccos, then one Newton
+// step on each lower root's shifted cubic; the top shift follows from the trace
+// (sum of shifts = A).
+__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
+    float r, t0, t1, cth;
+    seed_scaled32_rt(c, A, r, t0, t1, cth);
     // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) - r t_l
     dl0 = shifted_newton(fmaf(-r, t0, fmaf(A, 1.0f / 3.0f, c.td0)), A, c.S0, c.PI0, c.W0, c.E0);
     dl1 = shifted_newton(fmaf(-r, t1, fmaf(A, 1.0f / 3.0f, c.td1)), A, c.S1, c.PI1, c.W1, c.E1);
     dl2 = A - dl0 - dl1;
 }
-__device__ __forceinline__ void shifts32(const Pt32 &c, float A, float &dl0, float &dl1, float &dl2) {
-    float cth;
-    shifts32<false>(c, A, dl0, dl1, dl2, cth);
+
+// The same shifts for the single-layer FP32-bulk path, one or two events: the
+// seed with the four-term arccos (the per-event error bound guards it), formed
+// from -(-p/3) = -P0 - P1 A - A^2/9 so that r enters the seeds negated, and
+// cos(theta) returned unclamped (the short arccos clamps |x| itself).
+template <class V>
+__device__ __forceinline__ void shifts_bulk(const Pt32 &c, V A, V &dl0, V &dl1, V &dl2, V &cth) {
+    const V nmp3 = vmap(vfma(vfma(A, vb<V>(-1.0f / 9.0f), vb<V>(-c.p1)), A, vb<V>(-c.p0)),
+                        [](float v) { return fminf(v, -1e-30f); });
+    const V qh = vfma(vfma(vfma(A, vb<V>(1.0f / 27.0f), vb<V>(c.q2)), A, vb<V>(c.q1)), A, vb<V>(c.q0));
+    const V ir = vmap(nmp3, [](float v) { return rsqrt_approx(-v); });
+    const V nr = vmul(nmp3, ir);  // -r
+    cth = vmul(vmul(vmul(qh, ir), ir), ir);
+    V sn, cs;
+    vsincos(acos_third_short(cth), sn, cs);
+    const V t0 = vfma(vb<V>(1.7320508075688772f), sn, cs);
+    const V t1 = vfma(vb<V>(-1.7320508075688772f), sn, cs);
+    // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) - r t_l
+    dl0 = shifted_newton(vfma(nr, t0, vfma(A, vb<V>(1.0f / 3.0f), vb<V>(c.td0))), A, c.S0, c.PI0, c.W0, c.E0);
+    dl1 = shifted_newton(vfma(nr, t1, vfma(A, vb<V>(1.0f / 3.0f), vb<V>(c.td1))), A, c.S1, c.PI1, c.W1, c.E1);
+    dl2 = vsub(vsub(A, dl0), dl1);
 }
 
-// P(alpha -> beta) for one event and one point, FP32 bulk.  A: signed matter
-// term [eV^2]; (th, tl): c_L L / (2 pi E_true) as float-float.  redo is set
-// when the result may miss the FP32 tolerance: the amplitude's error estimate
-// exceeds kFp32EstMax, or the seed's |cos theta| exceeds kFp32SeedCos.
-template <bool REAL>
-__device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl, bool &redo) {
-    float dl0, dl1, dl2, cth;
-    shifts32(c, A, dl0, dl1, dl2, cth);
+// Phase of root l relative to root 0 in revolutions (as phase_rev), from
+// ntl = -tl: with nph = -th vh, th vh - rint(th vh) = rint(nph) - nph exactly.
+template <class V>
+__device__ __forceinline__ V phase_rev_bulk(V th, V ntl, float vh, float vl, V dd) {
+    const V nph = vmul(th, vb<V>(-vh));
+    const V e1 = vfma(th, vb<V>(vh), nph);  // exact residual of the product
+    const V fr = vsub(vmap(nph, [](float v) { return rintf(v); }), nph);
+    return vadd(fr, vfma(th, dd, vfma(th, vb<V>(vl), vfma(ntl, vb<V>(-vh), e1))));
+}
+
+// P(alpha -> beta) for one point and one or two events, FP32 bulk.  A: signed
+// matter term [eV^2]; (th, -ntl): c_L L / (2 pi E_true) as float-float.  Bit i
+// of redo is set when lane i's result may miss the FP32 tolerance: the
+// amplitude's error estimate exceeds kFp32EstMax, or the seed's |cos theta|
+// exceeds kFp32SeedCos.
+template <bool REAL, class V>
+__device__ __forceinline__ V prob_bulk(const Pt32 &c, const Ch32 &h, V A, V th, V ntl, unsigned &redo) {
+    V dl0, dl1, dl2, cth;
+    shifts_bulk(c, A, dl0, dl1, dl2, cth);
     // shift differences relative to root 0, shared by the gaps and the phases
-    const float dd1 = dl1 - dl0, dd2 = dl2 - dl0;
-    const float g01 = c.g01 - dd1, g02 = c.g02 - dd2, g12 = c.g12 + (dd1 - dd2);
+    const V dd1 = vsub(dl1, dl0), dd2 = vsub(dl2, dl0);
+    const V ng01 = vsub(dd1, vb<V>(c.g01)), g02 = vsub(vb<V>(c.g02), dd2);
+    const V g12 = vadd(vb<V>(c.g12), vsub(dd1, dd2));
     // half phases relative to root 0: pi * revolutions
-    const float f1 = phase_rev(th, tl, c.v1h, c.v1l, dd1);
-    const float f2 = phase_rev(th, tl, c.v2h, c.v2l, dd2);
-    float est;
-    const float P = amplitude_mass32<REAL>(c, h, A, dl0, dl1, dl2, g01, g02, g12, 3.14159265358979323846f * f1,
-                                           3.14159265358979323846f * f2, est);
-    redo = !(est <= kFp32EstMax) || fabsf(cth) > kFp32SeedCos;
+    const V h1 = vmul(vb<V>(3.14159265358979323846f), phase_rev_bulk(th, ntl, c.v1h, c.v1l, dd1));
+    const V h2 = vmul(vb<V>(3.14159265358979323846f), phase_rev_bulk(th, ntl, c.v2h, c.v2l, dd2));
+    V est;
+    const V P = amplitude_bulk<REAL>(c, h, A, dl0, dl1, dl2, ng01, g02, g12, h1, h2, est);
+    redo = 0;
+#pragma unroll
+    for (int i = 0; i < Lanes<V>::n; ++i)
+        if (!(Lanes<V>::get(est, i) <= kFp32EstMax) || fabsf(Lanes<V>::get(cth, i)) > kFp32SeedCos) redo |= 1u << i;
     return P;
 }
+// One event, from (th, tl).
 __device__ __forceinline__ float prob_fp32(const Pt32 &c, const Ch32 &h, float A, float th, float tl, bool &redo) {
-    return h.real ? prob_fp32<true>(c, h, A, th, tl, redo) : prob_fp32<false>(c, h, A, th, tl, redo);
+    unsigned x;
+    const float P = h.real ? prob_bulk<true>(c, h, A, th, -tl, x) : prob_bulk<false>(c, h, A, th, -tl, x);
+    redo = x != 0;
+    return P;
 }
 
 // ------------------------------------------------------------------ FP64 path
