@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
         const int sh = sd.frac_bits - 150;
         const int32_t *rmap = b.row_map + wi.acc_base * kChannels;
         unsigned long long *accp = prm.acc + kDigits * wi.acc_base * (int64_t)prm.nbins;
-        RunAcc r{0ull, 0ull, -1};
+        // FP64: the 128-bit run of fx_add_pw; FP32: the 96-bit run of acc_event_f32
+        typename AccOf<F64 ? kFP64 : kFP32>::T r;
         int cur_ch = -1;
         int64_t row_off = 0;
         for (int e0 = 0; e0 < end; e0 += 32 * kBcUnroll) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kNT) k_bc_hist(const BcParams b) {
                 const int64_t ti = row_off + (keep ? __float2int_rz(u) : 0);
                 if (keep && !debug_ok(row_off >= 0 && ti < (int64_t)b.n_rows * b.t_nbins, prm.counter, kDbgRow))
                     continue;
-                if (F64) {
+                if constexpr (F64) {
                     // binning as in acc_event_f64, integer addend
                     const float x = __fmul_rn(sf, q[k].y);
                     const float tr = __fsub_rn(x, prm.lo_f);

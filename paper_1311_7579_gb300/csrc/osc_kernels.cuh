@@ -388,26 +388,6 @@ __device__ __forceinline__ void fx_add(unsigned long long &lo, unsigned long lon
                                        unsigned long long h) {
     asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
 }
-// Adds w * 2^F, truncated to an integer (bits below the fixed-point LSB 2^-F
-// dropped).  F = 62 - ceil(log2 max|w_mc|) per sample, so x = |w| 2^F < 2^63.
-// x is formed by two exact power-of-two scalings (2^(F-64), then 2^64; F - 64
-// is a normal exponent for every F in [8, 190], and subnormal w scale exactly)
-// and split into 32-bit halves with float operations, each exact: the high half
-// floor(x 2^-32) and the remainder x - 2^32 floor(x 2^-32) are floats with at
-// most 24 significant bits, and both 32-bit conversions truncate toward zero.
-// (A 64-bit float-to-integer conversion is an FP64-pipe instruction on this
-// GPU; the two 32-bit ones are not.)  sh = F - 150.
-__device__ __forceinline__ void fx_add_f32(unsigned long long &lo, unsigned long long &hi, float w, int sh) {
-    const float x = __fmul_rn(__fmul_rn(fabsf(w), __int_as_float((sh + 213) << 23)), 18446744073709551616.0f);
-    const float hf = floorf(__fmul_rn(x, 2.3283064365386963e-10f));
-    const float lf = __fmaf_rn(-hf, 4294967296.0f, x);
-    const unsigned long long v = ((unsigned long long)__float2uint_rz(hf) << 32) | __float2uint_rz(lf);
-    if (__float_as_uint(w) >> 31) {
-        asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
-    } else {
-        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
-    }
-}
 __device__ __forceinline__ void fx_add_f64(unsigned long long &lo, unsigned long long &hi, double y) {
     const double fl = floor(y);
     const long long h = __double2ll_rz(fl);
@@ -552,37 +532,105 @@ __device__ __forceinline__ void convert_bins_warp(const HistParams &prm) {
 
 // Bin one weighted event under the point's energy scale and add it to the lane's
 // run-length accumulator (flushing the previous bin when the bin changes).
+// FP64: the 128-bit value (lo, hi).
 struct RunAcc {
-    unsigned long long lo, hi;
-    int cur_b;
+    unsigned long long lo = 0, hi = 0;
+    int cur_b = -1;
 };
-// tb = sf E_reco - lo and u = tb / width (by the reciprocal width) decide the bin.
-__device__ __forceinline__ void acc_event_u(RunAcc &r, unsigned long long *accp, const HistParams &prm, float tb,
-                                            float u, float wt, int sh, bool active) {
-    if (active && tb >= 0.0f && u < prm.nb_f) {
-        const int b = __float2int_rz(u);
-        if (!debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) return;
-        if (b != r.cur_b) {
-            if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + kDigits * r.cur_b, r.lo, r.hi);
-            r.lo = r.hi = 0;
-            r.cur_b = b;
-        }
-        fx_add_f32(r.lo, r.hi, wt, sh);
+// FP32 precisions: each addend is below 2^63 and a lane's run holds fewer than
+// 2^31 events, so the run fits a 96-bit two's-complement sum a0 + a1 2^32 + a2 2^64
+// (a2 signed), three 32-bit limbs added with one carry chain.
+struct RunAcc32 {
+    unsigned a0 = 0, a1 = 0, a2 = 0;
+    int cur_b = -1;
+};
+template <int PREC>
+struct AccOf { using T = RunAcc32; };
+template <>
+struct AccOf<kFP64> { using T = RunAcc; };
+
+// The run's 128-bit value: (lo, hi) with hi the sign extension of a2.
+__device__ __forceinline__ void run_value(const RunAcc32 &r, unsigned long long &lo, unsigned long long &hi) {
+    lo = ((unsigned long long)r.a1 << 32) | r.a0;
+    hi = (unsigned long long)(long long)(int)r.a2;
+}
+__device__ __forceinline__ void run_value(const RunAcc &r, unsigned long long &lo, unsigned long long &hi) {
+    lo = r.lo;
+    hi = r.hi;
+}
+__device__ __forceinline__ void run_clear(RunAcc32 &r) { r.a0 = r.a1 = r.a2 = 0; }
+__device__ __forceinline__ void run_clear(RunAcc &r) { r.lo = r.hi = 0; }
+template <class R>
+__device__ __forceinline__ void run_flush(const R &r, unsigned long long *accp) {
+    unsigned long long lo, hi;
+    run_value(r, lo, hi);
+    if (r.cur_b >= 0 && (lo | hi)) fx_flush(accp + kDigits * r.cur_b, lo, hi);
+}
+
+// The addend of weight w: x = |w| 2^F truncated to an integer (bits below the
+// fixed-point LSB 2^-F dropped), returned as its two 32-bit halves, for one or
+// two weights.  F = 62 - ceil(log2 max|w_mc|) per sample, so x < 2^63.
+// x is formed by two exact power-of-two scalings (2^(F-64), then 2^64; F - 64
+// is a normal exponent for every F in [8, 190], and subnormal w scale exactly)
+// and split into 32-bit halves with float operations, each exact: the high half
+// floor(x 2^-32) and the remainder x - 2^32 floor(x 2^-32) are floats with at
+// most 24 significant bits, and both 32-bit conversions truncate toward zero.
+// (A 64-bit float-to-integer conversion is an FP64-pipe instruction on this
+// GPU; the two 32-bit ones are not.)  sh = F - 150.
+template <class V>
+__device__ __forceinline__ void fx_halves(V wabs, int sh, V &hf, V &lf) {
+    const V x = vmul(vmul(wabs, vb<V>(__int_as_float((sh + 213) << 23))), vb<V>(18446744073709551616.0f));
+    hf = vmap(vmul(x, vb<V>(2.3283064365386963e-10f)), [](float v) { return floorf(v); });
+    lf = vfma(hf, vb<V>(-4294967296.0f), x);
+}
+// Adds (neg ? -1 : +1) (hi 2^32 + lo) to the lane's run.
+__device__ __forceinline__ void fx_add3(RunAcc32 &r, unsigned hi, unsigned lo, bool neg) {
+    if (neg) {
+        asm("sub.cc.u32 %0, %0, %3;\n\tsubc.cc.u32 %1, %1, %4;\n\tsubc.u32 %2, %2, 0;"
+            : "+r"(r.a0), "+r"(r.a1), "+r"(r.a2)
+            : "r"(lo), "r"(hi));
+    } else {
+        asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, 0;"
+            : "+r"(r.a0), "+r"(r.a1), "+r"(r.a2)
+            : "r"(lo), "r"(hi));
     }
 }
-__device__ __forceinline__ void acc_event_f32(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
+// One event: tb = sf E_reco - lo and u = tb / width (by the reciprocal width)
+// decide the bin; (hf, lf) are its addend's halves, neg the weight's sign.  An
+// event outside the histogram (or inactive) changes nothing: it takes no bin and
+// adds zero.
+__device__ __forceinline__ void acc_event_u(RunAcc32 &r, unsigned long long *accp, const HistParams &prm, float tb,
+                                            float u, float hf, float lf, bool neg, bool in) {
+    const int b = __float2int_rz(u);
+    if (in && !debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) in = false;
+    if (in && b != r.cur_b) {
+        run_flush(r, accp);
+        run_clear(r);
+        r.cur_b = b;
+    }
+    fx_add3(r, in ? __float2uint_rz(hf) : 0u, in ? __float2uint_rz(lf) : 0u, neg);
+}
+__device__ __forceinline__ void acc_event_f32(RunAcc32 &r, unsigned long long *accp, const HistParams &prm, float sf,
                                               float er, float wt, int sh, bool active) {
     const float tb = vsub(vmul(sf, er), prm.lo_f);
-    acc_event_u(r, accp, prm, tb, vmul(tb, prm.inv_f), wt, sh, active);
+    const float u = vmul(tb, prm.inv_f);
+    const bool in = active && tb >= 0.0f && u < prm.nb_f;
+    float hf, lf;
+    fx_halves(in ? fabsf(wt) : 0.0f, sh, hf, lf);
+    acc_event_u(r, accp, prm, tb, u, hf, lf, wt < 0.0f, in);
 }
-// Two events in order (a, then b), their bin arithmetic in one packed chain:
-// the same bins and sums as two acc_event_f32 calls.
-__device__ __forceinline__ void acc_pair_f32(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
+// Two events in order (a, then b), their bin and addend arithmetic in one packed
+// chain: the same bins and sums as two acc_event_f32 calls.
+__device__ __forceinline__ void acc_pair_f32(RunAcc32 &r, unsigned long long *accp, const HistParams &prm, float sf,
                                              float2 er, float2 wt, int sh, bool act_a, bool act_b) {
     const float2 tb = vsub(vmul(vb<float2>(sf), er), vb<float2>(prm.lo_f));
     const float2 u = vmul(tb, vb<float2>(prm.inv_f));
-    acc_event_u(r, accp, prm, tb.x, u.x, wt.x, sh, act_a);
-    acc_event_u(r, accp, prm, tb.y, u.y, wt.y, sh, act_b);
+    const bool in_a = act_a && tb.x >= 0.0f && u.x < prm.nb_f;
+    const bool in_b = act_b && tb.y >= 0.0f && u.y < prm.nb_f;
+    float2 hf, lf;
+    fx_halves(make_float2(in_a ? fabsf(wt.x) : 0.0f, in_b ? fabsf(wt.y) : 0.0f), sh, hf, lf);
+    acc_event_u(r, accp, prm, tb.x, u.x, hf.x, lf.x, wt.x < 0.0f, in_a);
+    acc_event_u(r, accp, prm, tb.y, u.y, hf.y, lf.y, wt.y < 0.0f, in_b);
 }
 __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
                                               float er, double wt, double hs, bool active) {
@@ -600,16 +648,20 @@ __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *acc
         fx_add_f64(r.lo, r.hi, wt * hs);
     }
 }
-__device__ __forceinline__ void acc_finish(RunAcc &r, unsigned long long *accp) {
-    if (r.cur_b >= 0 && (r.lo | r.hi)) fx_flush(accp + kDigits * r.cur_b, r.lo, r.hi);
+template <class R>
+__device__ __forceinline__ void acc_finish(R &r, unsigned long long *accp) {
+    run_flush(r, accp);
 }
 // End of a per-warp work item: lanes that end in the same bin (the lanes hold
 // consecutive sorted events, so such lanes are normally contiguous) first sum
 // their 128-bit values with shuffles, exactly, and one lane flushes the total.
-__device__ __forceinline__ void acc_finish_warp(RunAcc &r, unsigned long long *accp) {
+template <class R>
+__device__ __forceinline__ void acc_finish_warp(R &r, unsigned long long *accp) {
     __syncwarp();
     const int lane = threadIdx.x & 31;
-    const bool has = r.cur_b >= 0 && (r.lo | r.hi);
+    unsigned long long lo, hi;
+    run_value(r, lo, hi);
+    const bool has = r.cur_b >= 0 && (lo | hi);
     const int key = has ? r.cur_b : -1 - lane;
     const unsigned mask = __match_any_sync(0xffffffffu, key);
     const int first = __ffs(mask) - 1;
@@ -620,7 +672,6 @@ __device__ __forceinline__ void acc_finish_warp(RunAcc &r, unsigned long long *a
         return;
     }
     const int end = first + cnt;
-    unsigned long long lo = r.lo, hi = r.hi;
     for (int d = 1; d < 32; d <<= 1) {
         const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, d);
         const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, d);
@@ -804,10 +855,10 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             }
         }
         unsigned long long *accp = prm.acc + kDigits * wi.acc_base * (int64_t)prm.nbins;
-        RunAcc r{0ull, 0ull, -1};
+        typename AccOf<PREC>::T r;
         bool redo = false;  // an event of this item is left to the FP64 recomputation (k_redo)
         int e = lane;
-        if (PREC == kFP32) {
+        if constexpr (PREC == kFP32) {
             const int sh = sd.frac_bits - 150;
             for (; e < end; e += 64) {
                 const bool has_b = e + 32 < end;
@@ -854,7 +905,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 Ea = Ena; ra = rna; wa = wna; ca = cna;
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
             }
-        } else if (PREC == kMix) {
+        } else if constexpr (PREC == kMix) {
             const int sh = sd.frac_bits - 150;
             for (; e < end; e += 64) {
                 const bool has_b = e + 32 < end;
@@ -919,7 +970,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
                 Eb = Enb; rb = rnb; wb = wnb; cb = cnb;
             }
         }
-        if (PREC != kFP64) {
+        if constexpr (PREC != kFP64) {
             // mark the item for the FP64 recomputation of its left-out events
             const bool any = __any_sync(0xffffffffu, redo);
             if (any && lane == 0) {
@@ -996,10 +1047,10 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
             const bool active = lp < wi.n_pts;
             const int pidx = wi.point_base + (active ? lp : wi.n_pts - 1);
             unsigned long long *accp = prm.acc + kDigits * (wi.acc_base + lp) * (int64_t)prm.nbins;
-            RunAcc r{0ull, 0ull, -1};
+            typename AccOf<PREC>::T r;
             int cur_ch = -1;
             bool redo = false;  // an event of this item is left to the FP64 recomputation (k_redo)
-            if (PREC == kFP32) {
+            if constexpr (PREC == kFP32) {
                 const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
                 Pt32 c;
                 load_pt32(pc, c);
@@ -1048,7 +1099,7 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
                         }
                     }
                 }
-            } else if (PREC == kMix) {
+            } else if constexpr (PREC == kMix) {
                 const float *pc = prm.pc32 + (int64_t)pidx * C32_STRIDE;
                 Pt32 c;
                 load_pt32(pc, c);
@@ -1101,7 +1152,7 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
                     }
                 }
             }
-            if (PREC != kFP64) {
+            if constexpr (PREC != kFP64) {
                 // mark the item for the FP64 recomputation of its left-out events
                 if (__syncthreads_or(redo) && tid == 0) {
                     prm.redo[it] = 1;
@@ -1153,7 +1204,7 @@ __global__ void __launch_bounds__(kNT) k_redo(const HistParams prm) {
                 if (PREC == kMix) load_pt64(pc64, c64);
                 const float sf = pc32[C32_ESCALE];
                 unsigned long long *accp = prm.acc + kDigits * (wi.acc_base + q) * (int64_t)prm.nbins;
-                RunAcc r{0ull, 0ull, -1};
+                RunAcc32 r;
                 Ch32 h;
                 int cur_ch = -1;
                 for (int e = lane; e < wi.ev_count; e += 32) {

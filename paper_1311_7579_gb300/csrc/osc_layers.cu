@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kNT) k_hist_layers(const HistParams prm) {
         unsigned long long *accp = prm.acc + kDigits * wi.acc_base * (int64_t)prm.nbins;
         const int sh = sd.frac_bits - 150;
         const double hs = sd.hscale_d;
-        RunAcc r{0ull, 0ull, -1};
+        typename AccOf<PREC>::T r;
         const float4 *ev = sd.ev + wi.ev_begin;
         const bool valid = debug_ok(wi.ev_begin >= 0 && wi.ev_count >= 0 && wi.ev_begin + wi.ev_count <= sd.n,
                                     prm.counter, kDbgItem) &&
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kNT) k_hist_layers(const HistParams prm) {
                 else
                     load_layu(lp.lu32, nb, u32);
             }
-            if (PREC == kFP64) {
+            if constexpr (PREC == kFP64) {
                 const double P = prob_layers64(lp.c64, lp.d64, u64, sd, ch, q.x);
                 acc_event_f64(r, accp, prm, lp.sf, q.y, P * (double)q.z, hs, true);
             } else {

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
         if (it >= p.n_items) return;
         const int64_t beg = (int64_t)it * p.chunk;
         const int64_t end = min(p.n, beg + p.chunk);
-        RunAcc r{0ull, 0ull, -1};
+        typename AccOf<PREC>::T r;
         int cur_ch = -1;
         Pt32 c32;
         Ch32 h32;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kNT, 1) k_noalloc_hist(const NoAllocParams p) 
                 continue;
             }
             const int ch = chan_id(a, b, nb);
-            if (PREC != kFP64) {
+            if constexpr (PREC != kFP64) {
                 if (ch != cur_ch) {
                     cur_ch = ch;
                     load_ch32(s->pc32, ch, h32);
