@@ -181,6 +181,15 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return r;
 }
 
+// g and g' of the shifted cubic at dl, for a Newton step (see shifted_newton).
+template <class V>
+__device__ __forceinline__ void newton_terms(V dl, V A, float S, float PI, float W, float E, V &g, V &gp) {
+    const V b = vsub(vb<V>(S), A);
+    const V c = vfma(A, vb<V>(-W), vb<V>(PI));
+    const V t = vfma(vadd(dl, b), dl, c);
+    g = vfma(t, dl, vmul(A, vb<V>(-E)));
+    gp = vfma(dl, vfma(vb<V>(2.0f), dl, b), t);
+}
 template <class V>
 __device__ __forceinline__ V shifted_newton(V dl, V A, float S, float PI, float W, float E) {
     // one Newton step on g(delta) = delta^3 + b delta^2 + c delta - e, with
@@ -411,8 +420,18 @@ __device__ __forceinline__ void shifts_bulk(const Pt32 &c, V A, V &dl0, V &dl1, 
     const V t0 = vfma(vb<V>(1.7320508075688772f), sn, cs);
     const V t1 = vfma(vb<V>(-1.7320508075688772f), sn, cs);
     // seeds delta_l = (T0 + A) / 3 + m_l - d_l = (A / 3 + (T0 / 3 - d_l)) - r t_l
-    dl0 = shifted_newton(vfma(nr, t0, vfma(A, vb<V>(1.0f / 3.0f), vb<V>(c.td0))), A, c.S0, c.PI0, c.W0, c.E0);
-    dl1 = shifted_newton(vfma(nr, t1, vfma(A, vb<V>(1.0f / 3.0f), vb<V>(c.td1))), A, c.S1, c.PI1, c.W1, c.E1);
+    const V s0 = vfma(nr, t0, vfma(A, vb<V>(1.0f / 3.0f), vb<V>(c.td0)));
+    const V s1 = vfma(nr, t1, vfma(A, vb<V>(1.0f / 3.0f), vb<V>(c.td1)));
+    // one Newton step on each lower root's shifted cubic (as shifted_newton), the
+    // two reciprocals -1/g'_0 = g'_1 q and -1/g'_1 = g'_0 q from one approximate
+    // q = -1 / (g'_0 g'_1): one reciprocal instead of two (a few ulp; the step's
+    // correction needs far less)
+    V g0, gp0, g1, gp1;
+    newton_terms(s0, A, c.S0, c.PI0, c.W0, c.E0, g0, gp0);
+    newton_terms(s1, A, c.S1, c.PI1, c.W1, c.E1, g1, gp1);
+    const V q = vmap(vmul(gp0, gp1), [](float v) { return rcp_approx(-v); });
+    dl0 = vfma(g0, vmul(gp1, q), s0);
+    dl1 = vfma(g1, vmul(gp0, q), s1);
     dl2 = vsub(vsub(A, dl0), dl1);
 }
 
