@@ -50,15 +50,17 @@ FLUSH_BYTES = 256 << 20
 #  * The kernel's own arithmetic, counted from osc_math.cuh / osc_kernels.cuh
 #    (FMA = 2, add/mul = 1; conversions, comparisons, selects and integer work not
 #    counted) for the mu -> mu / tau -> tau channels, 90 % of the workload: event
-#    terms 11, matter shifts 74 (seed 36, seeds 6, two Newton steps 30, trace 2),
-#    gaps and phases 28, amplitude in the mass basis with its error bound 48,
-#    weight and bin 4 -- 165 flops; the other channels add the matter and
-#    electron terms, about 185.  SFU: 12 (1/E, the seed's rsqrt, sqrt and
-#    sin/cos, two Newton reciprocals, two sin/cos of half phases, 1/D).
+#    terms 11, matter shifts 70 (seed 27, seeds 8, two Newton steps with one shared
+#    reciprocal 33, trace 2), gaps and phases 30, amplitude in the mass
+#    basis with its error bound 48, weight and bin 4 -- 163 flops; the other
+#    channels add the matter and electron terms, about 185.  SFU: 11 (1/E, the
+#    seed's rsqrt, sqrt and sin/cos, the Newton steps' shared reciprocal, two
+#    sin/cos of half phases, 1/D).  On this GPU the FP32 adds, multiplies and FMAs
+#    of an event pair issue as packed pairs (add/mul/fma.f32x2).
 ALG_OPS_PER_EVPT = 95
 ALG_SFU_PER_EVPT = 6
-FP32_FLOP_PER_EVPT = 165
-SFU_PER_EVPT = 12
+FP32_FLOP_PER_EVPT = 163
+SFU_PER_EVPT = 11
 ALG_BYTES_PER_EVENT = 13  # E_true, E_reco, w_mc (FP32) and the channel byte
 
 

@@ -20,7 +20,10 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libosc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
+# host code: no floating-point contraction (the host's copy of the per-point
+# constants must round exactly as the device's explicit operations do)
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                "-Xcompiler", "-ffp-contract=off",
                 "-I" + os.path.join(ROOT, "include")]
 
 

@@ -52,9 +52,11 @@ __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddep
 struct cplx64 {
     double re, im;
 };
-// The constants are written with explicit fma wherever a product is added, so
-// that every kernel inlining them (the constants kernels, the allocation-free
-// call) rounds identically and gives bitwise the same constants.
+// The constants are written with explicit fma wherever a product is added (and
+// explicit adds where no product may be fused), so that every kernel inlining
+// them (the constants kernels, the allocation-free call) and the host's copy of
+// the computation (host_point_consts) round identically and give bitwise the
+// same constants.
 __device__ __forceinline__ cplx64 cmul_conj(cplx64 a, double m, cplx64 b) {
     // a * m * conj(b)
     return {m * fma(a.re, b.re, a.im * b.im), m * fma(a.im, b.re, -(a.re * b.im))};
@@ -193,7 +195,8 @@ __device__ inline void point_consts_block(const osc_point &P, float *c32, double
             cplx64 h = {0, 0}, h2 = {0, 0};
             for (int k = 1; k < 3; ++k) {
                 const cplx64 q = cmul_conj(Us[3 * b + k], m[k], Us[3 * a + k]);
-                h.re += q.re; h.im += q.im;
+                h.re = __dadd_rn(h.re, q.re);  // an explicit add: no product is fused into it
+                h.im = __dadd_rn(h.im, q.im);
                 h2.re = fma(q.re, m[k], h2.re); h2.im = fma(q.im, m[k], h2.im);
             }
             Hs[0][lane] = h.re; Hs[1][lane] = h.im; Hs[2][lane] = h2.re; Hs[3][lane] = h2.im;
@@ -477,7 +480,28 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
 
 // Per-warp variant for one-point items: warps that finish early exit without
 // waiting at a block barrier; the last warp converts four bins per lane per round.
-__device__ __forceinline__ void convert_bins_warp(const HistParams &prm);
+// The histogram metadata (scales, point index) of the first conversion round's
+// bins, four per lane: written by the host before any launch, so it can be read
+// before a kernel's grid-dependency wait.
+struct FinMeta {
+    double m0[4], m1[4], pt[4];
+};
+__device__ __forceinline__ void fin_meta_load(const HistParams &prm, FinMeta &fm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = lane + 32 * k;
+        fm.m0[k] = fm.m1[k] = fm.pt[k] = 0.0;
+        if (i < n) {
+            const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
+            fm.m0[k] = m[0];
+            fm.m1[k] = m[1];
+            fm.pt[k] = m[3];
+        }
+    }
+}
+__device__ __forceinline__ void convert_bins_warp(const HistParams &prm, const FinMeta *pre = nullptr);
 __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     const int lane = threadIdx.x & 31;
     __threadfence();
@@ -491,13 +515,14 @@ __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
 }
 // The last warp's conversion of the fused finalize (four bins per lane per round,
 // all loads of a round issued before any conversion), then the counter reset.
-__device__ __forceinline__ void convert_bins_warp(const HistParams &prm) {
+__device__ __forceinline__ void convert_bins_warp(const HistParams &prm, const FinMeta *pre) {
     const int lane = threadIdx.x & 31;
     constexpr int kU = 4;
     const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
     for (int64_t i0 = 0; i0 < n; i0 += 32 * kU) {
         Digits d[kU];
         double m0[kU], m1[kU], nm[kU];
+        const bool have = pre && i0 == 0;  // the first round's metadata loaded ahead
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
             const int64_t i = i0 + lane + 32 * k;
@@ -506,10 +531,16 @@ __device__ __forceinline__ void convert_bins_warp(const HistParams &prm) {
             m0[k] = m1[k] = nm[k] = 0.0;
             if (i < n) {
                 d[k] = load_digits(prm.acc, i);
-                const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
-                m0[k] = m[0];
-                m1[k] = m[1];
-                nm[k] = m[3];
+                if (have) {
+                    m0[k] = pre->m0[k];
+                    m1[k] = pre->m1[k];
+                    nm[k] = pre->pt[k];
+                } else {
+                    const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
+                    m0[k] = m[0];
+                    m1[k] = m[1];
+                    nm[k] = m[3];
+                }
             }
         }
 #pragma unroll
@@ -785,8 +816,10 @@ __device__ __forceinline__ void stage_tile(typename StageOf<PREC>::T &s, const S
 // the next two prefetched into registers.  The ticket of the warp's next item is
 // fetched a whole item ahead, and the sample scalars and point constants are
 // reloaded only when the item's sample or point changes.
+// pc_inline (FP32 bulk, one point): the point's FP32 constants, read in place
+// (a kernel parameter) instead of from the constants table.
 template <int PREC>
-__device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
+__device__ __forceinline__ void hist_items_per_warp(const HistParams &prm, const float *pc_inline = nullptr) {
     const int lane = threadIdx.x & 31;
     const int n_warps = (int)(gridDim.x * (blockDim.x >> 5));
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
@@ -844,7 +877,7 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm) {
             cur_point = wi.point_base;
             cur_ch = -1;
             if (PREC != kFP64) {
-                pc32 = prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
+                pc32 = pc_inline ? pc_inline : prm.pc32 + (int64_t)wi.point_base * C32_STRIDE;
                 load_pt32(pc32, c32);
                 sf = pc32[C32_ESCALE];
             }
@@ -1176,14 +1209,28 @@ __global__ void __launch_bounds__((hist_block_threads<PREC, PT>()), (hist_min_bl
 // do not depend on which kernel added which event.  Its last warp converts the
 // bins when the histogram kernel left its fused finalize to it, and resets the
 // counters.  The FP64 arithmetic sits here, out of the FP32 kernels' main loops.
+// The FP32-bulk one-point histogram kernel of a fit step whose point's constants
+// come by value (computed on the host, host_point_consts): no constants kernel
+// runs before it.  Block 0 also stores them in row 0 of the constants tables,
+// which the FP64 recomputation pass and the finalize read after this grid (and
+// later calls find there, as after the constants kernel).
+struct PointInline {
+    float c32[C32_STRIDE];
+    double c64[C64_STRIDE];
+};
 template <int PREC>
 __global__ void __launch_bounds__(kNT) k_redo(const HistParams prm) {
     grid_dependents_launch();  // a finalize kernel after this one may become resident early
+    // the converting warp reads the histograms' metadata before the wait, so that
+    // after it one round of loads (the digit columns and the norms) remains
+    FinMeta fm;
+    const bool conv = prm.fuse_final && blockIdx.x == 0 && threadIdx.x < 32;
+    if (conv) fin_meta_load(prm, fm);
     grid_dependency_wait();
     if (__ldcg(prm.counter + kRedoCount) == 0) {
         // nothing to recompute: one warp does the fused finalize the histogram
         // kernel left to this kernel (and resets the work counters)
-        if (prm.fuse_final && blockIdx.x == 0 && threadIdx.x < 32) convert_bins_warp(prm);
+        if (conv) convert_bins_warp(prm, &fm);
         return;
     }
     const int lane = threadIdx.x & 31;

@@ -4,6 +4,20 @@
 
 namespace osc {
 
+// With its constants read in place rather than held in registers it fits five
+// 128-thread blocks per SM (20 warps) without spilling, where k_hist<FP32, 1> fits four.
+constexpr int kInlineMinBlocks = 5;
+__global__ void __launch_bounds__((hist_block_threads<kFP32, 1>()), kInlineMinBlocks)
+    k_hist_inline(const HistParams prm, const __grid_constant__ PointInline pin) {
+    grid_dependents_launch();
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < C32_STRIDE; i += blockDim.x) const_cast<float *>(prm.pc32)[i] = pin.c32[i];
+        for (int i = threadIdx.x; i < C64_STRIDE; i += blockDim.x) const_cast<double *>(prm.pc64)[i] = pin.c64[i];
+    }
+    hist_items_per_warp<kFP32>(prm, pin.c32);
+    if (prm.fuse_final && !prm.redo) fused_final_warp(prm);
+}
+
 const void *hist_kernel_fn_fp32(int pt) {
     switch (pt) {
         case 1: return (const void *)k_hist<kFP32, 1>;
@@ -35,5 +49,17 @@ cudaError_t launch_reweight_fp32(const ReweightParams &p, cudaStream_t st) {
 }
 
 const void *redo_kernel_fn_fp32() { return (const void *)k_redo<kFP32>; }
+
+const void *hist_inline_kernel_fn() { return (const void *)k_hist_inline; }
+size_t point_inline_bytes() { return sizeof(PointInline); }
+int hist_inline_blocks_per_sm() {
+    static int per_sm = 0;  // the same on every device of a process (one GPU model)
+    if (!per_sm) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hist_inline, hist_block_threads<kFP32, 1>(), 0);
+        per_sm = n > 0 ? n : 1;
+    }
+    return per_sm;
+}
 
 }  // namespace osc

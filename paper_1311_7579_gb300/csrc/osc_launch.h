@@ -54,6 +54,15 @@ cudaError_t launch_from_digits(const unsigned long long *digits, const double *h
 // function) and its block size.
 const void *point_consts_one_fn();
 int point_consts_threads();
+// The FP32-bulk one-point histogram kernel of a fit step with the point's
+// constants by value (kernel parameters: HistParams, then the C32_STRIDE floats
+// and C64_STRIDE doubles of host_point_consts), and that second parameter's size.
+const void *hist_inline_kernel_fn();
+size_t point_inline_bytes();
+int hist_inline_blocks_per_sm();
+// The constants of one point computed on the host, bitwise those of the
+// constants kernel (the FP32 and FP64 rows of the constants tables).
+void host_point_consts(const osc_point &P, float *c32, double *c64);
 // Streaming multiprocessors of the current device (queried once per device).
 int device_sms();
 

@@ -1083,7 +1083,9 @@ static osc_status run_plan(osc_ctx *ctx, Plan *p, double lo, double hi, double *
 
 
 // One fit step (osc_histogram_point) as a CUDA graph: the constants kernel of
-// the step's point, then the histogram kernel, the FP64 recomputation pass
+// the step's point (for FP32 bulk at one point through constant density, the
+// constants computed on the host and passed by value to the histogram kernel
+// instead), then the histogram kernel, the FP64 recomputation pass
 // (FP32 precisions; it returns at once when no event was left out) and the
 // finalize kernel (larger outputs), each joined to the one before by a
 // programmatic edge, so that a kernel starts while the one before still runs and
@@ -1113,15 +1115,26 @@ static osc_status run_step_graph(osc_ctx *ctx, Plan *p, const osc_point &pt, dou
     void *cargs[] = {&pv, &pc32, &pc64};
     void *hargs[] = {&hp};
     void *fargs[] = {&fp};
+    // FP32 bulk, one point, constant density: the constants are computed here and
+    // passed by value to the histogram kernel (no constants kernel in the graph)
+    const bool inl = p->prec == kFP32 && p->pt == 1 && p->kind == kEventByEvent;
+    std::vector<unsigned char> pin;
+    void *iargs[] = {&hp, nullptr};
+    if (inl) {
+        pin.resize(point_inline_bytes());
+        host_point_consts(pt, reinterpret_cast<float *>(pin.data()),
+                          reinterpret_cast<double *>(pin.data() + sizeof(float) * C32_STRIDE));
+        iargs[1] = pin.data();
+    }
     cudaKernelNodeParams kc{}, kh{}, kr{}, kf{};
     kc.func = (void *)point_consts_one_fn();
     kc.gridDim = dim3(1);
     kc.blockDim = dim3(point_consts_threads());
     kc.kernelParams = cargs;
-    kh.func = (void *)plan_kernel(p);
-    kh.gridDim = dim3(p->grid);
+    kh.func = inl ? (void *)hist_inline_kernel_fn() : (void *)plan_kernel(p);
+    kh.gridDim = dim3(inl ? ctx->n_sm * hist_inline_blocks_per_sm() : p->grid);
     kh.blockDim = dim3(plan_threads(p));
-    kh.kernelParams = hargs;
+    kh.kernelParams = inl ? iargs : hargs;
     if (p->step_exec && p->step_fused != fused) {
         cudaGraphExecDestroy(p->step_exec);
         cudaGraphDestroy(p->step_graph);
@@ -1144,9 +1157,11 @@ static osc_status run_step_graph(osc_ctx *ctx, Plan *p, const osc_point &pt, dou
         ed.from_port = cudaGraphKernelNodePortProgrammatic;
         ed.type = cudaGraphDependencyTypeProgrammatic;
         const cudaGraphEdgeData *edge = p->kind == kEventByEvent ? &ed : nullptr;
-        CK(cudaGraphAddKernelNode(&p->s_const, p->step_graph, nullptr, 0, &kc));
         CK(cudaGraphAddKernelNode(&p->s_hist, p->step_graph, nullptr, 0, &kh));
-        CK(cudaGraphAddDependencies(p->step_graph, &p->s_const, &p->s_hist, edge, 1));
+        if (!inl) {
+            CK(cudaGraphAddKernelNode(&p->s_const, p->step_graph, nullptr, 0, &kc));
+            CK(cudaGraphAddDependencies(p->step_graph, &p->s_const, &p->s_hist, edge, 1));
+        }
         cudaGraphNode_t prev = p->s_hist;
         if (p->d_redo) {
             CK(cudaGraphAddKernelNode(&p->s_redo, p->step_graph, nullptr, 0, &kr));
@@ -1160,13 +1175,13 @@ static osc_status run_step_graph(osc_ctx *ctx, Plan *p, const osc_point &pt, dou
         CK(cudaGraphInstantiate(&p->step_exec, p->step_graph, 0));
         p->step_fused = fused;
     } else {
-        CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_const, &kc));
+        if (!inl) CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_const, &kc));
         CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_hist, &kh));
         if (p->d_redo) CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_redo, &kr));
         if (!fused) CK(cudaGraphExecKernelNodeSetParams(p->step_exec, p->s_final, &kf));
     }
     CK(cudaGraphLaunch(p->step_exec, ctx->stream));
-    ctx->launches += 2 + (p->d_redo ? 1 : 0) + (fused ? 0 : 1);
+    ctx->launches += (inl ? 1 : 2) + (p->d_redo ? 1 : 0) + (fused ? 0 : 1);
     return OSC_OK;
 }
 
@@ -1196,7 +1211,7 @@ static osc_status time_shape(osc_ctx *ctx, const std::vector<int32_t> &ids, int3
 // osc_histogram, and (digits != null) osc_histogram_digits: the same call with
 // the bins' digit columns as its output instead of doubles.
 // step_pt (osc_histogram_point): the table holds that one point, whose constants
-// the step's CUDA graph computes as its first kernel.
+// the step's CUDA graph computes as its first kernel (or takes by value).
 static osc_status histogram_impl(osc_ctx *ctx, const int32_t *sample_ids, int32_t n_samples, int32_t point_begin,
                                  int32_t n_points, osc_precision prec, double lo, double hi, int32_t nbins,
                                  double *out, uint64_t *digits, int out_on_device, const osc_point *step_pt = nullptr) {

@@ -368,13 +368,46 @@ def test_histogram_point_is_set_params_plus_histogram(ctx):
         api.osc_unload_sample(ctx, sid)
 
 
+def test_fit_step_constants_are_the_constants_kernels(ctx):
+    """The FP32-bulk fit step computes its point's constants on the host, passes
+    them by value to its histogram kernel and stores them in row 0 of the
+    constants tables; they must be bitwise the constants kernel's.  After
+    osc_histogram_point(pt) the per-event probabilities of every precision (which
+    read the stored row) equal those after osc_set_params([pt]), bit for bit,
+    through constant density and through layers, for points across the accepted
+    domain: both mass orderings, near-extreme mixing, tiny and large splittings,
+    |delta| up to 1e3; and the fit step's bins equal osc_histogram's."""
+    s = synth.all_channel_sample(3000, seed=61, L_km=810.0, rho=2.8)
+    sl = synth.all_channel_sample(2000, seed=64, L_km=1300.0)
+    sid, lid = api.osc_load_sample(ctx, s), api.osc_load_sample(ctx, sl)
+    api.osc_set_layers(ctx, lid, [(300.0, 2.2, 0.5), (700.0, 4.5, 0.49), (300.0, 1.0, 0.47)])
+    edge = np.array([[0.311, 0.0251, 0.5, 7.6e-5, 2.4e-3, 0.0, 1.0, 1.0],
+                     [0.02, 0.001, 0.98, 1.0e-6, -2.0e-3, -1000.0, 1.1, 0.5],
+                     [0.97, 0.2, 0.03, 3.0e-4, 3.5e-3, 987.654321, 0.95, 2.0],
+                     [0.5, 0.5, 0.5, 2.0e-5, -1.0e-2, 3.14159, 1.0, -1.0]])
+    pts = np.concatenate([synth.scan_points(12, seed=63), edge])
+    for k, pt in enumerate(pts):
+        h = api.osc_histogram_point(ctx, [sid], pt, "fp32", LO, HI, NB)
+        step = {(q, prec): _gpu_probs(ctx, q, 0, prec, n)[0]
+                for q, n in ((sid, s["n"]), (lid, sl["n"])) for prec in ("fp32", "fp64", "fp32_f64eig")}
+        api.osc_set_params(ctx, pt[None, :])
+        assert np.array_equal(h, api.osc_histogram(ctx, [sid], 0, 1, "fp32", LO, HI, NB)), k
+        for (q, prec), p in step.items():
+            n = s["n"] if q == sid else sl["n"]
+            assert np.array_equal(p, _gpu_probs(ctx, q, 0, prec, n)[0]), (k, q, prec)
+    for q in (sid, lid):
+        api.osc_unload_sample(ctx, q)
+
+
 def test_histogram_point_graph_step_separate_finalize_and_layers(ctx):
     """osc_histogram_point runs the fit step as one CUDA graph (constants,
     histogram, FP64 recomputation pass, finalize, joined by programmatic edges)
     replayed with its parameters refreshed: the bins equal set_params +
     osc_histogram bitwise for a separate finalize kernel (600 bins), a layered
     sample (completion edges) and points alternating between calls; the graph
-    launches the same kernels the two calls do."""
+    launches the kernels the two calls do, less the constants kernel where the
+    step passes host-computed constants by value (FP32 bulk through constant
+    density)."""
     s1 = synth.table1_sample(30000, seed=24)
     s2 = synth.all_channel_sample(12000, seed=25, L_km=810.0, rho=2.8)
     ids = [api.osc_load_sample(ctx, s1), api.osc_load_sample(ctx, s2)]
@@ -394,7 +427,8 @@ def test_histogram_point_graph_step_separate_finalize_and_layers(ctx):
                     got = api.osc_histogram_point(ctx, group, pts[k], prec, LO, HI, nb)
                     n2 = api.osc_launch_count(ctx)
                     assert np.array_equal(got, ref), (nb, prec, k)
-                    assert n2 - n1 == (n1 - n0) + 1, (nb, prec, k)  # the constants kernel is a node of the graph
+                    by_value = prec == "fp32" and group is ids
+                    assert n2 - n1 == (n1 - n0) + (0 if by_value else 1), (nb, prec, k)
     for sid in ids + [lid]:
         api.osc_unload_sample(ctx, sid)
 
