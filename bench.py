@@ -72,7 +72,7 @@ def _dist():
 
 
 KERNEL_SOURCES = ("osc_internal.h", "osc_math.cuh", "osc_kernels.cuh", "osc_kernels_fp32.cu")
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_hist_fp32_precision10M_1pt.md")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_hist_inline_fp32_precision10M_1pt.md")
 
 
 def _kernel_source_hash():
@@ -800,8 +800,9 @@ def run_profile_case(args):
     """Small fixed case for ncu captures: --events events of the beam-shaped
     sample x --points scan points, --launches histogram launches with the given
     points-per-block tile (0 = autotuned) and precision.  --method picks the
-    event-by-event histogram (ebe), the bin-centre method (bc, 410 true bins of
-    25 MeV) or event-by-event through three layers (layers)."""
+    event-by-event histogram (ebe), the fit step of the first point
+    (osc_histogram_point: the bench's step), the bin-centre method (bc, 410 true
+    bins of 25 MeV) or event-by-event through three layers (layers)."""
     import torch
 
     from paper_1311_7579_gb300 import api, synth
@@ -819,7 +820,10 @@ def run_profile_case(args):
         api.osc_set_layers(c, sid, [(100.0, 2.2, 0.5), (95.0, 3.0, 0.5), (100.0, 2.2, 0.5)])
     out = torch.zeros((1, args.points, NBINS), dtype=torch.float64, device="cuda")
     for _ in range(args.launches):
-        if args.method == "bc":
+        if args.method == "step":
+            # the fit step: one point by value, its constants computed on the host
+            api.osc_histogram_point(c, [sid], pts[0], args.prec, LO, HI, NBINS, out=out)
+        elif args.method == "bc":
             api.osc_histogram_bin_centre(c, [sid], 0, args.points, args.prec, 0.0, 10.25, 410, LO, HI, NBINS, out=out)
         else:
             api.osc_histogram(c, [sid], 0, args.points, args.prec, LO, HI, NBINS, out=out)
@@ -859,7 +863,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--launches", type=int, default=2)
-    ap.add_argument("--method", default="ebe", choices=["ebe", "bc", "layers"])
+    ap.add_argument("--method", default="ebe", choices=["ebe", "step", "bc", "layers"])
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)

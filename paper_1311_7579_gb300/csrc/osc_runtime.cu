@@ -1126,6 +1126,36 @@ static osc_status run_step_graph(osc_ctx *ctx, Plan *p, const osc_point &pt, dou
                           reinterpret_cast<double *>(pin.data() + sizeof(float) * C32_STRIDE));
         iargs[1] = pin.data();
     }
+    if (ctx->timing) {
+        // timing mode: direct launches with events around the kernels (the
+        // constants kernel, where one runs, and the histogram kernel)
+        if (!inl) {
+            cudaEvent_t c0 = pool_event(ctx), c1 = pool_event(ctx);
+            CK(cudaEventRecord(c0, ctx->stream));
+            CK(launch_point_consts_host(&pt, 1, ctx->d_pc32, ctx->d_pc64, ctx->stream));
+            CK(cudaEventRecord(c1, ctx->stream));
+            ctx->ev_pending.push_back({0, {c0, c1}});
+        }
+        cudaEvent_t h0 = pool_event(ctx), h1 = pool_event(ctx);
+        CK(cudaEventRecord(h0, ctx->stream));
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(inl ? ctx->n_sm * hist_inline_blocks_per_sm() : p->grid);
+        cfg.blockDim = dim3(plan_threads(p));
+        cfg.stream = ctx->stream;
+        CK(cudaLaunchKernelExC(&cfg, inl ? hist_inline_kernel_fn() : plan_kernel(p), inl ? iargs : hargs));
+        CK(cudaEventRecord(h1, ctx->stream));
+        ctx->ev_pending.push_back({1, {h0, h1}});
+        if (p->d_redo) CK(launch_redo_programmatic(p->prec, hp, ctx->stream));
+        if (!fused) {
+            cudaEvent_t f0 = pool_event(ctx), f1 = pool_event(ctx);
+            CK(cudaEventRecord(f0, ctx->stream));
+            CK(launch_final_programmatic(fp, ctx->stream));
+            CK(cudaEventRecord(f1, ctx->stream));
+            ctx->ev_pending.push_back({2, {f0, f1}});
+        }
+        ctx->launches += (inl ? 1 : 2) + (p->d_redo ? 1 : 0) + (fused ? 0 : 1);
+        return OSC_OK;
+    }
     cudaKernelNodeParams kc{}, kh{}, kr{}, kf{};
     kc.func = (void *)point_consts_one_fn();
     kc.gridDim = dim3(1);
@@ -1391,8 +1421,8 @@ extern "C" osc_status osc_histogram_point(osc_ctx *ctx, const int32_t *sample_id
                                           const osc_point *pt, osc_precision prec, double lo, double hi,
                                           int32_t nbins, double *out, int out_on_device) {
     NvtxRange nvtx_range("osc_histogram_point");
-    if (!ctx || !pt || !out || ctx->timing || ctx->poisoned) {
-        // timing mode keeps the per-kernel event records of the two calls
+    if (!ctx || !pt || !out || ctx->poisoned) {
+        // (the two calls report the argument errors)
         const osc_status s = osc_set_params(ctx, pt, 1);
         if (s) return s;
         return osc_histogram(ctx, sample_ids, n_samples, 0, 1, prec, lo, hi, nbins, out, out_on_device);
