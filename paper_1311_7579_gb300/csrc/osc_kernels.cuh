@@ -570,9 +570,11 @@ struct RunAcc {
 };
 // FP32 precisions: each addend is below 2^63 and a lane's run holds fewer than
 // 2^31 events, so the run fits a 96-bit two's-complement sum a0 + a1 2^32 + a2 2^64
-// (a2 signed), three 32-bit limbs added with one carry chain.
+// (a2 signed), three 32-bit limbs added with one carry chain.  A negative addend
+// enters as its one's complement; neg counts them, the +1 each that completes
+// the two's complement, added when the run's value is read.
 struct RunAcc32 {
-    unsigned a0 = 0, a1 = 0, a2 = 0;
+    unsigned a0 = 0, a1 = 0, a2 = 0, neg = 0;
     int cur_b = -1;
 };
 template <int PREC>
@@ -582,14 +584,15 @@ struct AccOf<kFP64> { using T = RunAcc; };
 
 // The run's 128-bit value: (lo, hi) with hi the sign extension of a2.
 __device__ __forceinline__ void run_value(const RunAcc32 &r, unsigned long long &lo, unsigned long long &hi) {
-    lo = ((unsigned long long)r.a1 << 32) | r.a0;
-    hi = (unsigned long long)(long long)(int)r.a2;
+    const unsigned long long l = ((unsigned long long)r.a1 << 32) | r.a0;
+    lo = l + r.neg;
+    hi = (unsigned long long)(long long)(int)(r.a2 + (lo < l ? 1u : 0u));
 }
 __device__ __forceinline__ void run_value(const RunAcc &r, unsigned long long &lo, unsigned long long &hi) {
     lo = r.lo;
     hi = r.hi;
 }
-__device__ __forceinline__ void run_clear(RunAcc32 &r) { r.a0 = r.a1 = r.a2 = 0; }
+__device__ __forceinline__ void run_clear(RunAcc32 &r) { r.a0 = r.a1 = r.a2 = r.neg = 0; }
 __device__ __forceinline__ void run_clear(RunAcc &r) { r.lo = r.hi = 0; }
 template <class R>
 __device__ __forceinline__ void run_flush(const R &r, unsigned long long *accp) {
@@ -614,32 +617,35 @@ __device__ __forceinline__ void fx_halves(V wabs, int sh, V &hf, V &lf) {
     hf = vmap(vmul(x, vb<V>(2.3283064365386963e-10f)), [](float v) { return floorf(v); });
     lf = vfma(hf, vb<V>(-4294967296.0f), x);
 }
-// Adds (neg ? -1 : +1) (hi 2^32 + lo) to the lane's run.
-__device__ __forceinline__ void fx_add3(RunAcc32 &r, unsigned hi, unsigned lo, bool neg) {
-    if (neg) {
-        asm("sub.cc.u32 %0, %0, %3;\n\tsubc.cc.u32 %1, %1, %4;\n\tsubc.u32 %2, %2, 0;"
-            : "+r"(r.a0), "+r"(r.a1), "+r"(r.a2)
-            : "r"(lo), "r"(hi));
-    } else {
-        asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, 0;"
-            : "+r"(r.a0), "+r"(r.a1), "+r"(r.a2)
-            : "r"(lo), "r"(hi));
-    }
+// Adds hi 2^32 + lo to the lane's run, negated when m = 0xffffffff (the weight's
+// sign, spread over 32 bits; m = 0: as is), without a branch: the one's
+// complement (lo ^ m, hi ^ m, m) goes through the carry chain and r.neg counts
+// the missing +1.
+__device__ __forceinline__ void fx_add3(RunAcc32 &r, unsigned hi, unsigned lo, unsigned m) {
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+        : "+r"(r.a0), "+r"(r.a1), "+r"(r.a2)
+        : "r"(lo ^ m), "r"(hi ^ m), "r"(m));
+    r.neg -= m;  // +1 for m = 0xffffffff
 }
+// The sign of w as a 32-bit mask (all ones for a negative w).
+__device__ __forceinline__ unsigned sign_mask(float w) { return (unsigned)((int)__float_as_uint(w) >> 31); }
 // One event: tb = sf E_reco - lo and u = tb / width (by the reciprocal width)
-// decide the bin; (hf, lf) are its addend's halves, neg the weight's sign.  An
-// event outside the histogram (or inactive) changes nothing: it takes no bin and
-// adds zero.
+// decide the bin; (hf, lf) are its addend's halves (zero for an event outside
+// the histogram or inactive, which then changes nothing), m its sign mask.
 __device__ __forceinline__ void acc_event_u(RunAcc32 &r, unsigned long long *accp, const HistParams &prm, float tb,
-                                            float u, float hf, float lf, bool neg, bool in) {
+                                            float u, float hf, float lf, unsigned m, bool in) {
     const int b = __float2int_rz(u);
-    if (in && !debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) in = false;
+    unsigned h = __float2uint_rz(hf), l = __float2uint_rz(lf);
+    if (in && !debug_ok(b >= 0 && b < prm.nbins, prm.counter, kDbgBin)) {
+        in = false;
+        h = l = m = 0u;
+    }
     if (in && b != r.cur_b) {
         run_flush(r, accp);
         run_clear(r);
         r.cur_b = b;
     }
-    fx_add3(r, in ? __float2uint_rz(hf) : 0u, in ? __float2uint_rz(lf) : 0u, neg);
+    fx_add3(r, h, l, m);
 }
 __device__ __forceinline__ void acc_event_f32(RunAcc32 &r, unsigned long long *accp, const HistParams &prm, float sf,
                                               float er, float wt, int sh, bool active) {
@@ -648,7 +654,7 @@ __device__ __forceinline__ void acc_event_f32(RunAcc32 &r, unsigned long long *a
     const bool in = active && tb >= 0.0f && u < prm.nb_f;
     float hf, lf;
     fx_halves(in ? fabsf(wt) : 0.0f, sh, hf, lf);
-    acc_event_u(r, accp, prm, tb, u, hf, lf, wt < 0.0f, in);
+    acc_event_u(r, accp, prm, tb, u, hf, lf, sign_mask(wt), in);
 }
 // Two events in order (a, then b), their bin and addend arithmetic in one packed
 // chain: the same bins and sums as two acc_event_f32 calls.
@@ -660,8 +666,8 @@ __device__ __forceinline__ void acc_pair_f32(RunAcc32 &r, unsigned long long *ac
     const bool in_b = act_b && tb.y >= 0.0f && u.y < prm.nb_f;
     float2 hf, lf;
     fx_halves(make_float2(in_a ? fabsf(wt.x) : 0.0f, in_b ? fabsf(wt.y) : 0.0f), sh, hf, lf);
-    acc_event_u(r, accp, prm, tb.x, u.x, hf.x, lf.x, wt.x < 0.0f, in_a);
-    acc_event_u(r, accp, prm, tb.y, u.y, hf.y, lf.y, wt.y < 0.0f, in_b);
+    acc_event_u(r, accp, prm, tb.x, u.x, hf.x, lf.x, sign_mask(wt.x), in_a);
+    acc_event_u(r, accp, prm, tb.y, u.y, hf.y, lf.y, sign_mask(wt.y), in_b);
 }
 __device__ __forceinline__ void acc_event_f64(RunAcc &r, unsigned long long *accp, const HistParams &prm, float sf,
                                               float er, double wt, double hs, bool active) {

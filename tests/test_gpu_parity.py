@@ -172,6 +172,44 @@ def test_histograms_of_subnormal_weights(ctx):
     api.osc_unload_sample(ctx, sid)
 
 
+def test_mixed_sign_weights_sum_exactly(ctx):
+    """Weights of both signs in the same bins (an FP32-precision run adds a
+    negative addend as its one's complement and counts the missing ones): every
+    FP32 bin equals the exact integer sum of floor(|w| 2^F) with the signs of the
+    GPU's own per-event weights, scaled by 2^-F, whatever the tile shape, and the
+    FP64 bins match the oracle's."""
+    import math
+    s = dict(synth.table1_sample(40000, seed=71))
+    rng = np.random.default_rng(72)
+    s["w_mc"] = (s["w_mc"] * np.where(rng.random(s["n"]) < 0.4, -1.0, 1.0)).astype(np.float32)
+    sid = api.osc_load_sample(ctx, s)
+    pts = synth.scan_points(3, seed=73)
+    api.osc_set_params(ctx, pts)
+    F = 62 - math.ceil(math.log2(float(np.max(np.abs(s["w_mc"])))))
+    ref = {}
+    for prec in ("fp32", "fp64"):
+        for ppb in (1, 4, 256):
+            api.osc_set_tile(ctx, ppb, 0)
+            h = api.osc_histogram(ctx, [sid], 0, 3, prec, LO, HI, NB)[0]
+            ref.setdefault(prec, h)
+            assert np.array_equal(h, ref[prec]), (prec, ppb)
+    api.osc_set_tile(ctx, 0, 0)
+    for k in range(3):
+        _, w = _gpu_probs(ctx, sid, k, "fp32", s["n"])
+        b = oracle.bins(s["e_reco"], pts[k, 6], LO, HI, NB)
+        exact = [0] * NB
+        for bi, wi in zip(b, w):
+            if bi >= 0:
+                x = math.floor(abs(float(wi)) * 2.0 ** F)
+                exact[bi] += -x if wi < 0 else x
+        want = np.array([math.ldexp(v, -F) for v in exact]) * pts[k, 7]
+        assert np.max(np.abs(ref["fp32"][k] - want) - 1e-15 * np.abs(want)) <= 0.0, k
+        _, wo = oracle.reweight(s, oracle.point_from_row(pts[k]))
+        ho = oracle.hist_from_weights(s["e_reco"], wo, pts[k, 6], LO, HI, NB, compensated=True)
+        assert np.max(np.abs(ref["fp64"][k] - ho)) <= 1e-9 * np.max(np.abs(ho)), k
+    api.osc_unload_sample(ctx, sid)
+
+
 def test_histogram_bitwise_independent_of_tile_shape(ctx):
     s = synth.table1_sample(50000, seed=12)
     sid = api.osc_load_sample(ctx, s)
