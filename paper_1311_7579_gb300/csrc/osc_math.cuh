@@ -28,10 +28,11 @@
 // (<= 0.72 rad for the beam workloads here), so those parts of the phases are
 // accurate in FP32; the large vacuum parts tau (d_l - d_0) are formed in
 // float-float and reduced exactly in revolutions.  The FP32 amplitude takes the
-// Sylvester numerators in the vacuum mass basis (amplitude_mass32), where every
+// Sylvester numerators in the vacuum mass basis (amplitude_bulk), where every
 // factor is a vacuum gap minus a matter shift, and bounds its own rounding error
 // per event; an event whose bound exceeds the tolerance is recomputed in FP64
-// (prob_redo64, osc_kernels.cuh).
+// (prob_redo64, osc_kernels.cuh).  The FP32-bulk chain runs on one event or on
+// two at once in packed instructions (see the lane notes below).
 #pragma once
 
 #include <stdint.h>
