@@ -478,30 +478,86 @@ __device__ __forceinline__ void fused_final(const HistParams &prm) {
     }
 }
 
-// Per-warp variant for one-point items: warps that finish early exit without
-// waiting at a block barrier; the last warp converts four bins per lane per round.
-// The histogram metadata (scales, point index) of the first conversion round's
-// bins, four per lane: written by the host before any launch, so it can be read
-// before a kernel's grid-dependency wait.
+// The histogram metadata (scales, point index) of a thread's first bin: written
+// by the host before any launch, so it can be read before a kernel's
+// grid-dependency wait; and, loaded after the wait, that bin's digit columns and
+// norm.
 struct FinMeta {
-    double m0[4], m1[4], pt[4];
+    double m0 = 0.0, m1 = 0.0, pt = 0.0, nm = 0.0;
+    bool loaded = false;
+    Digits d{};
 };
-__device__ __forceinline__ void fin_meta_load(const HistParams &prm, FinMeta &fm) {
-    const int lane = threadIdx.x & 31;
-    const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int64_t i = lane + 32 * k;
-        fm.m0[k] = fm.m1[k] = fm.pt[k] = 0.0;
-        if (i < n) {
-            const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
-            fm.m0[k] = m[0];
-            fm.m1[k] = m[1];
-            fm.pt[k] = m[3];
-        }
+// The converting group's threads g = 0 .. G - 1 take bins g, g + G, ... of the output.
+__device__ __forceinline__ void fin_meta_load(const HistParams &prm, FinMeta &fm, int g) {
+    if (g < prm.fin_n_hist * (int64_t)prm.nbins) {
+        const double *m = prm.fin_hmeta + 4 * (g / prm.nbins);
+        fm.m0 = m[0];
+        fm.m1 = m[1];
+        fm.pt = m[3];
     }
 }
-__device__ __forceinline__ void convert_bins_warp(const HistParams &prm, const FinMeta *pre = nullptr);
+// After the wait: the bin's digit columns and norm, issued together with the
+// caller's other loads (they go unused when the pass has events to recompute).
+__device__ __forceinline__ void fin_data_load(const HistParams &prm, FinMeta &fm, int g) {
+    if (g < prm.fin_n_hist * (int64_t)prm.nbins) {
+        fm.d = load_digits(prm.acc, g);
+        fm.nm = prm.pc64[(int64_t)fm.pt * C64_STRIDE + C64_NORM];
+    }
+    fm.loaded = true;
+}
+// Converts every bin of the output (kU bins per thread and round) and resets the
+// work counters; the group is threads g = 0 .. G - 1 (one warp: G = 32).
+__device__ __forceinline__ void convert_bins(const HistParams &prm, int g, int G, const FinMeta *pre) {
+    constexpr int kU = 4;
+    const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
+    for (int64_t i0 = 0; i0 < n; i0 += (int64_t)G * kU) {
+        Digits d[kU];
+        double m0[kU], m1[kU], nm[kU];
+        bool norm_in[kU];  // the norm itself (loaded ahead) rather than the point index
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t i = i0 + g + (int64_t)G * k;
+            const bool ahead = pre && i0 == 0 && k == 0;  // the thread's first bin, loaded ahead
+#pragma unroll
+            for (int q = 0; q < kDigits; ++q) d[k].d[q] = 0ull;
+            m0[k] = m1[k] = nm[k] = 0.0;
+            norm_in[k] = ahead && pre->loaded;
+            if (i < n) {
+                if (ahead) {
+                    m0[k] = pre->m0;
+                    m1[k] = pre->m1;
+                    nm[k] = pre->loaded ? pre->nm : pre->pt;
+                } else {
+                    const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
+                    m0[k] = m[0];
+                    m1[k] = m[1];
+                    nm[k] = m[3];
+                }
+                d[k] = (ahead && pre->loaded) ? pre->d : load_digits(prm.acc, i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (!norm_in[k] && i0 + g + (int64_t)G * k < n) nm[k] = prm.pc64[(int64_t)nm[k] * C64_STRIDE + C64_NORM];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t i = i0 + g + (int64_t)G * k;
+            if (i < n) {
+                clear_digits(prm.acc, i);
+                prm.fin_out[i] = bin_value(d[k], m0[k], m1[k], nm[k]);
+            }
+        }
+    }
+    if (g == 0) {
+        prm.counter[0] = 0;
+        prm.counter[1] = 0;
+    }
+}
+// The last warp's conversion of the fused finalize (four bins per lane per round,
+// all loads of a round issued before any conversion), then the counter reset.
+__device__ __forceinline__ void convert_bins_warp(const HistParams &prm) { convert_bins(prm, threadIdx.x & 31, 32, nullptr); }
+// Per-warp variant for one-point items: warps that finish early exit without
+// waiting at a block barrier; the last warp converts four bins per lane per round.
 __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     const int lane = threadIdx.x & 31;
     __threadfence();
@@ -512,53 +568,6 @@ __device__ __forceinline__ void fused_final_warp(const HistParams &prm) {
     if (!last) return;
     __threadfence();
     convert_bins_warp(prm);
-}
-// The last warp's conversion of the fused finalize (four bins per lane per round,
-// all loads of a round issued before any conversion), then the counter reset.
-__device__ __forceinline__ void convert_bins_warp(const HistParams &prm, const FinMeta *pre) {
-    const int lane = threadIdx.x & 31;
-    constexpr int kU = 4;
-    const int64_t n = prm.fin_n_hist * (int64_t)prm.nbins;
-    for (int64_t i0 = 0; i0 < n; i0 += 32 * kU) {
-        Digits d[kU];
-        double m0[kU], m1[kU], nm[kU];
-        const bool have = pre && i0 == 0;  // the first round's metadata loaded ahead
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const int64_t i = i0 + lane + 32 * k;
-#pragma unroll
-            for (int q = 0; q < kDigits; ++q) d[k].d[q] = 0ull;
-            m0[k] = m1[k] = nm[k] = 0.0;
-            if (i < n) {
-                d[k] = load_digits(prm.acc, i);
-                if (have) {
-                    m0[k] = pre->m0[k];
-                    m1[k] = pre->m1[k];
-                    nm[k] = pre->pt[k];
-                } else {
-                    const double *m = prm.fin_hmeta + 4 * (i / prm.nbins);
-                    m0[k] = m[0];
-                    m1[k] = m[1];
-                    nm[k] = m[3];
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kU; ++k)
-            if (i0 + lane + 32 * k < n) nm[k] = prm.pc64[(int64_t)nm[k] * C64_STRIDE + C64_NORM];
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const int64_t i = i0 + lane + 32 * k;
-            if (i < n) {
-                clear_digits(prm.acc, i);
-                prm.fin_out[i] = bin_value(d[k], m0[k], m1[k], nm[k]);
-            }
-        }
-    }
-    if (lane == 0) {
-        prm.counter[0] = 0;
-        prm.counter[1] = 0;
-    }
 }
 
 // Bin one weighted event under the point's energy scale and add it to the lane's
@@ -1225,18 +1234,21 @@ struct PointInline {
     double c64[C64_STRIDE];
 };
 template <int PREC>
-__global__ void __launch_bounds__(kNT) k_redo(const HistParams prm) {
+__global__ void __launch_bounds__(kNT, 2) k_redo(const HistParams prm) {
     grid_dependents_launch();  // a finalize kernel after this one may become resident early
-    // the converting warp reads the histograms' metadata before the wait, so that
-    // after it one round of loads (the digit columns and the norms) remains
+    // Four warps of block 0 convert the fused finalize's bins: they read the
+    // histograms' metadata before the wait, and after it issue the recomputation
+    // count, the digit columns and the norms in one round of loads.
+    constexpr int kConvThreads = 128;
     FinMeta fm;
-    const bool conv = prm.fuse_final && blockIdx.x == 0 && threadIdx.x < 32;
-    if (conv) fin_meta_load(prm, fm);
+    const bool conv = prm.fuse_final && blockIdx.x == 0 && threadIdx.x < kConvThreads;
+    if (conv) fin_meta_load(prm, fm, threadIdx.x);
     grid_dependency_wait();
+    if (conv) fin_data_load(prm, fm, threadIdx.x);
     if (__ldcg(prm.counter + kRedoCount) == 0) {
-        // nothing to recompute: one warp does the fused finalize the histogram
-        // kernel left to this kernel (and resets the work counters)
-        if (conv) convert_bins_warp(prm, &fm);
+        // nothing to recompute: the conversion the histogram kernel left to this
+        // kernel (it also resets the work counters)
+        if (conv) convert_bins(prm, threadIdx.x, kConvThreads, &fm);
         return;
     }
     const int lane = threadIdx.x & 31;
