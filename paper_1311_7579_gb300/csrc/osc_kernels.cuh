@@ -843,7 +843,10 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm, const
     // warp on the same counter; later tickets come from the counter, offset
     // past the static ones.  A second ticket is held ahead only when items are
     // plentiful (a warp holding two tickets of a scarce list would leave other
-    // warps idle).
+    // warps idle), and only until the last 2 x n_warps tickets: the list is
+    // sorted largest first, so those are its shortest items, and a warp holding
+    // one of them ahead when the counter runs out would end the grid up to two
+    // items after the first idle warp instead of one.
     const bool ahead = prm.n_items >= 3 * n_warps;
     const int dyn0 = ahead ? 2 * n_warps : n_warps;
     int it = gw, nxt = ahead ? gw + n_warps : 0;
@@ -1026,12 +1029,17 @@ __device__ __forceinline__ void hist_items_per_warp(const HistParams &prm, const
                 mark_redo(prm);
             }
         }
-        // move to the ticket held ahead and fetch the one after it, or (few
-        // items) take the next ticket now; the next item's first events are in
-        // flight while this item's runs are closed
+        // move to the ticket held ahead and fetch the one after it (none, -1,
+        // from the last 2 x n_warps tickets on), or (few items, or none held)
+        // take the next ticket now; the next item's first events are in flight
+        // while this item's runs are closed
         if (ahead) {
             it = __shfl_sync(0xffffffffu, nxt, 0);
-            if (lane == 0 && it < prm.n_items) nxt = atomicAdd(prm.counter, 1) + dyn0;
+            if (it < 0) {
+                if (lane == 0) it = atomicAdd(prm.counter, 1) + dyn0;
+                it = __shfl_sync(0xffffffffu, it, 0);
+            }
+            if (lane == 0) nxt = it < prm.n_items - dyn0 ? atomicAdd(prm.counter, 1) + dyn0 : -1;
         } else {
             if (lane == 0) it = atomicAdd(prm.counter, 1) + dyn0;
             it = __shfl_sync(0xffffffffu, it, 0);
