@@ -472,11 +472,12 @@ def test_histogram_point_graph_step_separate_finalize_and_layers(ctx):
 
 
 def test_histogram_point_graph_step_runs_the_recomputation_pass(ctx):
-    """At extreme mixing angles the FP32 kernels leave events to the FP64
-    recomputation pass: the graph step's conditional node then runs it, and the
-    bins equal the direct launches' (which always launch the pass) bitwise, for
-    the fused (100 bins) and separate (600 bins) finalize; the per-event
-    probabilities of those points stay within the FP32 tolerance."""
+    """At extreme mixing angles the FP32-bulk kernels leave events to the FP64
+    recomputation pass launched after them (in the fit step's graph, joined by a
+    programmatic edge).  The bins agree bitwise across the step, one-point items
+    of two sizes and point tiles of 4 and 16, for the fused (100 bins) and
+    separate (600 bins) finalize; the per-event probabilities of those points
+    stay within the FP32 tolerance."""
     s = synth.all_channel_sample(20000, seed=28, L_km=295.0, rho=2.6, e_lo=0.05, e_hi=3.0)
     sid = api.osc_load_sample(ctx, s)
     pts = np.array([[0.01, 0.0251, 0.99, 7.6e-5, -2.4e-3, 3.1, 1.0, 1.0],
@@ -491,6 +492,11 @@ def test_histogram_point_graph_step_runs_the_recomputation_pass(ctx):
             for _ in range(2):
                 got = api.osc_histogram_point(ctx, [sid], pts[k], "fp32", LO, HI, nb)
                 assert np.array_equal(got, ref), (k, nb)
+            for ppb, chunk in ((1, 256), (1, 4096), (4, 0), (16, 0)):
+                api.osc_set_tile(ctx, ppb, chunk)
+                got = api.osc_histogram(ctx, [sid], 0, 1, "fp32", LO, HI, nb)
+                api.osc_set_tile(ctx, 0, 0)
+                assert np.array_equal(got, ref), (k, nb, ppb, chunk)
     api.osc_unload_sample(ctx, sid)
 
 
