@@ -210,6 +210,29 @@ def test_mixed_sign_weights_sum_exactly(ctx):
     api.osc_unload_sample(ctx, sid)
 
 
+def test_one_point_ticket_modes_give_the_same_bins(ctx):
+    """One-point work items are scheduled three ways: few items (one ticket at a
+    time), many items (a ticket held one item ahead), and, over the last
+    2 x warps tickets of a long list, one ticket at a time again.  64-event items
+    over 2M events (31250 items, more than three per warp) run all three; the
+    bins equal those of 4096-event items (few items) bitwise, in both
+    precisions, through osc_histogram and the fit step."""
+    s = synth.precision_sample(2_000_000, seed=29)
+    sid = api.osc_load_sample(ctx, s)
+    pt = synth.table1_point()
+    api.osc_set_params(ctx, pt[None, :])
+    for prec in ("fp32", "fp64"):
+        api.osc_set_tile(ctx, 1, 4096)
+        ref = api.osc_histogram(ctx, [sid], 0, 1, prec, LO, HI, NB)
+        api.osc_set_tile(ctx, 1, 64)
+        for _ in range(2):
+            assert np.array_equal(api.osc_histogram(ctx, [sid], 0, 1, prec, LO, HI, NB), ref), prec
+            assert np.array_equal(api.osc_histogram_point(ctx, [sid], pt, prec, LO, HI, NB), ref), prec
+        api.osc_set_tile(ctx, 0, 0)
+        assert np.array_equal(api.osc_histogram(ctx, [sid], 0, 1, prec, LO, HI, NB), ref), prec
+    api.osc_unload_sample(ctx, sid)
+
+
 def test_histogram_bitwise_independent_of_tile_shape(ctx):
     s = synth.table1_sample(50000, seed=12)
     sid = api.osc_load_sample(ctx, s)
